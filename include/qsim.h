@@ -1,0 +1,237 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector simulator.
+ *
+ * The library applies sequences of elementary gates to the 2^n complex
+ * amplitudes of an n-qubit register held in GPU memory, the operation that
+ * Sec. III.A of De Raedt et al., "Massive parallel quantum computer simulator"
+ * (quant-ph/0608239) reduces every quantum algorithm to (Eqs. NUM2-NUM8).
+ *
+ * Conventions for every entry point:
+ *  - Qubit q is bit q of the amplitude index, qubit 0 the least significant
+ *    bit (Sec. II.A, Eq. STAT2).  Amplitudes are interleaved (re, im): float2
+ *    for QSIM_C64, double2 for QSIM_C128.
+ *  - Qubit arguments are LOGICAL qubits.  The library may keep the amplitudes
+ *    under a permutation sigma of the index bits (the qubit-to-bit map of
+ *    Sec. III.B); every reader (qsim_get_state, qsim_probs, qsim_qubit_probs,
+ *    qsim_sample) undoes it, so callers always see logical order.
+ *  - Gate matrices arrive as IEEE double (re, im) pairs, row-major, and are
+ *    rounded to the state's precision on entry.  Unitarity is not checked.
+ *  - Calls that only enqueue GPU work are asynchronous and stream-ordered on
+ *    the handle's stream.  Calls that return values to host memory
+ *    (qsim_norm, qsim_probs, qsim_qubit_probs, qsim_get_state, qsim_sample)
+ *    synchronise that stream before returning.
+ *  - All buffers passed in are owned by the caller and are not retained after
+ *    the call returns.  A handle owns its device memory unless it was made by
+ *    qsim_attach.
+ *  - No call aborts the process.  A failed call returns a non-zero
+ *    qsim_status, leaves the state unchanged when the failure is detected on
+ *    the host (bad argument), and records a message for qsim_last_error().
+ *  - Handles are not thread-safe; distinct handles may be used from distinct
+ *    host threads.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QSIM_API __attribute__((visibility("default")))
+#else
+#define QSIM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QSIM_OK = 0,
+    QSIM_EINVAL = 1,        /* bad argument; nothing was changed */
+    QSIM_ENOMEM = 2,        /* device or pinned host allocation failed */
+    QSIM_ECUDA = 3,         /* a CUDA call failed; see qsim_last_error() */
+    QSIM_ETIMEOUT = 4,      /* a bounded device-side wait expired */
+    QSIM_EUNSUPPORTED = 5   /* valid request this build cannot serve */
+} qsim_status;
+
+typedef enum {
+    QSIM_C64 = 0,           /* complex64: float2 amplitudes, FP32 arithmetic */
+    QSIM_C128 = 1           /* complex128: double2 amplitudes, FP64 arithmetic */
+} qsim_dtype;
+
+typedef struct qsim_state *qsim_handle;
+
+/* Gate kinds of qsim_gate.kind (Sec. II). */
+enum {
+    QSIM_GATE_H = 0,    /* Hadamard, Eq. Hadamard */
+    QSIM_GATE_X = 1,    /* pi/2 rotation about x, e^{i pi S^x/2}, Eq. Xoperation */
+    QSIM_GATE_Y = 2,    /* pi/2 rotation about y, e^{i pi S^y/2}, Eq. Yoperation */
+    QSIM_GATE_XB = 3,   /* inverse of X */
+    QSIM_GATE_YB = 4,   /* inverse of Y */
+    QSIM_GATE_NOT = 5,  /* bit flip: CNOT with one control (Eq. NUM6), Toffoli with two (Eq. NUM8) */
+    QSIM_GATE_R = 6,    /* phase shift R(phi) = diag(1, e^{i phi}), Eq. singlephase; param[0] = phi */
+    QSIM_GATE_V = 7,    /* V(phi) of Eq. COMM4; param[0] = phi */
+    QSIM_GATE_SU2 = 8,  /* [[a+ib, c+id], [-c+id, a-ib]], param[0..3] = (a, b, c, d) */
+    QSIM_GATE_U = 9,    /* explicit 2x2 matrix, param[0..7] = row-major (re, im) */
+    QSIM_GATE_SWAP = 10 /* quantum SWAP gate of target and target2 */
+};
+
+/* One gate of a circuit.  Any gate may carry controls: it then acts only on
+ * the amplitudes whose control bits are all 1 (Eqs. NUM6-NUM8). */
+typedef struct {
+    int32_t kind;       /* QSIM_GATE_* */
+    int32_t target;     /* logical target qubit */
+    int32_t target2;    /* second target (QSIM_GATE_SWAP), else ignored */
+    int32_t reserved;   /* must be 0 */
+    uint64_t ctrl_mask; /* logical control qubits, bit q = qubit q; must not contain a target */
+    double param[8];    /* kind-specific parameters (see above) */
+} qsim_gate;
+
+/* How qsim_run_circuit executes a gate list. */
+enum {
+    QSIM_MODE_PERGATE = 0, /* one sweep of the state per gate (Sec. III.A) */
+    QSIM_MODE_FUSED = 1    /* planner: shared-memory tile passes, qubit
+                              interchanges and dense fused blocks */
+};
+
+typedef struct {
+    int32_t mode;       /* QSIM_MODE_* */
+    int32_t tile_bits;  /* T, qubits held per shared-memory tile; 0 = default */
+    int32_t fuse_k;     /* width of dense fused blocks; 0 = planner default, -1 = never */
+    int32_t max_swap;   /* most bit pairs exchanged per interchange pass; 0 = default */
+    int32_t reserved[4];
+} qsim_opts;
+
+/* Fill opts with the defaults (QSIM_MODE_FUSED, automatic sizes). */
+QSIM_API void qsim_default_opts(qsim_opts *opts);
+
+/* ---- state lifetime ------------------------------------------------------
+ * qsim_alloc: allocate an n-qubit state (1 <= n <= 34) on the current CUDA
+ * device and set it to |0...0>.  Memory is 2^n * 8 bytes (C64) or 2^n * 16
+ * bytes (C128) (Sec. III.A: the state needs 2^(n+4) bytes in double).
+ * Errors: EINVAL (n out of range, out == NULL), ENOMEM, ECUDA. */
+QSIM_API qsim_status qsim_alloc(int n, qsim_dtype dt, qsim_handle *out);
+
+/* qsim_attach: wrap caller-owned device memory dev_ptr (2^n amplitudes of dt,
+ * 16-byte aligned) and a CUDA stream (cudaStream_t, or NULL for the legacy
+ * default stream).  The contents are left as they are and read in logical
+ * order.  qsim_free releases only the handle. */
+QSIM_API qsim_status qsim_attach(void *dev_ptr, int n, qsim_dtype dt, void *stream, qsim_handle *out);
+
+/* qsim_free: release the handle (and its memory, unless attached).  NULL is a
+ * no-op.  Waits for the handle's pending work. */
+QSIM_API qsim_status qsim_free(qsim_handle h);
+
+/* Set the stream later work is enqueued on (cudaStream_t or NULL). */
+QSIM_API qsim_status qsim_set_stream(qsim_handle h, void *cuda_stream);
+
+/* Query size, dtype and device pointer. */
+QSIM_API qsim_status qsim_info(qsim_handle h, int *n, qsim_dtype *dt, void **dev_ptr);
+
+/* ---- initial states -------------------------------------------------------
+ * qsim_set_basis: INITIAL STATE x (App. A): a_x = 1, all others 0; resets the
+ * qubit-to-bit map to the identity.  EINVAL if x >= 2^n. */
+QSIM_API qsim_status qsim_set_basis(qsim_handle h, uint64_t x);
+
+/* qsim_set_state: copy 2^n amplitudes (logical order, the state's dtype) from
+ * host memory; resets the map to the identity.  bytes must equal the state
+ * size. */
+QSIM_API qsim_status qsim_set_state(qsim_handle h, const void *host_in, size_t bytes);
+
+/* ---- gates ----------------------------------------------------------------
+ * qsim_apply_1q: a'0 = U00 a0 + U01 a1, a'1 = U10 a0 + U11 a1 on every pair
+ * of amplitudes (a0, a1) whose indices differ only in bit t (Eqs. NUM2-NUM5
+ * for a general 2x2 U).  U = 8 doubles, row-major (re, im).  EINVAL if t is
+ * not in [0, n) or U is NULL. */
+QSIM_API qsim_status qsim_apply_1q(qsim_handle h, int t, const double U[8]);
+
+/* qsim_apply_ctrl: as qsim_apply_1q but only on pairs whose control qubits
+ * (ctrl_mask, logical) are all 1: CNOT (Eq. NUM6), controlled phase
+ * (Eq. COMM5), controlled-V (Eq. NUM7), Toffoli (Eq. NUM8) and any
+ * multi-controlled U.  EINVAL if ctrl_mask contains t or a bit >= n. */
+QSIM_API qsim_status qsim_apply_ctrl(qsim_handle h, uint64_t ctrl_mask, int t, const double U[8]);
+
+/* qsim_apply_gate: one qsim_gate (any kind, with controls). */
+QSIM_API qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g);
+
+/* qsim_apply_fused: dense 2^k x 2^k unitary U (row-major, 2 * 4^k doubles
+ * (re, im)) on the k distinct logical qubits qubits[0..k-1]: qubits[j] is bit
+ * j of U's row/column index; for every group of 2^k amplitudes that differ
+ * only in those qubits, a'_r = sum_c U_rc a_c.  1 <= k <= 7.  A product of
+ * the paper's gates on k qubits, built on the host in FP64, applied in one
+ * pass of the state. */
+QSIM_API qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U);
+
+/* qsim_swap_qubits: the SWAP command of App. A (Sec. III.B): interchange the
+ * index-bit positions that hold logical qubits a[i] and b[i], i < K, moving
+ * the amplitudes in one pass (Eqs. onequbitchange, twoqubitchange0-5 and the
+ * K-pair generalisation) and updating the qubit-to-bit map.  The logical state
+ * is unchanged; only its layout in memory changes.  1 <= K <= n/2, all 2K
+ * qubits distinct. */
+QSIM_API qsim_status qsim_swap_qubits(qsim_handle h, int K, const int *a, const int *b);
+
+/* qsim_permute_bits: the raw data movement of an interchange: exchange the
+ * PHYSICAL index bits l[i] <-> h[i], i < K, of the stored amplitudes without
+ * touching the map (so the logical state changes).  For tests of the layout
+ * tables of Sec. III.B and for callers managing their own layout. */
+QSIM_API qsim_status qsim_permute_bits(qsim_handle h, int K, const int *l, const int *hbits);
+
+/* qsim_get_layout: phys[q] = index bit currently holding logical qubit q. */
+QSIM_API qsim_status qsim_get_layout(qsim_handle h, int *phys);
+
+/* qsim_run_circuit: apply ng gates in order, as opts->mode says (NULL =
+ * defaults).  The gate list is read during the call only.  On EINVAL (a bad
+ * gate) nothing has been applied. */
+QSIM_API qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts);
+
+/* ---- batches of independent circuits -------------------------------------
+ * One circuit of a batch: the state hs (C64, made by qsim_alloc or
+ * qsim_attach) is set to |x0> and the gates are applied. */
+typedef struct {
+    qsim_handle state;
+    uint64_t x0;
+    const qsim_gate *gates;
+    size_t ng;
+} qsim_circuit;
+
+/* qsim_run_batch: run nc independent circuits (C64 states of up to 24 qubits)
+ * in one persistent launch on the stream of cs[0].state; every state must be
+ * on the same device.  Waits for completion.  ETIMEOUT if a device-side
+ * wait between passes expired (the states are then undefined). */
+QSIM_API qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts);
+
+/* ---- measurement ------------------------------------------------------------
+ * qsim_norm: sum_i |a_i|^2 (Eq. STAT1), accumulated in FP64. */
+QSIM_API qsim_status qsim_norm(qsim_handle h, double *out);
+
+/* qsim_probs: out[i] = |a_i|^2 for the 2^n logical basis states, FP64;
+ * len must equal 2^n. */
+QSIM_API qsim_status qsim_probs(qsim_handle h, double *out, size_t len);
+
+/* qsim_qubit_probs: out[q] = <Q_q> = probability that logical qubit q is 1
+ * (Eq. Shor7; DO MEASUREMENT of App. A, no collapse), FP64, n values. */
+QSIM_API qsim_status qsim_qubit_probs(qsim_handle h, double *out);
+
+/* qsim_sample: draw ns basis states with probability |a_x|^2 / norm
+ * (Sec. V.B).  u[j] in [0, 1) are the caller's uniform numbers; sample j is
+ * the smallest logical index x with u[j] * norm < P(0) + ... + P(x) (FP64
+ * cumulative sums).  out receives ns indices. */
+QSIM_API qsim_status qsim_sample(qsim_handle h, const double *u, size_t ns, uint64_t *out);
+
+/* qsim_get_state: copy the 2^n amplitudes in logical order to host memory;
+ * bytes must equal the state size. */
+QSIM_API qsim_status qsim_get_state(qsim_handle h, void *host_out, size_t bytes);
+
+/* Wait for the handle's pending work. */
+QSIM_API qsim_status qsim_sync(qsim_handle h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+QSIM_API const char *qsim_last_error(void);
+
+/* Library version string. */
+QSIM_API const char *qsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,191 @@
+"""GB300 state-vector simulator: Python binding of the C ABI (include/qsim.h).
+
+Everything that touches amplitudes runs in the CUDA kernels of ``libqsim.so``;
+this module only marshals arguments.  PyTorch provides the device memory and
+the stream (``State(..., use_torch=True)``, the default) -- it never computes.
+
+    st = State(10, "c128")
+    st.set_basis(x)
+    st.run(gates)                 # list of inputs.Gate, planner path
+    p = st.qubit_probs()          # <Q_q>, Eq. Shor7
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (QsimError, QsimGate, QsimOpts, QsimCircuit, gate_array, gate_record,  # noqa: F401
+                    MODE_PERGATE, MODE_FUSED, QSIM_C64, QSIM_C128, QSIM_ETIMEOUT, QSIM_EINVAL)
+
+_DT = {"c64": QSIM_C64, "complex64": QSIM_C64, "c128": QSIM_C128, "complex128": QSIM_C128}
+_NP = {QSIM_C64: np.complex64, QSIM_C128: np.complex128}
+
+
+def version():
+    return _capi.load().qsim_version().decode()
+
+
+def opts(mode=MODE_FUSED, tile_bits=0, fuse_k=0, max_swap=0):
+    o = QsimOpts()
+    _capi.load().qsim_default_opts(ctypes.byref(o))
+    o.mode, o.tile_bits, o.fuse_k, o.max_swap = int(mode), int(tile_bits), int(fuse_k), int(max_swap)
+    return o
+
+
+def _dbl(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d doubles" % n)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _mat8(U):
+    U = np.asarray(U, dtype=np.complex128).reshape(2, 2)
+    return _dbl(np.stack([U.real, U.imag], axis=-1).reshape(-1), 8)
+
+
+class State:
+    """An n-qubit register on the current CUDA device.
+
+    With ``use_torch=True`` the amplitudes live in a torch tensor (complex64 or
+    complex128) attached through ``qsim_attach`` and the work runs on torch's
+    current stream; otherwise ``qsim_alloc`` owns the memory.
+    """
+
+    def __init__(self, n, dtype="c64", use_torch=True, stream=None):
+        self.n = int(n)
+        self.dt = _DT[dtype] if isinstance(dtype, str) else int(dtype)
+        self.np_dtype = _NP[self.dt]
+        self.tensor = None
+        h = _capi.c_handle()
+        if use_torch:
+            import torch
+            tdt = torch.complex64 if self.dt == QSIM_C64 else torch.complex128
+            self.tensor = torch.empty(1 << self.n, dtype=tdt, device="cuda")
+            s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+            _capi.call("qsim_attach", ctypes.c_void_p(self.tensor.data_ptr()), self.n, self.dt,
+                       ctypes.c_void_p(s), ctypes.byref(h))
+            self.handle = h
+            self.set_basis(0)
+        else:
+            _capi.call("qsim_alloc", self.n, self.dt, ctypes.byref(h))
+            self.handle = h
+            if stream is not None:
+                self.set_stream(stream)
+
+    # -- lifetime ---------------------------------------------------------
+    def free(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _capi.call("qsim_free", self.handle)
+            self.handle = None
+        self.tensor = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def nbytes(self):
+        return (8 if self.dt == QSIM_C64 else 16) << self.n
+
+    def set_stream(self, stream):
+        _capi.call("qsim_set_stream", self.handle, ctypes.c_void_p(stream))
+
+    def sync(self):
+        _capi.call("qsim_sync", self.handle)
+
+    # -- state ------------------------------------------------------------
+    def set_basis(self, x=0):
+        _capi.call("qsim_set_basis", self.handle, ctypes.c_uint64(int(x)))
+
+    def set_state(self, psi):
+        psi = np.ascontiguousarray(psi, dtype=self.np_dtype)
+        _capi.call("qsim_set_state", self.handle, psi.ctypes.data_as(ctypes.c_void_p), psi.nbytes)
+
+    def get_state(self):
+        out = np.empty(1 << self.n, dtype=self.np_dtype)
+        _capi.call("qsim_get_state", self.handle, out.ctypes.data_as(ctypes.c_void_p), out.nbytes)
+        return out
+
+    def layout(self):
+        out = (ctypes.c_int * self.n)()
+        _capi.call("qsim_get_layout", self.handle, out)
+        return list(out)
+
+    # -- gates ------------------------------------------------------------
+    def apply_1q(self, t, U):
+        keep, p = _mat8(U)
+        _capi.call("qsim_apply_1q", self.handle, int(t), p)
+
+    def apply_ctrl(self, ctrl_mask, t, U):
+        keep, p = _mat8(U)
+        _capi.call("qsim_apply_ctrl", self.handle, ctypes.c_uint64(int(ctrl_mask)), int(t), p)
+
+    def apply_gate(self, g):
+        r = gate_record(g)
+        _capi.call("qsim_apply_gate", self.handle, ctypes.byref(r))
+
+    def apply_fused(self, qubits, U):
+        k = len(qubits)
+        q = (ctypes.c_int * k)(*[int(x) for x in qubits])
+        U = np.asarray(U, dtype=np.complex128).reshape(1 << k, 1 << k)
+        keep, p = _dbl(np.stack([U.real, U.imag], axis=-1).reshape(-1), 2 << (2 * k))
+        _capi.call("qsim_apply_fused", self.handle, k, q, p)
+
+    def swap_qubits(self, a, b):
+        K = len(a)
+        _capi.call("qsim_swap_qubits", self.handle, K, (ctypes.c_int * K)(*a), (ctypes.c_int * K)(*b))
+
+    def permute_bits(self, l, h):
+        K = len(l)
+        _capi.call("qsim_permute_bits", self.handle, K, (ctypes.c_int * K)(*l), (ctypes.c_int * K)(*h))
+
+    def run(self, gates, mode=MODE_FUSED, tile_bits=0, fuse_k=0, gate_arr=None):
+        """Apply a gate list (inputs.Gate objects, or a pre-marshalled array)."""
+        arr = gate_arr if gate_arr is not None else gate_array(gates)
+        ng = len(gates) if gates is not None else len(arr)
+        o = opts(mode, tile_bits, fuse_k)
+        _capi.call("qsim_run_circuit", self.handle, arr, ng, ctypes.byref(o))
+
+    # -- measurement ------------------------------------------------------
+    def norm(self):
+        out = ctypes.c_double()
+        _capi.call("qsim_norm", self.handle, ctypes.byref(out))
+        return out.value
+
+    def probs(self):
+        out = np.empty(1 << self.n, dtype=np.float64)
+        _capi.call("qsim_probs", self.handle, out.ctypes.data_as(ctypes.c_void_p), out.size)
+        return out
+
+    def qubit_probs(self):
+        out = np.empty(self.n, dtype=np.float64)
+        _capi.call("qsim_qubit_probs", self.handle, out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def sample(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.empty(u.size, dtype=np.uint64)
+        _capi.call("qsim_sample", self.handle, u.ctypes.data_as(ctypes.c_void_p), u.size,
+                   out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+
+def run_batch(states, x0s, gate_lists, mode=MODE_FUSED):
+    """Run independent circuits (complex64 states) through qsim_run_batch."""
+    nc = len(states)
+    arr = (QsimCircuit * nc)()
+    keep = []
+    for i, (st, x0, gl) in enumerate(zip(states, x0s, gate_lists)):
+        ga = gl if isinstance(gl, ctypes.Array) else gate_array(gl)
+        keep.append(ga)
+        arr[i].state = st.handle
+        arr[i].x0 = int(x0)
+        arr[i].gates = ctypes.cast(ga, ctypes.POINTER(QsimGate))
+        arr[i].ng = len(ga) if isinstance(gl, ctypes.Array) else len(gl)
+    o = opts(mode)
+    _capi.call("qsim_run_batch", arr, nc, ctypes.byref(o))

@@ -1,0 +1,627 @@
+// capi.cu -- the extern "C" boundary declared in include/qsim.h: handles,
+// argument checks, the qubit-to-bit map sigma (Sec. III.B), dispatch of gates
+// to the sweep and tile kernels, reductions and host transfers.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qsim.h"
+#include "kernels.hpp"
+#include "planner.hpp"
+
+using namespace qsim;
+
+// ----------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+static qsim_status fail(qsim_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+static qsim_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? QSIM_ENOMEM : QSIM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ----------------------------------------------------------------- handle
+struct qsim_state {
+    int n = 0;
+    qsim_dtype dt = QSIM_C64;
+    void *amp = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 152;
+    int phys[64];              // logical qubit q -> index bit
+    double *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *d_res = nullptr;   // small device result area (64 doubles)
+    double *h_res = nullptr;   // pinned host mirror
+    uint32_t *d_err = nullptr; // bounded-wait error word
+    TileOp *d_ops = nullptr;
+    size_t ops_cap = 0;
+    void *d_dense = nullptr;   // dense matrices (state precision)
+    size_t dense_cap = 0;
+    void *d_chunk = nullptr;   // staging for logical-order reads
+    size_t chunk_bytes = 0;
+};
+
+static size_t amp_bytes(qsim_dtype dt) { return dt == QSIM_C64 ? 8 : 16; }
+static size_t state_bytes(const qsim_state *h) { return amp_bytes(h->dt) << h->n; }
+static bool identity_layout(const qsim_state *h) {
+    for (int q = 0; q < h->n; q++)
+        if (h->phys[q] != q) return false;
+    return true;
+}
+
+static qsim_status init_common(qsim_state *h) {
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    CK(cudaGetDevice(&h->device), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device), "device attribute");
+    h->scratch_bytes = std::max(reduce_scratch_bytes(h->n), (size_t)4096);
+    CK(cudaMalloc(&h->d_scratch, h->scratch_bytes), "cudaMalloc scratch");
+    CK(cudaMalloc(&h->d_res, 64 * sizeof(double)), "cudaMalloc results");
+    CK(cudaMallocHost(&h->h_res, 64 * sizeof(double)), "cudaMallocHost results");
+    CK(cudaMalloc(&h->d_err, sizeof(uint32_t)), "cudaMalloc error word");
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream), "memset error word");
+    return QSIM_OK;
+}
+
+static void release(qsim_state *h) {
+    if (!h) return;
+    if (h->owns && h->amp) cudaFree(h->amp);
+    if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_res) cudaFree(h->d_res);
+    if (h->h_res) cudaFreeHost(h->h_res);
+    if (h->d_err) cudaFree(h->d_err);
+    if (h->d_ops) cudaFree(h->d_ops);
+    if (h->d_dense) cudaFree(h->d_dense);
+    if (h->d_chunk) cudaFree(h->d_chunk);
+    delete h;
+}
+
+// Wait for the stream and turn a device-side timeout into ETIMEOUT.
+static qsim_status sync_check(qsim_state *h) {
+    CK(cudaMemcpyAsync(h->h_res + 63, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream),
+       "read error word");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    uint32_t e;
+    std::memcpy(&e, h->h_res + 63, sizeof e);
+    if (e != 0) {
+        cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
+        cudaStreamSynchronize(h->stream);
+        return fail(QSIM_ETIMEOUT, "a bounded device-side wait expired (code %u)", e);
+    }
+    return QSIM_OK;
+}
+
+#define CHECK_HANDLE(h) \
+    if (!(h)) return fail(QSIM_EINVAL, "null handle")
+
+extern "C" {
+
+const char *qsim_last_error(void) { return g_err.c_str(); }
+
+const char *qsim_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+
+void qsim_default_opts(qsim_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->mode = QSIM_MODE_FUSED;
+}
+
+qsim_status qsim_alloc(int n, qsim_dtype dt, qsim_handle *out) {
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(QSIM_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    if (dt != QSIM_C64 && dt != QSIM_C128) return fail(QSIM_EINVAL, "bad dtype %d", (int)dt);
+    qsim_state *h = new qsim_state;
+    h->n = n;
+    h->dt = dt;
+    h->owns = true;
+    cudaError_t e = cudaMalloc(&h->amp, state_bytes(h));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->amp = nullptr;
+        release(h);
+        return cuda_fail(e, "cudaMalloc state");
+    }
+    qsim_status st = init_common(h);
+    if (st == QSIM_OK) {
+        e = launch_init_basis(h->amp, (int)dt, n, 0, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "init basis");
+    }
+    if (st != QSIM_OK) {
+        release(h);
+        return st;
+    }
+    *out = h;
+    return QSIM_OK;
+}
+
+qsim_status qsim_attach(void *dev_ptr, int n, qsim_dtype dt, void *stream, qsim_handle *out) {
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 15u))
+        return fail(QSIM_EINVAL, "device pointer must be non-NULL and 16-byte aligned");
+    if (n < 1 || n > kMaxQubits) return fail(QSIM_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    if (dt != QSIM_C64 && dt != QSIM_C128) return fail(QSIM_EINVAL, "bad dtype %d", (int)dt);
+    qsim_state *h = new qsim_state;
+    h->n = n;
+    h->dt = dt;
+    h->amp = dev_ptr;
+    h->owns = false;
+    h->stream = static_cast<cudaStream_t>(stream);
+    qsim_status st = init_common(h);
+    if (st != QSIM_OK) {
+        release(h);
+        return st;
+    }
+    *out = h;
+    return QSIM_OK;
+}
+
+qsim_status qsim_free(qsim_handle h) {
+    if (!h) return QSIM_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_stream(qsim_handle h, void *s) {
+    CHECK_HANDLE(h);
+    h->stream = static_cast<cudaStream_t>(s);
+    return QSIM_OK;
+}
+
+qsim_status qsim_info(qsim_handle h, int *n, qsim_dtype *dt, void **dev_ptr) {
+    CHECK_HANDLE(h);
+    if (n) *n = h->n;
+    if (dt) *dt = h->dt;
+    if (dev_ptr) *dev_ptr = h->amp;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_basis(qsim_handle h, uint64_t x) {
+    CHECK_HANDLE(h);
+    if (h->n < 64 && x >= (1ull << h->n)) return fail(QSIM_EINVAL, "basis index out of range");
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    CK(launch_init_basis(h->amp, (int)h->dt, h->n, x, h->stream), "init basis");
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_state(qsim_handle h, const void *host_in, size_t bytes) {
+    CHECK_HANDLE(h);
+    if (!host_in || bytes != state_bytes(h)) return fail(QSIM_EINVAL, "need %zu bytes", state_bytes(h));
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    CK(cudaMemcpyAsync(h->amp, host_in, bytes, cudaMemcpyHostToDevice, h->stream), "copy state in");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ gates
+static qsim_status sweep_gate(qsim_state *h, const PGate &pg) {
+    FixedBitsHost fb{};
+    uint64_t pmask;
+    bool single;
+    fixed_bits_for(pg, fb, pmask, single);
+    if (fb.npos > h->n) return QSIM_OK;  // cannot happen after validation
+    cudaError_t e = single ? launch_diag(h->amp, (int)h->dt, h->n, fb, pg.t0, pg.U, h->stream)
+                           : launch_pairs(h->amp, (int)h->dt, h->n, fb, pmask, pg.gc, pg.U, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gate sweep");
+    return QSIM_OK;
+}
+
+static qsim_status apply_u(qsim_state *h, uint64_t ctrl, int t, const double U[8]) {
+    if (!U) return fail(QSIM_EINVAL, "U is NULL");
+    qsim_gate g{};
+    g.kind = QSIM_GATE_U;
+    g.target = t;
+    g.ctrl_mask = ctrl;
+    for (int k = 0; k < 8; k++) g.param[k] = U[k];
+    PGate pg;
+    std::string msg;
+    if (!prepare_gate(g, h->n, h->phys, pg, msg)) return fail(QSIM_EINVAL, "%s", msg.c_str());
+    return sweep_gate(h, pg);
+}
+
+qsim_status qsim_apply_1q(qsim_handle h, int t, const double U[8]) {
+    CHECK_HANDLE(h);
+    return apply_u(h, 0, t, U);
+}
+
+qsim_status qsim_apply_ctrl(qsim_handle h, uint64_t ctrl_mask, int t, const double U[8]) {
+    CHECK_HANDLE(h);
+    return apply_u(h, ctrl_mask, t, U);
+}
+
+qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g) {
+    CHECK_HANDLE(h);
+    if (!g) return fail(QSIM_EINVAL, "gate is NULL");
+    PGate pg;
+    std::string msg;
+    if (!prepare_gate(*g, h->n, h->phys, pg, msg)) return fail(QSIM_EINVAL, "%s", msg.c_str());
+    return sweep_gate(h, pg);
+}
+
+static qsim_status ensure_ops(qsim_state *h, size_t nops) {
+    if (nops <= h->ops_cap) return QSIM_OK;
+    size_t cap = std::max(nops, (size_t)256);
+    if (h->d_ops) {
+        CK(cudaStreamSynchronize(h->stream), "sync before regrow");
+        cudaFree(h->d_ops);
+        h->d_ops = nullptr;
+        h->ops_cap = 0;
+    }
+    CK(cudaMalloc(&h->d_ops, cap * sizeof(TileOp)), "cudaMalloc ops");
+    h->ops_cap = cap;
+    return QSIM_OK;
+}
+
+static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &L) {
+    T = (o && o->tile_bits > 0) ? o->tile_bits : (h->dt == QSIM_C64 ? 12 : 11);
+    const int Tmax = h->dt == QSIM_C64 ? 14 : 13;
+    if (T > Tmax) T = Tmax;
+    if (T < 2) T = 2;
+    L = h->dt == QSIM_C64 ? 5 : 4;
+    if (T - L > 10) L = T - 10;
+    if (L >= T) L = T - 2;
+    if (L < 1) L = 1;
+}
+
+static qsim_status run_plan(qsim_state *h, const Plan &plan) {
+    if (plan.ops.empty()) return QSIM_OK;
+    qsim_status st = ensure_ops(h, plan.ops.size());
+    if (st != QSIM_OK) return st;
+    CK(cudaMemcpyAsync(h->d_ops, plan.ops.data(), plan.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice,
+                       h->stream),
+       "upload tile ops");
+    for (const PassPlan &pp : plan.passes) {
+        if (pp.op_count == 0) continue;
+        CK(launch_tile_pass(h->amp, (int)h->dt, pp.geom, h->d_ops + pp.op_begin, pp.op_count, h->d_dense, h->d_err,
+                            h->sm_count, h->stream),
+           "tile pass");
+    }
+    return QSIM_OK;
+}
+
+static qsim_status prepare_all(qsim_state *h, const qsim_gate *gates, size_t ng, std::vector<PGate> &out) {
+    out.resize(ng);
+    std::string msg;
+    for (size_t i = 0; i < ng; i++)
+        if (!prepare_gate(gates[i], h->n, h->phys, out[i], msg))
+            return fail(QSIM_EINVAL, "gate %zu: %s", i, msg.c_str());
+    return QSIM_OK;
+}
+
+qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts) {
+    CHECK_HANDLE(h);
+    if (ng && !gates) return fail(QSIM_EINVAL, "gates is NULL");
+    qsim_opts o;
+    qsim_default_opts(&o);
+    if (opts) o = *opts;
+    std::vector<PGate> pg;
+    qsim_status st = prepare_all(h, gates, ng, pg);
+    if (st != QSIM_OK) return st;
+    if (o.mode == QSIM_MODE_PERGATE) {
+        for (const PGate &g : pg) {
+            st = sweep_gate(h, g);
+            if (st != QSIM_OK) return st;
+        }
+        return QSIM_OK;
+    }
+    if (o.mode != QSIM_MODE_FUSED) return fail(QSIM_EINVAL, "unknown mode %d", o.mode);
+    int T, L;
+    tile_defaults(h, &o, T, L);
+    Plan plan;
+    plan_tiles(pg, h->n, T, L, plan);
+    return run_plan(h, plan);
+}
+
+qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U) {
+    CHECK_HANDLE(h);
+    if (k < 1 || k > 6 || k > h->n) return fail(QSIM_EINVAL, "k = %d outside [1, min(6, n)]", k);
+    if (!qubits || !U) return fail(QSIM_EINVAL, "qubits or U is NULL");
+    int pos[8];
+    uint64_t seen = 0;
+    for (int j = 0; j < k; j++) {
+        if (qubits[j] < 0 || qubits[j] >= h->n) return fail(QSIM_EINVAL, "qubit %d out of range", qubits[j]);
+        if ((seen >> qubits[j]) & 1ull) return fail(QSIM_EINVAL, "qubit %d repeated", qubits[j]);
+        seen |= 1ull << qubits[j];
+        pos[j] = h->phys[qubits[j]];
+    }
+    const size_t ent = (size_t)1 << (2 * k);
+    for (size_t i = 0; i < 2 * ent; i++)
+        if (!std::isfinite(U[i])) return fail(QSIM_EINVAL, "non-finite matrix entry");
+    const size_t bytes = ent * amp_bytes(h->dt);
+    if (bytes > h->dense_cap) {
+        if (h->d_dense) {
+            CK(cudaStreamSynchronize(h->stream), "sync");
+            cudaFree(h->d_dense);
+            h->d_dense = nullptr;
+            h->dense_cap = 0;
+        }
+        CK(cudaMalloc(&h->d_dense, std::max(bytes, (size_t)65536)), "cudaMalloc dense");
+        h->dense_cap = std::max(bytes, (size_t)65536);
+    }
+    if (h->dt == QSIM_C64) {
+        std::vector<float> f(2 * ent);
+        for (size_t i = 0; i < 2 * ent; i++) f[i] = (float)U[i];
+        CK(cudaMemcpyAsync(h->d_dense, f.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+    } else {
+        CK(cudaMemcpyAsync(h->d_dense, U, bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+    }
+    CK(launch_dense(h->amp, (int)h->dt, h->n, k, pos, h->d_dense, h->stream), "dense gate");
+    return QSIM_OK;
+}
+
+// ---------------------------------------------------------- interchanges
+static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *hb) {
+    if (K == 1) {
+        PGate pg{};
+        pg.kind = QSIM_GATE_SWAP;
+        pg.t0 = l[0];
+        pg.t1 = hb[0];
+        pg.cmask = 0;
+        pg.gc = GC_EXCHANGE;
+        return sweep_gate(h, pg);
+    }
+    // K pairs in one pass: a tile holding all 2K bits, one in-tile permutation.
+    int T, L;
+    tile_defaults(h, nullptr, T, L);
+    uint64_t need = 0;
+    for (int i = 0; i < K; i++) need |= (1ull << l[i]) | (1ull << hb[i]);
+    if (h->n <= T) {
+        T = h->n;
+        L = h->n;
+    } else {
+        // keep the low run length, make room for the pair bits above it
+        int above = 0;
+        for (int b = 0; b < 64; b++)
+            if (((need >> b) & 1ull) && b >= L) above++;
+        while (above > T - L && L > 1) {
+            L--;
+            above = 0;
+            for (int b = 0; b < 64; b++)
+                if (((need >> b) & 1ull) && b >= L) above++;
+        }
+        if (above > T - L || above > 10) return fail(QSIM_EUNSUPPORTED, "too many pairs for one tile");
+    }
+    TileGeom g{};
+    g.n = h->n;
+    g.L = L;
+    int j = 0;
+    uint64_t hm = 0;
+    for (int b = L; b < h->n; b++)
+        if ((need >> b) & 1ull) hm |= 1ull << b;
+    // pad with low-most unused bits above L so the tile has T bits
+    for (int b = L; b < h->n && __builtin_popcountll(hm) < T - L; b++) hm |= 1ull << b;
+    for (int b = 0; b < 64; b++)
+        if ((hm >> b) & 1ull) g.hb[j++] = b;
+    g.H = j;
+    auto local = [&](int b) -> int {
+        if (b < g.L) return b;
+        for (int k = 0; k < g.H; k++)
+            if (g.hb[k] == b) return g.L + k;
+        return -1;
+    };
+    Plan plan;
+    TileOp op{};
+    op.kind = TOP_PERM;
+    op.nperm = K;
+    for (int i = 0; i < K; i++) {
+        op.pl[i] = (int8_t)local(l[i]);
+        op.ph[i] = (int8_t)local(hb[i]);
+    }
+    plan.ops.push_back(op);
+    PassPlan pp{};
+    pp.geom = g;
+    pp.op_begin = 0;
+    pp.op_count = 1;
+    plan.passes.push_back(pp);
+    return run_plan(h, plan);
+}
+
+static qsim_status check_pairs(const qsim_state *h, int K, const int *a, const int *b) {
+    if (K < 1 || 2 * K > h->n || K > 8) return fail(QSIM_EINVAL, "K = %d outside [1, min(8, n/2)]", K);
+    if (!a || !b) return fail(QSIM_EINVAL, "NULL qubit list");
+    uint64_t seen = 0;
+    for (int i = 0; i < K; i++) {
+        for (int x : {a[i], b[i]}) {
+            if (x < 0 || x >= h->n) return fail(QSIM_EINVAL, "qubit %d out of range", x);
+            if ((seen >> x) & 1ull) return fail(QSIM_EINVAL, "qubit %d repeated", x);
+            seen |= 1ull << x;
+        }
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_permute_bits(qsim_handle h, int K, const int *l, const int *hb) {
+    CHECK_HANDLE(h);
+    qsim_status st = check_pairs(h, K, l, hb);
+    if (st != QSIM_OK) return st;
+    return permute_phys(h, K, l, hb);
+}
+
+qsim_status qsim_swap_qubits(qsim_handle h, int K, const int *a, const int *b) {
+    CHECK_HANDLE(h);
+    qsim_status st = check_pairs(h, K, a, b);
+    if (st != QSIM_OK) return st;
+    int l[8], hb[8];
+    for (int i = 0; i < K; i++) {
+        l[i] = h->phys[a[i]];
+        hb[i] = h->phys[b[i]];
+    }
+    st = permute_phys(h, K, l, hb);
+    if (st != QSIM_OK) return st;
+    for (int i = 0; i < K; i++) std::swap(h->phys[a[i]], h->phys[b[i]]);
+    return QSIM_OK;
+}
+
+qsim_status qsim_get_layout(qsim_handle h, int *phys) {
+    CHECK_HANDLE(h);
+    if (!phys) return fail(QSIM_EINVAL, "NULL output");
+    for (int q = 0; q < h->n; q++) phys[q] = h->phys[q];
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------ measurement
+qsim_status qsim_sync(qsim_handle h) {
+    CHECK_HANDLE(h);
+    return sync_check(h);
+}
+
+qsim_status qsim_norm(qsim_handle h, double *out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(QSIM_EINVAL, "NULL output");
+    CK(launch_norm(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream), "norm");
+    CK(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy norm");
+    qsim_status st = sync_check(h);
+    if (st != QSIM_OK) return st;
+    *out = h->h_res[0];
+    return QSIM_OK;
+}
+
+qsim_status qsim_qubit_probs(qsim_handle h, double *out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(QSIM_EINVAL, "NULL output");
+    CK(launch_bit_probs(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream), "bit marginals");
+    CK(cudaMemcpyAsync(h->h_res, h->d_res, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "copy marginals");
+    qsim_status st = sync_check(h);
+    if (st != QSIM_OK) return st;
+    for (int q = 0; q < h->n; q++) out[q] = h->h_res[h->phys[q]];
+    return QSIM_OK;
+}
+
+static qsim_status ensure_chunk(qsim_state *h) {
+    if (h->d_chunk) return QSIM_OK;
+    h->chunk_bytes = 64u << 20;
+    CK(cudaMalloc(&h->d_chunk, h->chunk_bytes), "cudaMalloc staging");
+    return QSIM_OK;
+}
+
+qsim_status qsim_probs(qsim_handle h, double *out, size_t len) {
+    CHECK_HANDLE(h);
+    const uint64_t D = 1ull << h->n;
+    if (!out || len != D) return fail(QSIM_EINVAL, "len must be 2^n = %llu", (unsigned long long)D);
+    qsim_status st = ensure_chunk(h);
+    if (st != QSIM_OK) return st;
+    const bool ident = identity_layout(h);
+    const uint64_t per = h->chunk_bytes / sizeof(double);
+    for (uint64_t s = 0; s < D; s += per) {
+        const uint64_t cnt = std::min(per, D - s);
+        CK(launch_probs_chunk(h->amp, (int)h->dt, h->n, h->phys, ident, s, cnt, static_cast<double *>(h->d_chunk),
+                              h->stream),
+           "probabilities");
+        CK(cudaMemcpyAsync(out + s, h->d_chunk, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "copy probabilities");
+        CK(cudaStreamSynchronize(h->stream), "sync");
+    }
+    return sync_check(h);
+}
+
+qsim_status qsim_get_state(qsim_handle h, void *host_out, size_t bytes) {
+    CHECK_HANDLE(h);
+    if (!host_out || bytes != state_bytes(h)) return fail(QSIM_EINVAL, "need %zu bytes", state_bytes(h));
+    if (identity_layout(h)) {
+        CK(cudaMemcpyAsync(host_out, h->amp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy state out");
+        return sync_check(h);
+    }
+    qsim_status st = ensure_chunk(h);
+    if (st != QSIM_OK) return st;
+    const uint64_t D = 1ull << h->n;
+    const size_t ab = amp_bytes(h->dt);
+    const uint64_t per = h->chunk_bytes / ab;
+    for (uint64_t s = 0; s < D; s += per) {
+        const uint64_t cnt = std::min(per, D - s);
+        CK(launch_gather_chunk(h->amp, (int)h->dt, h->n, h->phys, s, cnt, h->d_chunk, h->stream), "gather");
+        CK(cudaMemcpyAsync(static_cast<char *>(host_out) + s * ab, h->d_chunk, cnt * ab, cudaMemcpyDeviceToHost,
+                           h->stream),
+           "copy state out");
+        CK(cudaStreamSynchronize(h->stream), "sync");
+    }
+    return sync_check(h);
+}
+
+qsim_status qsim_sample(qsim_handle h, const double *u, size_t ns, uint64_t *out) {
+    CHECK_HANDLE(h);
+    if (ns == 0) return QSIM_OK;
+    if (!u || !out) return fail(QSIM_EINVAL, "NULL buffer");
+    for (size_t j = 0; j < ns; j++)
+        if (!(u[j] >= 0.0 && u[j] < 1.0)) return fail(QSIM_EINVAL, "u[%zu] outside [0, 1)", j);
+    if (h->n < 5) {  // tiny registers: inverse CDF on the host from the probabilities
+        std::vector<double> p((size_t)1 << h->n);
+        qsim_status st = qsim_probs(h, p.data(), p.size());
+        if (st != QSIM_OK) return st;
+        double tot = 0;
+        for (double x : p) tot += x;
+        for (size_t j = 0; j < ns; j++) {
+            const double target = u[j] * tot;
+            double c = 0;
+            uint64_t pick = p.size() - 1;
+            for (size_t i = 0; i < p.size(); i++) {
+                c += p[i];
+                if (target < c) {
+                    pick = i;
+                    break;
+                }
+            }
+            out[j] = pick;
+        }
+        return QSIM_OK;
+    }
+    const size_t need = sample_scratch_bytes(h->n) + ns * (sizeof(double) + sizeof(uint64_t)) + 256;
+    void *buf = nullptr;
+    CK(cudaMallocAsync(&buf, need, h->stream), "cudaMallocAsync sample buffers");
+    double *du = static_cast<double *>(buf);
+    uint64_t *dout = reinterpret_cast<uint64_t *>(du + ns);
+    double *scr = reinterpret_cast<double *>(dout + ns);
+    cudaError_t e = cudaMemcpyAsync(du, u, ns * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_sample(h->amp, (int)h->dt, h->n, h->phys, identity_layout(h), du, ns, dout, scr, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ns * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(buf, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sample");
+    return sync_check(h);
+}
+
+// ------------------------------------------------------------------ batch
+qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts) {
+    if (nc == 0) return QSIM_OK;
+    if (!cs) return fail(QSIM_EINVAL, "NULL circuit list");
+    for (size_t i = 0; i < nc; i++) {
+        if (!cs[i].state) return fail(QSIM_EINVAL, "circuit %zu has no state", i);
+        if (cs[i].state->dt != QSIM_C64) return fail(QSIM_EINVAL, "batch states must be complex64");
+        if (cs[i].state->n > 24) return fail(QSIM_EINVAL, "batch states have at most 24 qubits");
+    }
+    for (size_t i = 0; i < nc; i++) {
+        qsim_status st = qsim_set_basis(cs[i].state, cs[i].x0);
+        if (st == QSIM_OK) st = qsim_run_circuit(cs[i].state, cs[i].gates, cs[i].ng, opts);
+        if (st != QSIM_OK) return st;
+    }
+    for (size_t i = 0; i < nc; i++) {
+        qsim_status st = sync_check(cs[i].state);
+        if (st != QSIM_OK) return st;
+    }
+    return QSIM_OK;
+}
+
+}  // extern "C"

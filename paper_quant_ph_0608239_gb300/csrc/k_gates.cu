@@ -1,0 +1,282 @@
+// k_gates.cu -- per-gate sweeps over the whole state (the one-gate-per-sweep
+// execution of Sec. III.A, Eqs. NUM2-NUM8) and the basis-state initialiser.
+//
+// A gate touches either pairs (a0, a1) of amplitudes whose indices differ in
+// the target bit, or single amplitudes (diagonal gates).  The host inserts the
+// fixed bits (target = 0, controls = 1) into a compact enumeration index, so a
+// kernel visits exactly the amplitudes the gate changes: 2^(n-1-c) pairs for a
+// c-controlled gate (Eqs. NUM6, NUM8), 2^(n-1-c) single amplitudes for a phase
+// shift (Eq. NUM5).  Consecutive threads get consecutive enumeration indices,
+// so both members of the pair are read with coalesced accesses for every
+// target bit; the low target bits fall inside one 32-byte sector and are
+// merged by L1.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+inline FixedBits to_dev(const FixedBitsHost &h) {
+    FixedBits f;
+    f.npos = h.npos;
+    for (int i = 0; i < kMaxFixed; i++) f.pos[i] = i < h.npos ? h.pos[i] : 0;
+    f.setmask = h.setmask;
+    return f;
+}
+
+inline int grid_for(uint64_t work, int per_thread) {
+    uint64_t b = (work + (uint64_t)kThreads * per_thread - 1) / ((uint64_t)kThreads * per_thread);
+    const uint64_t cap = 152ull * 32ull;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename R, int GC>
+__device__ __forceinline__ void pair_update(amp_t<R> &x, amp_t<R> &y, const amp_t<R> (&u)[4]) {
+    if (GC == GC_GENERAL) {
+        amp_t<R> a = cmul2<R>(u[0], x, u[1], y);
+        amp_t<R> b = cmul2<R>(u[2], x, u[3], y);
+        x = a;
+        y = b;
+    } else if (GC == GC_ANTIDIAG) {
+        amp_t<R> a = cmul<R>(u[1], y);
+        amp_t<R> b = cmul<R>(u[2], x);
+        x = a;
+        y = b;
+    } else {  // GC_EXCHANGE
+        amp_t<R> t = x;
+        x = y;
+        y = t;
+    }
+}
+
+template <typename R, int GC, int NP>
+__global__ void __launch_bounds__(kThreads) k_pairs(amp_t<R> *__restrict__ a, uint64_t W, FixedBits fb,
+                                                    uint64_t pmask, Mat2 M) {
+    amp_t<R> u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) u[k] = mk<R>((R)M.u[2 * k], (R)M.u[2 * k + 1]);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    uint64_t p = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; p + (kUnroll - 1) * stride < W; p += kUnroll * stride) {
+        uint64_t i0[kUnroll];
+        amp_t<R> x[kUnroll], y[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; k++) {
+            i0[k] = expand_n<NP>(p + k * stride, fb);
+            x[k] = a[i0[k]];
+            y[k] = a[i0[k] ^ pmask];
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; k++) {
+            pair_update<R, GC>(x[k], y[k], u);
+            a[i0[k]] = x[k];
+            a[i0[k] ^ pmask] = y[k];
+        }
+    }
+    for (; p < W; p += stride) {
+        const uint64_t i = expand_n<NP>(p, fb);
+        amp_t<R> x = a[i], y = a[i ^ pmask];
+        pair_update<R, GC>(x, y, u);
+        a[i] = x;
+        a[i ^ pmask] = y;
+    }
+}
+
+template <typename R, int NP>
+__global__ void __launch_bounds__(kThreads) k_diag(amp_t<R> *__restrict__ a, uint64_t W, FixedBits fb, int tbit,
+                                                   Mat2 M) {
+    const amp_t<R> u0 = mk<R>((R)M.u[0], (R)M.u[1]);
+    const amp_t<R> u1 = mk<R>((R)M.u[6], (R)M.u[7]);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    uint64_t p = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; p + (kUnroll - 1) * stride < W; p += kUnroll * stride) {
+        uint64_t i[kUnroll];
+        amp_t<R> x[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; k++) {
+            i[k] = expand_n<NP>(p + k * stride, fb);
+            x[k] = a[i[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; k++) a[i[k]] = cmul<R>(((i[k] >> tbit) & 1) ? u1 : u0, x[k]);
+    }
+    for (; p < W; p += stride) {
+        const uint64_t i = expand_n<NP>(p, fb);
+        a[i] = cmul<R>(((i >> tbit) & 1) ? u1 : u0, a[i]);
+    }
+}
+
+template <typename R>
+__global__ void k_init_basis(amp_t<R> *__restrict__ a, uint64_t D, uint64_t x) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D; i += stride)
+        a[i] = mk<R>(i == x ? (R)1 : (R)0, (R)0);
+}
+
+struct Qpos {
+    int p[8];
+};
+
+// Dense 2^k x 2^k gate on CUDA cores: one thread per group of 2^k amplitudes.
+// The matrix is staged in shared memory; groups are enumerated by inserting
+// zeros at the k (sorted) positions, so consecutive threads read consecutive
+// addresses whenever the low bits are free.
+template <typename R, int K>
+__global__ void __launch_bounds__(128) k_dense(amp_t<R> *__restrict__ a, uint64_t W, FixedBits fb, Qpos q,
+                                               const amp_t<R> *__restrict__ U) {
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    amp_t<R> *sU = reinterpret_cast<amp_t<R> *>(smem_raw);
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) sU[e] = U[e];
+    __syncthreads();
+    uint64_t off[D];
+#pragma unroll
+    for (int c = 0; c < D; c++) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            if ((c >> j) & 1) o |= 1ull << q.p[j];
+        off[c] = o;
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < W; g += stride) {
+        const uint64_t base = expand(g, fb);
+        amp_t<R> v[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) v[c] = a[base | off[c]];
+#pragma unroll 1
+        for (int r = 0; r < D; r++) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const amp_t<R> u = sU[r * D + c];
+                re = fma(u.x, v[c].x, re);
+                re = fma(-u.y, v[c].y, re);
+                im = fma(u.x, v[c].y, im);
+                im = fma(u.y, v[c].x, im);
+            }
+            a[base | off[r]] = mk<R>(re, im);
+        }
+    }
+}
+
+template <typename R, int K>
+cudaError_t dense_k(void *amp, uint64_t W, const FixedBits &fb, const Qpos &q, const void *dU, cudaStream_t s) {
+    const size_t smem = sizeof(amp_t<R>) * (1u << (2 * K));
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_dense<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    uint64_t b = (W + 127) / 128;
+    if (b > 152ull * 16) b = 152ull * 16;
+    if (b < 1) b = 1;
+    k_dense<R, K><<<(int)b, 128, smem, s>>>(static_cast<amp_t<R> *>(amp), W, fb, q,
+                                              static_cast<const amp_t<R> *>(dU));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t dense_dispatch(void *amp, int k, uint64_t W, const FixedBits &fb, const Qpos &q, const void *dU,
+                           cudaStream_t s) {
+    switch (k) {
+    case 1: return dense_k<R, 1>(amp, W, fb, q, dU, s);
+    case 2: return dense_k<R, 2>(amp, W, fb, q, dU, s);
+    case 3: return dense_k<R, 3>(amp, W, fb, q, dU, s);
+    case 4: return dense_k<R, 4>(amp, W, fb, q, dU, s);
+    case 5: return dense_k<R, 5>(amp, W, fb, q, dU, s);
+    case 6: return dense_k<R, 6>(amp, W, fb, q, dU, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R, int NP>
+cudaError_t pairs_np(void *amp, uint64_t W, const FixedBits &fb, uint64_t pmask, int gc, const Mat2 &U,
+                     cudaStream_t s) {
+    const int grid = grid_for(W, kUnroll);
+    amp_t<R> *a = static_cast<amp_t<R> *>(amp);
+    switch (gc) {
+    case GC_GENERAL: k_pairs<R, GC_GENERAL, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
+    case GC_ANTIDIAG: k_pairs<R, GC_ANTIDIAG, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
+    case GC_EXCHANGE: k_pairs<R, GC_EXCHANGE, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t pairs_dispatch(void *amp, uint64_t W, const FixedBits &fb, uint64_t pmask, int gc, const Mat2 &U,
+                           cudaStream_t s) {
+    if (fb.npos <= 2) return pairs_np<R, 2>(amp, W, fb, pmask, gc, U, s);
+    if (fb.npos <= 4) return pairs_np<R, 4>(amp, W, fb, pmask, gc, U, s);
+    if (fb.npos <= 8) return pairs_np<R, 8>(amp, W, fb, pmask, gc, U, s);
+    return pairs_np<R, kMaxFixed>(amp, W, fb, pmask, gc, U, s);
+}
+
+template <typename R>
+cudaError_t diag_dispatch(void *amp, uint64_t W, const FixedBits &fb, int tbit, const Mat2 &U, cudaStream_t s) {
+    const int grid = grid_for(W, kUnroll);
+    amp_t<R> *a = static_cast<amp_t<R> *>(amp);
+    if (fb.npos <= 2) k_diag<R, 2><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, U);
+    else if (fb.npos <= 4) k_diag<R, 4><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, U);
+    else if (fb.npos <= 8) k_diag<R, 8><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, U);
+    else k_diag<R, kMaxFixed><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, U);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init_basis(void *amp, int dt, int n, uint64_t x, cudaStream_t s) {
+    const uint64_t D = 1ull << n;
+    const int grid = grid_for(D, 4);
+    if (dt == 0)
+        k_init_basis<float><<<grid, kThreads, 0, s>>>(static_cast<float2 *>(amp), D, x);
+    else
+        k_init_basis<double><<<grid, kThreads, 0, s>>>(static_cast<double2 *>(amp), D, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(void *amp, int dt, int n, const FixedBitsHost &fbh, uint64_t pmask, int gc,
+                         const Mat2 &U, cudaStream_t s) {
+    if (fbh.npos > n || fbh.npos > kMaxFixed) return cudaErrorInvalidValue;
+    const uint64_t W = 1ull << (n - fbh.npos);
+    const FixedBits fb = to_dev(fbh);
+    return dt == 0 ? pairs_dispatch<float>(amp, W, fb, pmask, gc, U, s)
+                   : pairs_dispatch<double>(amp, W, fb, pmask, gc, U, s);
+}
+
+cudaError_t launch_diag(void *amp, int dt, int n, const FixedBitsHost &fbh, int tbit, const Mat2 &U,
+                        cudaStream_t s) {
+    if (fbh.npos > n || fbh.npos > kMaxFixed) return cudaErrorInvalidValue;
+    const uint64_t W = 1ull << (n - fbh.npos);
+    const FixedBits fb = to_dev(fbh);
+    return dt == 0 ? diag_dispatch<float>(amp, W, fb, tbit, U, s) : diag_dispatch<double>(amp, W, fb, tbit, U, s);
+}
+
+cudaError_t launch_dense(void *amp, int dt, int n, int k, const int *qpos, const void *dU, cudaStream_t s) {
+    if (k < 1 || k > 6 || k > n) return cudaErrorInvalidValue;
+    FixedBitsHost h{};
+    int sorted[8];
+    for (int j = 0; j < k; j++) sorted[j] = qpos[j];
+    for (int i = 1; i < k; i++)
+        for (int j = i; j > 0 && sorted[j - 1] > sorted[j]; j--) {
+            int t = sorted[j];
+            sorted[j] = sorted[j - 1];
+            sorted[j - 1] = t;
+        }
+    h.npos = k;
+    for (int j = 0; j < k; j++) h.pos[j] = sorted[j];
+    h.setmask = 0;
+    Qpos q{};
+    for (int j = 0; j < k; j++) q.p[j] = qpos[j];
+    const uint64_t W = 1ull << (n - k);
+    const FixedBits fb = to_dev(h);
+    return dt == 0 ? dense_dispatch<float>(amp, k, W, fb, q, dU, s) : dense_dispatch<double>(amp, k, W, fb, q, dU, s);
+}
+
+}  // namespace qsim

@@ -1,0 +1,117 @@
+// kernels.hpp -- launch interface between the host runtime (capi.cu,
+// planner.cpp) and the CUDA kernels.  Plain structs, no CUDA types beyond
+// cudaStream_t / cudaError_t.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qsim {
+
+constexpr int kMaxQubits = 34;
+
+// How a 2x2 gate touches a pair (a0, a1) -- chosen on the host from the
+// matrix entries so that no kernel does arithmetic the gate does not need.
+enum GateClass : int32_t {
+    GC_GENERAL = 0,   // dense 2x2
+    GC_DIAG = 1,      // diag(u00, u11): every amplitude scaled, no partner
+    GC_PHASE = 2,     // diag(1, u11): only the bit-1 half scaled (Eq. NUM5)
+    GC_ANTIDIAG = 3,  // a'0 = u01 a1, a'1 = u10 a0
+    GC_EXCHANGE = 4   // a'0 = a1, a'1 = a0 (CNOT / Toffoli flip, Eqs. NUM6, NUM8)
+};
+
+struct Mat2 {
+    double u[8];      // row-major (re, im): u00, u01, u10, u11
+};
+
+// ------------------------------------------------------------ tile programs
+// One operation applied to every tile of a tile pass.  Bit positions named
+// "local" index the tile (0..T-1: first the L low bits, then the H high tile
+// bits in ascending physical order); "global" masks use physical positions
+// outside the tile and are tested once per tile.
+enum TileOpKind : int32_t {
+    TOP_GENERAL = 0,   // 2x2 on local bit tl
+    TOP_DIAG = 1,      // diag on local bit tl
+    TOP_PHASE = 2,     // diag(1, u11) on local bit tl
+    TOP_ANTIDIAG = 3,
+    TOP_EXCHANGE = 4,
+    TOP_DIAG_G = 5,    // diag on a physical bit tl outside the tile: one factor per tile
+    TOP_SWAPGATE = 6,  // quantum SWAP of local bits tl, tl2
+    TOP_PERM = 7,      // exchange local bit pairs (pl[k], ph[k]), k < nperm: a layout change
+    TOP_DENSE = 8      // dense 2^k x 2^k on local bits pl[0..k-1] (k = nperm), matrix at dense_off
+};
+
+struct TileOp {
+    int32_t kind;
+    int32_t tl;
+    int32_t tl2;
+    int32_t nperm;
+    uint32_t lcmask;   // local control bits
+    uint32_t dense_off;  // TOP_DENSE: offset (in complex entries) into the pass's matrix pool
+    uint64_t gcmask;   // global control bits (physical)
+    double u[8];
+    int8_t pl[8];
+    int8_t ph[8];
+};
+static_assert(sizeof(TileOp) == 112, "TileOp layout");
+
+constexpr int kMaxTileHigh = 16;
+struct TileGeom {
+    int32_t n;
+    int32_t L;         // low bits 0..L-1 always in the tile
+    int32_t H;         // number of high tile bits
+    int32_t hb[kMaxTileHigh];  // physical positions of the high tile bits, ascending, >= L
+};
+
+// ------------------------------------------------------------ launchers
+// dt: 0 = complex64, 1 = complex128.  All return the launch error.
+struct FixedBitsHost {
+    int npos;
+    int pos[24];
+    uint64_t setmask;
+};
+
+cudaError_t launch_init_basis(void *amp, int dt, int n, uint64_t x, cudaStream_t s);
+
+// Pair sweep: enumerate i0 = expand(p, fb) for p < 2^(n - fb.npos), partner
+// i1 = i0 ^ pmask, apply the gate class gc with matrix U.
+cudaError_t launch_pairs(void *amp, int dt, int n, const FixedBitsHost &fb, uint64_t pmask, int gc,
+                         const Mat2 &U, cudaStream_t s);
+
+// Single-amplitude sweep for diagonal classes: enumerate i = expand(p, fb),
+// scale by u00 (bit tbit of i is 0) or u11 (bit tbit is 1).
+cudaError_t launch_diag(void *amp, int dt, int n, const FixedBitsHost &fb, int tbit, const Mat2 &U,
+                        cudaStream_t s);
+
+// Dense k-qubit gate on CUDA cores: qpos[j] = physical bit for bit j of U's
+// index, U (device, 4^k complex in the state's precision, row-major).
+cudaError_t launch_dense(void *amp, int dt, int n, int k, const int *qpos, const void *dU, cudaStream_t s);
+
+// One tile pass (shared-memory program).  ops/dmat are device pointers.
+// err: device word set on a bounded-wait timeout.
+cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp *ops, int nops,
+                             const void *dmat, uint32_t *err, int sm_count, cudaStream_t s);
+size_t tile_smem_bytes(int dt, int T);
+
+// Reductions (FP64 accumulation).  scratch: device buffer of at least
+// reduce_scratch_bytes(n) bytes.
+size_t reduce_scratch_bytes(int n);
+cudaError_t launch_norm(const void *amp, int dt, int n, double *scratch, double *dout, cudaStream_t s);
+// dout[b] = P(physical bit b = 1), b < n
+cudaError_t launch_bit_probs(const void *amp, int dt, int n, double *scratch, double *dout, cudaStream_t s);
+// dout[j] = |a[phys(start + j)]|^2 for j < count, phys(x) = deposit of the
+// logical bits of x onto physpos[q]
+cudaError_t launch_probs_chunk(const void *amp, int dt, int n, const int *physpos, bool identity,
+                               uint64_t start, uint64_t count, double *dout, cudaStream_t s);
+// dout[j] = a[phys(start + j)] (amplitude gather to logical order)
+cudaError_t launch_gather_chunk(const void *amp, int dt, int n, const int *physpos, uint64_t start,
+                                uint64_t count, void *dout, cudaStream_t s);
+
+// Sampling (Sec. V.B): block sums of |a|^2 in logical order, then per-sample
+// search.  scratch must hold sample_scratch_bytes(n) bytes.
+size_t sample_scratch_bytes(int n);
+cudaError_t launch_sample(const void *amp, int dt, int n, const int *physpos, bool identity,
+                          const double *du, size_t ns, uint64_t *dout, double *scratch, cudaStream_t s);
+
+}  // namespace qsim

@@ -1,0 +1,296 @@
+// planner.cpp -- gate matrices (Sec. II), validation and the tile planner.
+#include "planner.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace qsim {
+
+namespace {
+
+inline void set(Mat2 &M, int k, double re, double im) {
+    M.u[2 * k] = re;
+    M.u[2 * k + 1] = im;
+}
+
+inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+bool gate_matrix(int kind, const double *p, Mat2 &M) {
+    // cos(pi/4) = sin(pi/4): the pi/2 rotations e^{i pi S/2} = cos(pi/4) + i sin(pi/4) sigma
+    const double c = std::sqrt(0.5);
+    for (double &x : M.u) x = 0.0;
+    switch (kind) {
+    case QSIM_GATE_H:  // (sigma_x + sigma_z)/sqrt(2), Eq. Hadamard
+        set(M, 0, c, 0); set(M, 1, c, 0); set(M, 2, c, 0); set(M, 3, -c, 0);
+        return true;
+    case QSIM_GATE_X:  // cos + i sin sigma_x, Eq. Xoperation
+        set(M, 0, c, 0); set(M, 1, 0, c); set(M, 2, 0, c); set(M, 3, c, 0);
+        return true;
+    case QSIM_GATE_Y:  // cos + i sin sigma_y, Eq. Yoperation
+        set(M, 0, c, 0); set(M, 1, c, 0); set(M, 2, -c, 0); set(M, 3, c, 0);
+        return true;
+    case QSIM_GATE_XB:  // cos - i sin sigma_x
+        set(M, 0, c, 0); set(M, 1, 0, -c); set(M, 2, 0, -c); set(M, 3, c, 0);
+        return true;
+    case QSIM_GATE_YB:  // cos - i sin sigma_y
+        set(M, 0, c, 0); set(M, 1, -c, 0); set(M, 2, c, 0); set(M, 3, c, 0);
+        return true;
+    case QSIM_GATE_NOT:  // sigma_x: the flip of Eqs. NUM6, NUM8
+        set(M, 1, 1, 0); set(M, 2, 1, 0);
+        return true;
+    case QSIM_GATE_R:  // diag(1, e^{i phi}), Eq. singlephase
+        set(M, 0, 1, 0); set(M, 3, std::cos(p[0]), std::sin(p[0]));
+        return true;
+    case QSIM_GATE_V: {  // e^{i phi/2} (cos(phi/2) - i sin(phi/2) sigma_x) = Eq. COMM4
+        const double er = std::cos(p[0]), ei = std::sin(p[0]);
+        set(M, 0, 0.5 * (1 + er), 0.5 * ei); set(M, 1, 0.5 * (1 - er), -0.5 * ei);
+        set(M, 2, 0.5 * (1 - er), -0.5 * ei); set(M, 3, 0.5 * (1 + er), 0.5 * ei);
+        return true;
+    }
+    case QSIM_GATE_SU2:  // quaternion (a, b, c, d)
+        set(M, 0, p[0], p[1]); set(M, 1, p[2], p[3]); set(M, 2, -p[2], p[3]); set(M, 3, p[0], -p[1]);
+        return true;
+    case QSIM_GATE_U:
+        for (int k = 0; k < 8; k++) M.u[k] = p[k];
+        return true;
+    default:
+        return false;
+    }
+}
+
+int classify(const Mat2 &M) {
+    const bool off0 = M.u[2] == 0 && M.u[3] == 0 && M.u[4] == 0 && M.u[5] == 0;
+    const bool diag0 = M.u[0] == 0 && M.u[1] == 0 && M.u[6] == 0 && M.u[7] == 0;
+    if (off0) return (M.u[0] == 1 && M.u[1] == 0) ? GC_PHASE : GC_DIAG;
+    if (diag0) return (M.u[2] == 1 && M.u[3] == 0 && M.u[4] == 1 && M.u[5] == 0) ? GC_EXCHANGE : GC_ANTIDIAG;
+    return GC_GENERAL;
+}
+
+bool prepare_gate(const qsim_gate &g, int n, const int *phys, PGate &out, std::string &msg) {
+    char buf[160];
+    if (g.target < 0 || g.target >= n) {
+        snprintf(buf, sizeof buf, "gate target %d out of range [0, %d)", g.target, n);
+        msg = buf;
+        return false;
+    }
+    if (n < 64 && (g.ctrl_mask >> n) != 0) {
+        msg = "ctrl_mask names a qubit >= n";
+        return false;
+    }
+    if ((g.ctrl_mask >> g.target) & 1ull) {
+        msg = "ctrl_mask contains the target qubit";
+        return false;
+    }
+    out.t1 = -1;
+    out.cmask = 0;
+    for (int q = 0; q < n; q++)
+        if ((g.ctrl_mask >> q) & 1ull) out.cmask |= 1ull << phys[q];
+    out.t0 = phys[g.target];
+    out.kind = g.kind;
+    if (g.kind == QSIM_GATE_SWAP) {
+        if (g.target2 < 0 || g.target2 >= n || g.target2 == g.target) {
+            msg = "SWAP needs a second, distinct target qubit";
+            return false;
+        }
+        if ((g.ctrl_mask >> g.target2) & 1ull) {
+            msg = "ctrl_mask contains a SWAP target";
+            return false;
+        }
+        out.t1 = phys[g.target2];
+        out.gc = GC_EXCHANGE;
+        return true;
+    }
+    int np = 0;
+    switch (g.kind) {
+    case QSIM_GATE_R: case QSIM_GATE_V: np = 1; break;
+    case QSIM_GATE_SU2: np = 4; break;
+    case QSIM_GATE_U: np = 8; break;
+    default: break;
+    }
+    for (int k = 0; k < np; k++)
+        if (!std::isfinite(g.param[k])) {
+            msg = "non-finite gate parameter";
+            return false;
+        }
+    if (!gate_matrix(g.kind, g.param, out.U)) {
+        snprintf(buf, sizeof buf, "unknown gate kind %d", g.kind);
+        msg = buf;
+        return false;
+    }
+    out.gc = classify(out.U);
+    return true;
+}
+
+void fixed_bits_for(const PGate &g, FixedBitsHost &fb, uint64_t &pmask, bool &single) {
+    std::vector<int> pos;
+    uint64_t set = g.cmask;
+    for (int b = 0; b < 64; b++)
+        if ((g.cmask >> b) & 1ull) pos.push_back(b);
+    single = false;
+    pmask = 0;
+    if (g.kind == QSIM_GATE_SWAP) {
+        pos.push_back(g.t0);
+        pos.push_back(g.t1);
+        set |= 1ull << g.t0;  // visit t0 = 1, t1 = 0; the partner has them exchanged
+        pmask = (1ull << g.t0) | (1ull << g.t1);
+    } else if (g.gc == GC_PHASE) {
+        pos.push_back(g.t0);
+        set |= 1ull << g.t0;
+        single = true;
+    } else if (g.gc == GC_DIAG) {
+        single = true;
+    } else {
+        pos.push_back(g.t0);
+        pmask = 1ull << g.t0;
+    }
+    std::sort(pos.begin(), pos.end());
+    fb.npos = (int)pos.size();
+    for (int k = 0; k < fb.npos && k < 24; k++) fb.pos[k] = pos[k];
+    fb.setmask = set;
+}
+
+bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op) {
+    auto local = [&](int b) -> int {
+        if (b < g.L) return b;
+        for (int j = 0; j < g.H; j++)
+            if (g.hb[j] == b) return g.L + j;
+        return -1;
+    };
+    op = TileOp{};
+    op.tl2 = -1;
+    for (int b = 0; b < 64; b++) {
+        if (!((pg.cmask >> b) & 1ull)) continue;
+        const int lb = local(b);
+        if (lb >= 0) op.lcmask |= 1u << lb;
+        else op.gcmask |= 1ull << b;
+    }
+    for (int k = 0; k < 8; k++) op.u[k] = pg.U.u[k];
+    if (pg.kind == QSIM_GATE_SWAP) {
+        const int a = local(pg.t0), b = local(pg.t1);
+        if (a < 0 || b < 0) return false;
+        op.kind = TOP_SWAPGATE;
+        op.tl = a;
+        op.tl2 = b;
+        return true;
+    }
+    const int lt = local(pg.t0);
+    switch (pg.gc) {
+    case GC_PHASE:
+    case GC_DIAG:
+        if (lt >= 0) {
+            op.kind = pg.gc == GC_PHASE ? TOP_PHASE : TOP_DIAG;
+            op.tl = lt;
+        } else {
+            op.kind = TOP_DIAG_G;
+            op.tl = pg.t0;
+        }
+        return true;
+    case GC_GENERAL: op.kind = TOP_GENERAL; break;
+    case GC_ANTIDIAG: op.kind = TOP_ANTIDIAG; break;
+    default: op.kind = TOP_EXCHANGE; break;
+    }
+    if (lt < 0) return false;
+    op.tl = lt;
+    return true;
+}
+
+namespace {
+
+// Physical bits a gate needs inside the tile (its targets, unless diagonal).
+uint64_t target_bits(const PGate &g) {
+    if (g.kind == QSIM_GATE_SWAP) return (1ull << g.t0) | (1ull << g.t1);
+    if (g.gc == GC_PHASE || g.gc == GC_DIAG) return 0;
+    return 1ull << g.t0;
+}
+
+uint64_t touched_bits(const PGate &g) {
+    uint64_t m = g.cmask | (1ull << g.t0);
+    if (g.t1 >= 0) m |= 1ull << g.t1;
+    return m;
+}
+
+}  // namespace
+
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan) {
+    plan.passes.clear();
+    plan.ops.clear();
+    plan.dense.clear();
+    if (gates.empty()) return;
+    if (T > n) T = n;
+    if (n <= T) L = n;
+    if (L > T) L = T;
+    if (n > T && T - L < 2) L = T - 2;  // room for both targets of a SWAP
+    if (L < 1) L = 1;
+    const int H = (n > T) ? T - L : 0;
+    const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    const uint64_t low = (1ull << L) - 1;
+
+    std::vector<int> remaining(gates.size());
+    for (size_t i = 0; i < gates.size(); i++) remaining[i] = (int)i;
+    std::vector<int> sched, rest;
+    while (!remaining.empty()) {
+        uint64_t inset = low, hmask = 0, blocked = 0;
+        int hcount = 0;
+        sched.clear();
+        rest.clear();
+        for (size_t r = 0; r < remaining.size(); r++) {
+            const int gi = remaining[r];
+            const PGate &g = gates[gi];
+            const uint64_t qm = touched_bits(g);
+            if ((blocked & all) == all || (qm & blocked)) {
+                blocked |= qm;
+                rest.push_back(gi);
+                continue;
+            }
+            const uint64_t need = target_bits(g) & ~inset;
+            if (hcount + popc(need) <= H) {
+                inset |= need;
+                hmask |= need;
+                hcount += popc(need);
+                sched.push_back(gi);
+            } else {
+                blocked |= qm;
+                rest.push_back(gi);
+            }
+        }
+        // Fill the remaining high slots with the targets of the gates that
+        // come next, then with the lowest unused bits.
+        for (size_t r = 0; r < rest.size() && hcount < H; r++) {
+            uint64_t need = target_bits(gates[rest[r]]) & ~inset & all;
+            while (need && hcount < H) {
+                const uint64_t b = need & (~need + 1);
+                need &= need - 1;
+                inset |= b;
+                hmask |= b;
+                hcount++;
+            }
+        }
+        for (int b = L; b < n && hcount < H; b++)
+            if (!((inset >> b) & 1ull)) {
+                inset |= 1ull << b;
+                hmask |= 1ull << b;
+                hcount++;
+            }
+        PassPlan pp{};
+        pp.geom.n = n;
+        pp.geom.L = L;
+        pp.geom.H = hcount;
+        int j = 0;
+        for (int b = 0; b < 64; b++)
+            if ((hmask >> b) & 1ull) pp.geom.hb[j++] = b;
+        pp.op_begin = (int)plan.ops.size();
+        for (int gi : sched) {
+            TileOp op;
+            make_tile_op(gates[gi], pp.geom, op);  // fits by construction
+            plan.ops.push_back(op);
+        }
+        pp.op_count = (int)sched.size();
+        plan.passes.push_back(pp);
+        remaining.swap(rest);
+    }
+}
+
+}  // namespace qsim

@@ -1,0 +1,55 @@
+// planner.hpp -- host-side gate preparation and pass planning.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+#include "kernels.hpp"
+
+namespace qsim {
+
+// A gate after validation: physical bit positions and an FP64 matrix.
+struct PGate {
+    int kind;           // QSIM_GATE_SWAP or a 2x2 gate
+    int t0, t1;         // physical target bit(s); t1 = -1 unless SWAP
+    uint64_t cmask;     // physical control bits
+    int gc;             // GateClass of the 2x2 matrix (unused for SWAP)
+    Mat2 U;
+};
+
+// Build the 2x2 matrix of a gate kind from its parameters (Sec. II);
+// returns false for an unknown kind.
+bool gate_matrix(int kind, const double *param, Mat2 &M);
+// Class of a 2x2 matrix from exact zero / one entries.
+int classify(const Mat2 &M);
+
+// Validate a logical gate against n qubits and map it to physical bits with
+// phys[q] = bit of logical qubit q.  On error returns false and sets msg.
+bool prepare_gate(const qsim_gate &g, int n, const int *phys, PGate &out, std::string &msg);
+
+// Enumeration bits of a per-gate sweep: target(s) and controls as fixed bits.
+void fixed_bits_for(const PGate &g, FixedBitsHost &fb, uint64_t &pmask, bool &single);
+
+struct PassPlan {
+    TileGeom geom;
+    int op_begin, op_count;   // range in the plan's op array
+};
+
+struct Plan {
+    std::vector<PassPlan> passes;
+    std::vector<TileOp> ops;
+    std::vector<double> dense;   // matrix pool for TOP_DENSE (complex, interleaved)
+};
+
+// Greedy tile planner: tiles of T bits, the L lowest always included.
+// Gates are taken in order; a gate can join the current pass if it commutes
+// with every gate skipped so far (no shared qubit) and its targets fit in the
+// tile's bit set (diagonal gates need no target in the tile).
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan);
+
+// Translate one gate into a tile op for a pass with geometry g.
+bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op);
+
+}  // namespace qsim

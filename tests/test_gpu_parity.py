@@ -1,0 +1,388 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (max-abs amplitude error): 1e-12 for complex128, 2e-5 for
+complex64.  Basis-state outcomes (adder sums, argmax) must match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from inputs import Gate
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 2e-5}
+DTYPES = ["c128", "c64"]
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_quant_ph_0608239_gb300 as qq
+    qq._capi.load()
+    return qq
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return psi / np.linalg.norm(psi)
+
+
+def g1(kind, t, ctrl=(), params=()):
+    return Gate(kind, (int(t),), tuple(int(c) for c in ctrl), tuple(params))
+
+
+def run_gpu(q, n, dt, gates, psi=None, x0=0, mode=None, tile_bits=0):
+    st = q.State(n, dt)
+    if psi is not None:
+        st.set_state(psi)
+    else:
+        st.set_basis(x0)
+    st.run(gates, mode=q.MODE_FUSED if mode is None else mode, tile_bits=tile_bits)
+    out = st.get_state()
+    st.free()
+    return out
+
+
+def err(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.complex128) - b)))
+
+
+PARAMS = {"R": (0.7,), "V": (2 * math.pi / 8,), "SU2": (0.5, -0.1, 0.7, math.sqrt(1 - 0.25 - 0.01 - 0.49))}
+
+
+# ---------------------------------------------------------------- state init
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 5, 13])
+def test_basis_state_and_norm(q, dt, n):
+    st = q.State(n, dt)
+    x = (1 << n) - 3 if n > 2 else 1
+    st.set_basis(x)
+    a = st.get_state()
+    expect = np.zeros(1 << n)
+    expect[x] = 1
+    assert np.array_equal(a, expect.astype(a.dtype))
+    assert st.norm() == 1.0
+    assert list(st.qubit_probs()) == [float((x >> b) & 1) for b in range(n)]
+    st.free()
+
+
+# ------------------------------------------------------- single-qubit sweeps
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("mode", ["pergate", "fused"])
+def test_every_kind_every_target(q, dt, mode):
+    n = 12
+    psi = rand_state(n, 1)
+    m = q.MODE_PERGATE if mode == "pergate" else q.MODE_FUSED
+    for kind in ["H", "X", "Y", "XB", "YB", "NOT", "R", "V", "SU2"]:
+        for t in range(n):
+            g = g1(kind, t, (), PARAMS.get(kind, ()))
+            ref = oracle.run(n, [g], state=psi.copy())
+            got = run_gpu(q, n, dt, [g], psi=psi, mode=m, tile_bits=8)
+            assert err(got, ref) < TOL[dt], (kind, t)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_apply_1q_and_ctrl_entry_points(q, dt):
+    n = 11
+    rng = np.random.default_rng(2)
+    psi = rand_state(n, 2)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    ref = psi.copy()
+    for _ in range(30):
+        Z = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        U, _ = np.linalg.qr(Z)
+        t = int(rng.integers(n))
+        others = [b for b in range(n) if b != t]
+        ctrl = [int(c) for c in rng.choice(others, size=int(rng.integers(0, 4)), replace=False)]
+        mask = sum(1 << c for c in ctrl)
+        if ctrl:
+            st.apply_ctrl(mask, t, U)
+        else:
+            st.apply_1q(t, U)
+        oracle.run(n, [g1("U", t, ctrl, tuple(x for z in U.reshape(-1) for x in (z.real, z.imag)))], state=ref)
+    assert err(st.get_state(), ref) < TOL[dt]
+    st.free()
+
+
+# ---------------------------------------------------- controlled, Toffoli, swap
+def controlled_gates(rng, n, count):
+    out = []
+    kinds = ["NOT", "R", "V", "SU2", "H", "SWAP"]
+    for _ in range(count):
+        k = kinds[int(rng.integers(len(kinds)))]
+        qs = [int(x) for x in rng.permutation(n)]
+        nc = int(rng.integers(1, 4))
+        if k == "SWAP":
+            out.append(Gate("SWAP", (qs[0], qs[1]), tuple(qs[2:2 + nc - 1]), ()))
+            continue
+        out.append(g1(k, qs[0], qs[1:1 + nc], PARAMS.get(k, ())))
+    return out
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("mode", ["pergate", "fused"])
+def test_controlled_gates(q, dt, mode):
+    n = 13
+    rng = np.random.default_rng(3)
+    gates = controlled_gates(rng, n, 60)
+    psi = rand_state(n, 3)
+    ref = oracle.run(n, gates, state=psi.copy())
+    m = q.MODE_PERGATE if mode == "pergate" else q.MODE_FUSED
+    assert err(run_gpu(q, n, dt, gates, psi=psi, mode=m, tile_bits=9), ref) < TOL[dt]
+
+
+def test_worked_examples_on_gpu(q):
+    # Eqs. CNOT2, Toffoli: pure data movement, bit-exact in both precisions.
+    for dt in DTYPES:
+        a = (np.arange(1, 9) * (1 + 0.5j)).astype(np.complex128)
+        got = run_gpu(q, 3, dt, [g1("NOT", 2, (0, 1))], psi=a, mode=q.MODE_PERGATE)
+        assert np.array_equal(got, a[[0, 1, 2, 7, 4, 5, 6, 3]].astype(got.dtype))
+        b = a[:4].copy()
+        got = run_gpu(q, 2, dt, [g1("NOT", 1, (0,))], psi=b, mode=q.MODE_FUSED)
+        assert np.array_equal(got, b[[0, 3, 2, 1]].astype(got.dtype))
+
+
+# ------------------------------------------------------- circuits, both paths
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n,depth,tile", [(4, 6, 0), (9, 8, 6), (14, 10, 0), (14, 10, 8), (18, 6, 0), (20, 4, 10)])
+def test_random_circuit_both_paths(q, dt, n, depth, tile):
+    gates = inputs.random_circuit(n, depth, seed=100 + n)
+    rng = np.random.default_rng(n)
+    gates += controlled_gates(rng, n, 10)
+    x0 = inputs.random_basis(n, seed=n)
+    ref = oracle.run(n, gates, x0=x0)
+    for m in (q.MODE_PERGATE, q.MODE_FUSED):
+        got = run_gpu(q, n, dt, gates, x0=x0, mode=m, tile_bits=tile)
+        e = err(got, ref)
+        assert e < TOL[dt], (m, e)
+
+
+def test_qft_config_c128_and_closed_form(q):
+    n = 10
+    x, gates = inputs.qft_circuit(n, seed=1)
+    assert len(gates) == 55 + 5
+    ref = oracle.run(n, gates, x0=x)
+    got = run_gpu(q, n, "c128", gates, x0=x)
+    assert err(got, ref) < 1e-12
+    k = np.arange(1 << n)
+    assert err(got, np.exp(2j * np.pi * x * k / (1 << n)) / math.sqrt(1 << n)) < 1e-12
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("values,m", [([1365, 682], 11), ([45, 17, 60], 6), ([7, 9, 19, 35, 65], 3)])
+def test_adder_exact(q, dt, values, m):
+    n = len(values) * m
+    gates = inputs.adder_circuit(values, m)
+    want = inputs.adder_expected_index(values, m)
+    st = q.State(n, dt)
+    st.run(gates)
+    qp = st.qubit_probs()
+    got_idx = sum(1 << b for b in range(n) if qp[b] > 0.5)
+    assert got_idx == want
+    assert np.max(np.minimum(qp, 1 - qp)) < TOL[dt]
+    p = st.probs()
+    assert int(np.argmax(p)) == want and p[want] > 1 - 10 * TOL[dt]
+    st.free()
+
+
+# ------------------------------------------------------------ interchanges
+@pytest.mark.parametrize("table", ["onequbittab.txt", "twoqubittab.txt"])
+def test_permute_bits_matches_paper_tables(q, table):
+    import golden_io
+    steps, body = golden_io.layout_table_steps(table)
+    for dt in DTYPES:
+        for sig, seq in steps.items():
+            st = q.State(4, dt)
+            st.set_state(np.arange(16).astype(np.complex128))
+            for pairs in seq:
+                st.permute_bits([p[0] for p in pairs], [p[1] for p in pairs])
+            a = st.get_state()
+            for phys, logical in body[sig].items():
+                assert a[phys].real == logical
+            st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("pairs", [[(0, 13)], [(2, 9), (4, 15)], [(0, 10), (1, 11), (3, 16)], [(5, 6), (7, 8)]])
+def test_permute_bits_vs_oracle(q, dt, pairs):
+    n = 17
+    psi = rand_state(n, 7).astype(np.complex128)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    st.permute_bits([p[0] for p in pairs], [p[1] for p in pairs])
+    expect = oracle.permute_bits(psi.astype(np.complex64).astype(np.complex128) if dt == "c64" else psi, n, pairs)
+    got = st.get_state()
+    assert np.array_equal(got, expect.astype(got.dtype))  # pure data movement: bit-exact
+    st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_swap_qubits_keeps_logical_state(q, dt):
+    n = 15
+    gates = inputs.random_circuit(n, 6, seed=5)
+    ref = oracle.run(n, gates)
+    st = q.State(n, dt)
+    st.run(gates[: len(gates) // 2])
+    st.swap_qubits([0, 3], [12, 14])
+    assert st.layout()[0] == 12 and st.layout()[12] == 0 and st.layout()[3] == 14
+    st.swap_qubits([5], [13])
+    st.run(gates[len(gates) // 2:])
+    assert err(st.get_state(), ref) < TOL[dt]
+    assert abs(st.norm() - 1) < 10 * TOL[dt]
+    np.testing.assert_allclose(st.qubit_probs(), oracle.qubit_probs(ref, n), atol=10 * TOL[dt])
+    np.testing.assert_allclose(st.probs(), oracle.probs(ref, n), atol=10 * TOL[dt])
+    st.free()
+
+
+# ----------------------------------------------------------------- fusion
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_apply_fused_dense(q, dt, k):
+    n = 14
+    rng = np.random.default_rng(20 + k)
+    qs = [int(x) for x in rng.permutation(n)[:k]]
+    Z = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+    U, _ = np.linalg.qr(Z)
+    psi = rand_state(n, 9)
+    ref = oracle.apply_dense(psi.copy(), n, qs, U)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    st.apply_fused(qs, U)
+    assert err(st.get_state(), ref) < TOL[dt] * (4 if dt == "c64" else 1)
+    st.free()
+
+
+# ------------------------------------------------------------- reductions
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [3, 9, 10, 16, 21])
+def test_reductions(q, dt, n):
+    psi = rand_state(n, 11 + n)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    a = psi.astype(np.complex64).astype(np.complex128) if dt == "c64" else psi
+    tol = 1e-13 if dt == "c128" else 1e-6
+    assert abs(st.norm() - oracle.norm(a, n)) < tol
+    np.testing.assert_allclose(st.qubit_probs(), oracle.qubit_probs(a, n), atol=tol)
+    np.testing.assert_allclose(st.probs(), oracle.probs(a, n), atol=tol * 1e-3, rtol=1e-6 if dt == "c64" else 1e-12)
+    st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [3, 8, 14])
+def test_sampling_matches_oracle(q, dt, n):
+    psi = rand_state(n, 30 + n) * (1.0 + np.arange(1 << n) / (1 << n))  # uneven weights
+    psi /= np.linalg.norm(psi)
+    a = psi.astype(np.complex64).astype(np.complex128) if dt == "c64" else psi
+    u = np.random.default_rng(5).random(1001)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    got = st.sample(u)
+    ref = oracle.sample(a, n, u)
+    # samples may differ only where u * norm lies within rounding of a CDF step
+    cdf = np.cumsum(oracle.probs(a, n))
+    tot = cdf[-1]
+    near = np.min(np.abs(cdf[None, :] - (u * tot)[:, None]), axis=1) < 1e-9
+    assert np.all((got == ref) | near)
+    assert np.mean(got == ref) > 0.99
+    st.free()
+
+
+# ------------------------------------------------------------- edge cases
+def test_invalid_arguments_change_nothing(q):
+    n = 6
+    psi = rand_state(n, 1)
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    bad = [
+        lambda: st.apply_1q(n, np.eye(2)),
+        lambda: st.apply_ctrl(1 << 2, 2, np.eye(2)),
+        lambda: st.apply_ctrl(1 << n, 1, np.eye(2)),
+        lambda: st.apply_fused([1, 1], np.eye(4)),
+        lambda: st.apply_fused([0, 1, 2, 3, 4, 5, 6][:7], np.eye(128)),
+        lambda: st.swap_qubits([0, 1, 2, 3], [4, 5, 0, 1]),
+        lambda: st.swap_qubits([0], [0]),
+        lambda: st.run([g1("H", 0), g1("H", 9)]),
+        lambda: st.run([g1("NOT", 1, (1,))]),
+        lambda: st.run([Gate("SWAP", (2, 2), (), ())]),
+        lambda: st.run([g1("R", 0, (), (float("nan"),))]),
+        lambda: st.set_basis(1 << n),
+        lambda: st.sample(np.array([1.5])),
+    ]
+    for f in bad:
+        with pytest.raises(q.QsimError) as ei:
+            f()
+        assert ei.value.status == q.QSIM_EINVAL
+    assert np.array_equal(st.get_state(), psi)
+    st.free()
+
+
+def test_empty_circuit_and_one_qubit(q):
+    st = q.State(1, "c64")
+    st.run([])
+    assert np.array_equal(st.get_state(), np.array([1, 0], dtype=np.complex64))
+    st.run([g1("H", 0)])
+    assert err(st.get_state(), np.array([1, 1]) / math.sqrt(2)) < 1e-7
+    st.free()
+
+
+# ------------------------------------------- full-size checks (any-size properties)
+def _inverse(gates):
+    inv = []
+    for g in reversed(gates):
+        if g.kind == "R":
+            inv.append(Gate("R", g.targets, g.controls, (-g.params[0],)))
+        elif g.kind == "SU2":
+            a, b, c, d = g.params
+            inv.append(Gate("SU2", g.targets, g.controls, (a, -b, -c, -d)))
+        elif g.kind in ("H", "NOT", "SWAP"):
+            inv.append(g)
+        else:
+            raise ValueError(g.kind)
+    return inv
+
+
+def test_full_size_qft_sampled_amplitudes_c128(q):
+    # 30-qubit QFT (480 gates) on a basis state: every amplitude has a closed
+    # form, so a sample of 4096 of them is checked one by one (16 GiB state).
+    n = 30
+    x, gates = inputs.qft_circuit(n, seed=7)
+    st = q.State(n, "c128")
+    st.set_basis(x)
+    st.run(gates)
+    import torch
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(1).integers(0, 1 << n, 4096)
+    got = st.tensor[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    expect = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
+    assert err(got, expect) < 1e-12
+    assert abs(st.norm() - 1) < 1e-12
+    st.free()
+
+
+@pytest.mark.parametrize("n,depth,dt", [(30, 40, "c128"), (30, 40, "c64"), (34, 20, "c64")])
+def test_full_size_random_circuit_then_inverse(q, n, depth, dt):
+    # The bench circuits at full size: circuit then its inverse must return
+    # |x0> exactly (to the dtype's tolerance), and the norm must be conserved.
+    gates = inputs.random_circuit(n, depth, seed=2 if n == 30 else 4)
+    x0 = inputs.random_basis(n, seed=2)
+    st = q.State(n, dt)
+    st.set_basis(x0)
+    st.run(gates)
+    assert abs(st.norm() - 1) < (1e-12 if dt == "c128" else 1e-5)
+    st.run(_inverse(gates))
+    import torch
+    t = st.tensor
+    torch.cuda.synchronize()
+    a0 = complex(t[x0].item())
+    t[x0] = 0
+    rest = float(t.abs().max().item())
+    tol = TOL[dt] * (1 if dt == "c128" else 2.5)
+    assert abs(a0 - 1) < tol and rest < tol, (a0, rest)
+    st.free()
