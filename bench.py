@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 state-vector simulator.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step is one pass of the whole hot path over one synthetic input: set the
+register to its basis state, apply the circuit (planner path: shared-memory
+tile passes), and read the per-qubit expectations <Q_q> (Eq. Shor7).  The
+default workload is a seeded random circuit on 30 qubits, depth 40 (1800
+gates), in complex128: the configuration the headline metric is quoted on.
+
+Printed (rank 0, one JSON line): gates/s over all ranks (``value``, inputs
+resident in device memory, timed with CUDA events), the same through the
+C-ABI call with the gate list in host memory (``e2e``), the roofline of the
+dominant kernel from event-timed launches, the CPU oracle on a bounded sample
+(``cpu_baseline``), SM clocks sampled during the timed region, and the number
+of kernel launches.  ``--impl reference`` times the CPU oracle instead.
+
+N > 1 (torchrun): every rank runs its own replica of the workload (the method
+needs no exchange between replicas); ``value`` = all ranks' gates / max time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+METRIC = "gates/s and effective HBM GB/s (fraction of peak) at 30-34 qubits; fused FP32 vs FP64"
+
+WORKLOADS = {
+    "random30_c128": dict(kind="random", n=30, depth=40, seed=2, dtype="c128",
+                          text="seeded random circuit, 30 qubits, depth 40 (1800 gates), complex128"),
+    "random30_c64": dict(kind="random", n=30, depth=40, seed=2, dtype="c64",
+                         text="seeded random circuit, 30 qubits, depth 40 (1800 gates), complex64"),
+    "random34_c64": dict(kind="random", n=34, depth=20, seed=4, dtype="c64",
+                         text="seeded random circuit, 34 qubits, depth 20 (1020 gates), complex64 (128 GiB)"),
+    "adder30_c64": dict(kind="adder", n=30, m=15, seed=3, dtype="c64",
+                        text="QFT register adder of two 15-qubit registers (30 qubits), complex64"),
+    "qft10_c128": dict(kind="qft", n=10, seed=1, dtype="c128",
+                       text="10-qubit QFT with reversal swaps on a seeded basis state, complex128"),
+    "hadamard30_c128": dict(kind="hadamard", n=30, dtype="c128",
+                            text="Hadamard on every qubit of 30 qubits (the paper's scaling test), complex128"),
+}
+
+# Peaks: measured copy bandwidth from MEASURED_PEAKS.json; ALU peaks are the
+# nominal GB300 figures (FP64 1.25 TFLOP/s from the vendor figure;
+# FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_gates(w):
+    if w["kind"] == "random":
+        return inputs.random_circuit(w["n"], w["depth"], w["seed"]), inputs.random_basis(w["n"], w["seed"])
+    if w["kind"] == "adder":
+        rng = np.random.default_rng(w["seed"])
+        a, b = (int(v) for v in rng.integers(0, 1 << w["m"], 2))
+        return inputs.adder_circuit([a, b], w["m"]), 0
+    if w["kind"] == "qft":
+        x, g = inputs.qft_circuit(w["n"], seed=w["seed"])
+        return g, x
+    if w["kind"] == "hadamard":
+        return inputs.hadamard_all(w["n"]), 0
+    raise ValueError(w["kind"])
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for ln in f:
+            ln = ln.split("#", 1)[0].split()
+            if len(ln) >= 3 and ln[0] == kernel and ln[1] == workload:
+                return float(ln[2])
+    return None
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        first = vis.split(",")[0].strip() if vis else ""
+        if first.isdigit():
+            cmd += ["-i", first]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- distributed glue
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(units, seconds, ws, device=None):
+    """Total units over ranks and the max elapsed time (for N > 1)."""
+    if ws == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=device)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(w, gates, x0, budget_s=15.0):
+    """The oracle, as it stands, on the first gates of the workload until
+    about budget_s seconds of work; returns (gates/s, gates done, threads)."""
+    import oracle
+    n = w["n"]
+    a = oracle.basis(n, x0)
+    done, t0 = 0, time.perf_counter()
+    for g in gates:
+        oracle.run(n, [g], state=a)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    del a
+    return done / el, done, oracle.num_threads()
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args, w, ws, rank, local):
+    import torch
+    import paper_quant_ph_0608239_gb300 as q
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    gates, x0 = workload_gates(w)
+    n, ng = w["n"], len(gates)
+    st = q.State(n, w["dtype"])
+    plan = st.plan(gates)
+    pst = plan.stats()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        st.set_basis(x0)
+        plan.run()
+        return st.qubit_probs()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c0 = st.counters()
+    st.profile(True)
+    clocks = ClockSampler()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        qp = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    el = e0.elapsed_time(e1) / 1e3
+    prof = st.profile_read()
+    st.profile(False)
+    c1 = st.counters()
+    launches = c1["launches"] - c0["launches"]
+    total_gates, max_el = aggregate(float(ng * args.steps), el, ws, dev)
+    value = total_gates / max_el
+    norm_drift = abs(st.norm() - 1.0)
+
+    # e2e: the gate list in host memory through qsim_run_circuit each step,
+    # the expectations read back to host memory.
+    arr = q.gate_array(gates)
+    for _ in range(1):
+        st.set_basis(x0)
+        st.run(None, gate_arr=arr)
+        st.qubit_probs()
+    torch.cuda.synchronize()
+    c2 = st.counters()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.set_basis(x0)
+        st.run(None, gate_arr=arr)
+        st.qubit_probs()
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    c3 = st.counters()
+    e2e_gates, e2e_max = aggregate(float(ng * args.steps), e2e_el, ws, dev)
+
+    hbm_peak, peak_src = peaks()
+    fam, (nl, ms, by, fl) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / nl / 1e3
+    gbs = by / nl / per_launch_s / 1e9
+    tflops = fl / nl / per_launch_s / 1e12
+    alu_peak = FP64_PEAK_TFLOPS if w["dtype"] == "c128" else FP32_PEAK_TFLOPS
+    frac_hbm, frac_alu = gbs / hbm_peak, tflops / alu_peak
+    traffic = ncu_traffic(fam, args.workload)
+    hbm_roof = {"bound": "hbm", "kernel": fam, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": frac_hbm, "traffic": traffic, "peak_source": peak_src + " copy (MEASURED_PEAKS.json)",
+                "alg_bytes_per_launch": by / nl, "launches": nl, "avg_launch_ms": ms / nl}
+    alu_roof = {"bound": "alu", "kernel": fam, "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": traffic,
+                "peak_source": ("nominal GB300 FP64" if w["dtype"] == "c128" else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
+                "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
+    roof, other = (alu_roof, hbm_roof) if frac_alu > frac_hbm else (hbm_roof, alu_roof)
+
+    # effective bandwidth of the whole step (algorithmic bytes / step time)
+    step_bytes = sum(v[2] for v in prof.values()) / args.steps
+    eff_gbs = step_bytes / (el / args.steps) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w["dtype"] == "c128" else "f32",
+        "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
+        "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
+                   "path": "planner (tile passes)", "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
+                   "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
+                   "parallelism": "replicas x%d" % ws},
+        "eff_hbm_gbs": eff_gbs, "eff_hbm_frac": eff_gbs / hbm_peak,
+        "norm_drift": norm_drift,
+        "roofline": roof, "roofline_other": other,
+        "kernels": {k: {"launches": v[0], "ms": v[1], "alg_bytes": v[2], "alg_flops": v[3]} for k, v in prof.items()},
+        "e2e": {"value": e2e_gates / e2e_max, "unit": "gates/s",
+                "h2d_bytes_per_step": (c3["h2d_bytes"] - c2["h2d_bytes"]) // args.steps,
+                "d2h_bytes_per_step": (c3["d2h_bytes"] - c2["d2h_bytes"]) // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    plan.free()
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+
+    if rank == 0 and ws == 1 and not args.no_companions and w["kind"] == "random":
+        out["companions"] = companions(q, w, gates, x0, args)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, done, thr = oracle_sample(w, gates, x0, args.cpu_budget)
+        out["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle",
+                               "sample": "first %d of %d gates of the workload at full size (%d qubits, complex128 "
+                                         "oracle), timed on %d host threads" % (done, ng, n, thr)}
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def companions(q, w, gates, x0, args):
+    """Same circuit through the FP32 planner path and a per-gate FP64 sample."""
+    import torch
+    res = {}
+    n, ng = w["n"], len(gates)
+    for dt in (["c64"] if w["dtype"] == "c128" else ["c128"]):
+        st = q.State(n, dt)
+        plan = st.plan(gates)
+        st.set_basis(x0)
+        plan.run()
+        st.qubit_probs()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            st.set_basis(x0)
+            plan.run()
+            st.qubit_probs()
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / max(1, args.steps)
+        res["fused_" + ("fp32_c64" if dt == "c64" else "fp64_c128")] = {
+            "gates_per_s": ng / el, "ms_per_step": el * 1e3, "passes": plan.stats()["passes"]}
+        plan.free()
+        st.free()
+        torch.cuda.empty_cache()
+    # per-gate FP64 path, timed on the first two layers of the circuit
+    sub = gates[: 2 * (n + n // 2)] if w["kind"] == "random" else gates[:64]
+    st = q.State(n, "c128")
+    st.run(sub, mode=q.MODE_PERGATE)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.run(sub, mode=q.MODE_PERGATE)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    res["pergate_fp64_c128_sample"] = {"gates_per_s": len(sub) / el, "sample": "first %d gates" % len(sub)}
+    st.free()
+    torch.cuda.empty_cache()
+    return res
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args, w, ws, rank):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    gates, x0 = workload_gates(w)
+    budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(w, gates, x0, budget / 4)
+    vals = []
+    thr, done = 1, 0
+    for _ in range(args.steps):
+        v, done, thr = oracle_sample(w, gates, x0, budget)
+        vals.append(v)
+    v = statistics.median(vals)
+    sample = "first %d of %d gates per step at full size (%d qubits, complex128 oracle), %d host threads" % (
+        done, len(gates), w["n"], thr)
+    return {
+        "metric": METRIC, "value": v, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * done / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded generator (inputs/circuits.py)",
+        "config": {"workload": w["text"], "name": args.workload, "n": w["n"], "gates": len(gates)},
+        "impl": "reference",
+        "cpu_baseline": {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random30_c128")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-companions", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the qubit count (smaller cases for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    ws, rank, local = dist_env()
+    w = dict(WORKLOADS[args.workload])
+    if args.n and w["kind"] in ("random", "hadamard"):
+        w["n"] = args.n
+        w["text"] = w["text"].replace("%d qubits" % WORKLOADS[args.workload]["n"], "%d qubits" % args.n)
+        args.workload = args.workload + "_n%d" % args.n
+    if args.impl == "reference":
+        out = run_reference(args, w, ws, rank)
+    else:
+        out = run_ours(args, w, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

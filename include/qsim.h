@@ -184,6 +184,61 @@ QSIM_API qsim_status qsim_get_layout(qsim_handle h, int *phys);
  * gate) nothing has been applied. */
 QSIM_API qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts);
 
+/* ---- plans: a circuit planned and uploaded once, run many times ------------
+ * qsim_plan_create validates and plans gates for handle h (its n, dtype and
+ * current qubit-to-bit map) and uploads the tile programs to device memory,
+ * so that qsim_plan_run only enqueues kernels.  A plan may be run on any
+ * handle with the same n, dtype and map; EINVAL otherwise.  qsim_plan_run
+ * leaves the map unchanged. */
+typedef struct qsim_plan_s *qsim_plan;
+
+typedef struct {
+    int32_t passes;      /* shared-memory tile passes per run */
+    int32_t sweeps;      /* whole-state per-gate sweeps per run */
+    int32_t ops;         /* gate operations in all tile programs */
+    int32_t tile_bits;   /* T of the tile passes (0 if none) */
+    double gates;        /* logical gates of the circuit */
+    double alg_bytes;    /* algorithmic bytes of one run: 2 * amplitude size * amplitudes
+                            each pass or sweep must read and write */
+    double alg_flops;    /* algorithmic real floating-point operations of one run:
+                            14 per amplitude for a dense 2x2 gate, 6 for a diagonal
+                            or anti-diagonal one, 0 for a pure exchange, scaled by
+                            the fraction of amplitudes the gate's controls select */
+} qsim_plan_stats;
+
+QSIM_API qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
+                                      qsim_plan *out);
+QSIM_API qsim_status qsim_plan_run(qsim_handle h, qsim_plan p);
+QSIM_API qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out);
+QSIM_API qsim_status qsim_plan_free(qsim_plan p);
+
+/* ---- instrumentation --------------------------------------------------------
+ * qsim_profile_enable(h, 1): from now on every kernel launch made for h is
+ * bracketed by CUDA events recorded on h's stream.  qsim_profile_read waits
+ * for the stream, aggregates the event timings per kernel family and resets
+ * the record: out[i] for i < *count (at most max entries). */
+typedef struct {
+    char name[32];       /* kernel family, e.g. "tile_pass", "pair_sweep" */
+    uint64_t launches;
+    double total_ms;     /* sum of event-timed durations */
+    double alg_bytes;    /* algorithmic bytes of those launches */
+    double alg_flops;    /* algorithmic floating-point operations of those launches */
+} qsim_kernel_time;
+
+QSIM_API qsim_status qsim_profile_enable(qsim_handle h, int on);
+QSIM_API qsim_status qsim_profile_read(qsim_handle h, qsim_kernel_time *out, int max, int *count);
+
+/* Running totals since the handle was created: kernel launches made for it
+ * and bytes it copied host->device (inputs: states, gate programs, uniforms)
+ * and device->host (results). */
+typedef struct {
+    uint64_t launches;
+    uint64_t h2d_bytes;
+    uint64_t d2h_bytes;
+} qsim_counters;
+
+QSIM_API qsim_status qsim_get_counters(qsim_handle h, qsim_counters *out);
+
 /* ---- batches of independent circuits -------------------------------------
  * One circuit of a batch: the state hs (C64, made by qsim_alloc or
  * qsim_attach) is set to |x0> and the gates are applied. */

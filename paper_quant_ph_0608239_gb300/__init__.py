@@ -16,7 +16,8 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import (QsimError, QsimGate, QsimOpts, QsimCircuit, gate_array, gate_record,  # noqa: F401
+from ._capi import (QsimError, QsimGate, QsimOpts, QsimCircuit, QsimPlanStats, QsimKernelTime,  # noqa: F401
+                    QsimCounters, gate_array, gate_record,
                     MODE_PERGATE, MODE_FUSED, QSIM_C64, QSIM_C128, QSIM_ETIMEOUT, QSIM_EINVAL)
 
 _DT = {"c64": QSIM_C64, "complex64": QSIM_C64, "c128": QSIM_C128, "complex128": QSIM_C128}
@@ -151,6 +152,27 @@ class State:
         o = opts(mode, tile_bits, fuse_k)
         _capi.call("qsim_run_circuit", self.handle, arr, ng, ctypes.byref(o))
 
+    def plan(self, gates, mode=MODE_FUSED, tile_bits=0, fuse_k=0):
+        """Plan and upload a circuit once (qsim_plan_create); returns a Plan."""
+        return Plan(self, gates, mode, tile_bits, fuse_k)
+
+    # -- instrumentation --------------------------------------------------
+    def profile(self, on=True):
+        _capi.call("qsim_profile_enable", self.handle, 1 if on else 0)
+
+    def profile_read(self):
+        """{kernel family: (launches, total_ms, alg_bytes, alg_flops)} since the last read."""
+        out = (QsimKernelTime * 16)()
+        cnt = ctypes.c_int()
+        _capi.call("qsim_profile_read", self.handle, out, 16, ctypes.byref(cnt))
+        return {out[i].name.decode(): (out[i].launches, out[i].total_ms, out[i].alg_bytes, out[i].alg_flops)
+                for i in range(cnt.value)}
+
+    def counters(self):
+        c = QsimCounters()
+        _capi.call("qsim_get_counters", self.handle, ctypes.byref(c))
+        return {"launches": c.launches, "h2d_bytes": c.h2d_bytes, "d2h_bytes": c.d2h_bytes}
+
     # -- measurement ------------------------------------------------------
     def norm(self):
         out = ctypes.c_double()
@@ -173,6 +195,38 @@ class State:
         _capi.call("qsim_sample", self.handle, u.ctypes.data_as(ctypes.c_void_p), u.size,
                    out.ctypes.data_as(ctypes.c_void_p))
         return out
+
+
+class Plan:
+    """A circuit planned and uploaded once; ``run()`` only enqueues kernels."""
+
+    def __init__(self, state, gates, mode=MODE_FUSED, tile_bits=0, fuse_k=0):
+        self.state = state
+        arr = gate_array(gates)
+        o = opts(mode, tile_bits, fuse_k)
+        p = ctypes.c_void_p()
+        _capi.call("qsim_plan_create", state.handle, arr, len(gates), ctypes.byref(o), ctypes.byref(p))
+        self.ptr = p
+
+    def run(self, state=None):
+        _capi.call("qsim_plan_run", (state or self.state).handle, self.ptr)
+
+    def stats(self):
+        s = QsimPlanStats()
+        _capi.call("qsim_plan_get_stats", self.ptr, ctypes.byref(s))
+        return {"passes": s.passes, "sweeps": s.sweeps, "ops": s.ops, "tile_bits": s.tile_bits,
+                "gates": s.gates, "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
+
+    def free(self):
+        if self.ptr is not None and self.ptr.value:
+            _capi.call("qsim_plan_free", self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def run_batch(states, x0s, gate_lists, mode=MODE_FUSED):

@@ -38,6 +38,21 @@ class QsimCircuit(ctypes.Structure):
                 ("gates", ctypes.POINTER(QsimGate)), ("ng", ctypes.c_size_t)]
 
 
+class QsimPlanStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("ops", ctypes.c_int32),
+                ("tile_bits", ctypes.c_int32), ("gates", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("alg_flops", ctypes.c_double)]
+
+
+class QsimKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
+
+
+class QsimCounters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+
+
 class QsimError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("qsim status %d: %s" % (status, msg))
@@ -74,6 +89,15 @@ _SIGS = {
     "qsim_sample": ([c_handle, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], None),
     "qsim_get_state": ([c_handle, ctypes.c_void_p, ctypes.c_size_t], None),
     "qsim_sync": ([c_handle], None),
+    "qsim_plan_create": ([c_handle, ctypes.POINTER(QsimGate), ctypes.c_size_t, ctypes.POINTER(QsimOpts),
+                          ctypes.POINTER(ctypes.c_void_p)], None),
+    "qsim_plan_run": ([c_handle, ctypes.c_void_p], None),
+    "qsim_plan_get_stats": ([ctypes.c_void_p, ctypes.POINTER(QsimPlanStats)], None),
+    "qsim_plan_free": ([ctypes.c_void_p], None),
+    "qsim_profile_enable": ([c_handle, ctypes.c_int], None),
+    "qsim_profile_read": ([c_handle, ctypes.POINTER(QsimKernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                          None),
+    "qsim_get_counters": ([c_handle, ctypes.POINTER(QsimCounters)], None),
     "qsim_last_error": ([], ctypes.c_char_p),
     "qsim_version": ([], ctypes.c_char_p),
 }

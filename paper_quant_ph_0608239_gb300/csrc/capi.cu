@@ -41,6 +41,12 @@ static qsim_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 // ----------------------------------------------------------------- handle
+struct ProfRec {
+    int fam;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+
 struct qsim_state {
     int n = 0;
     qsim_dtype dt = QSIM_C64;
@@ -61,7 +67,47 @@ struct qsim_state {
     size_t dense_cap = 0;
     void *d_chunk = nullptr;   // staging for logical-order reads
     size_t chunk_bytes = 0;
+    TileOp *h_ops = nullptr;   // pinned staging of gate programs
+    size_t h_ops_cap = 0;
+    cudaEvent_t upload_done = nullptr;
+    // instrumentation
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    uint64_t launches = 0, h2d = 0, d2h = 0;
 };
+
+// Kernel families reported by qsim_profile_read.
+enum Fam { F_INIT, F_PAIR, F_DIAG, F_DENSE, F_TILE, F_NORM, F_BITS, F_PROBS, F_GATHER, F_SAMPLE, F_FUSED_TC,
+           F_BATCH, F_COUNT };
+static const char *kFamName[F_COUNT] = {"init_basis", "pair_sweep", "diag_sweep", "dense_cuda_core", "tile_pass",
+                                        "norm", "bit_probs", "probs", "gather", "sample", "fused_tensor_core",
+                                        "batch"};
+
+static cudaEvent_t take_event(qsim_state *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Every kernel launch made for a handle goes through here: it is counted and,
+// when profiling is on, bracketed by events on the handle's stream.
+template <class F>
+static cudaError_t launch(qsim_state *h, int fam, double alg_bytes, int nkernels, F &&f, double alg_flops = 0.0) {
+    h->launches += (uint64_t)nkernels;
+    if (!h->prof) return f();
+    cudaEvent_t a = take_event(h), b = take_event(h);
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = f();
+    cudaEventRecord(b, h->stream);
+    h->recs.push_back(ProfRec{fam, a, b, alg_bytes, alg_flops});
+    return e;
+}
 
 static size_t amp_bytes(qsim_dtype dt) { return dt == QSIM_C64 ? 8 : 16; }
 static size_t state_bytes(const qsim_state *h) { return amp_bytes(h->dt) << h->n; }
@@ -86,6 +132,13 @@ static qsim_status init_common(qsim_state *h) {
 
 static void release(qsim_state *h) {
     if (!h) return;
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->upload_done) cudaEventDestroy(h->upload_done);
+    if (h->h_ops) cudaFreeHost(h->h_ops);
     if (h->owns && h->amp) cudaFree(h->amp);
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_res) cudaFree(h->d_res);
@@ -101,6 +154,7 @@ static void release(qsim_state *h) {
 static qsim_status sync_check(qsim_state *h) {
     CK(cudaMemcpyAsync(h->h_res + 63, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream),
        "read error word");
+    h->d2h += sizeof(uint32_t);
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     uint32_t e;
     std::memcpy(&e, h->h_res + 63, sizeof e);
@@ -145,7 +199,8 @@ qsim_status qsim_alloc(int n, qsim_dtype dt, qsim_handle *out) {
     }
     qsim_status st = init_common(h);
     if (st == QSIM_OK) {
-        e = launch_init_basis(h->amp, (int)dt, n, 0, h->stream);
+        e = launch(h, F_INIT, (double)state_bytes(h), 1,
+                   [&] { return launch_init_basis(h->amp, (int)dt, n, 0, h->stream); });
         if (e != cudaSuccess) st = cuda_fail(e, "init basis");
     }
     if (st != QSIM_OK) {
@@ -203,7 +258,9 @@ qsim_status qsim_set_basis(qsim_handle h, uint64_t x) {
     CHECK_HANDLE(h);
     if (h->n < 64 && x >= (1ull << h->n)) return fail(QSIM_EINVAL, "basis index out of range");
     for (int q = 0; q < 64; q++) h->phys[q] = q;
-    CK(launch_init_basis(h->amp, (int)h->dt, h->n, x, h->stream), "init basis");
+    CK(launch(h, F_INIT, (double)state_bytes(h), 1,
+              [&] { return launch_init_basis(h->amp, (int)h->dt, h->n, x, h->stream); }),
+       "init basis");
     return QSIM_OK;
 }
 
@@ -212,6 +269,7 @@ qsim_status qsim_set_state(qsim_handle h, const void *host_in, size_t bytes) {
     if (!host_in || bytes != state_bytes(h)) return fail(QSIM_EINVAL, "need %zu bytes", state_bytes(h));
     for (int q = 0; q < 64; q++) h->phys[q] = q;
     CK(cudaMemcpyAsync(h->amp, host_in, bytes, cudaMemcpyHostToDevice, h->stream), "copy state in");
+    h->h2d += bytes;
     CK(cudaStreamSynchronize(h->stream), "sync");
     return QSIM_OK;
 }
@@ -223,8 +281,15 @@ static qsim_status sweep_gate(qsim_state *h, const PGate &pg) {
     bool single;
     fixed_bits_for(pg, fb, pmask, single);
     if (fb.npos > h->n) return QSIM_OK;  // cannot happen after validation
-    cudaError_t e = single ? launch_diag(h->amp, (int)h->dt, h->n, fb, pg.t0, pg.U, h->stream)
-                           : launch_pairs(h->amp, (int)h->dt, h->n, fb, pmask, pg.gc, pg.U, h->stream);
+    const double touched = std::ldexp(single ? 1.0 : 2.0, h->n - fb.npos);
+    const double bytes = 2.0 * (double)amp_bytes(h->dt) * touched;
+    const double flops = gate_flops(pg, h->n);
+    cudaError_t e = single ? launch(h, F_DIAG, bytes, 1,
+                                    [&] { return launch_diag(h->amp, (int)h->dt, h->n, fb, pg.t0, pg.U, h->stream); },
+                                    flops)
+                           : launch(h, F_PAIR, bytes, 1, [&] {
+                                 return launch_pairs(h->amp, (int)h->dt, h->n, fb, pmask, pg.gc, pg.U, h->stream);
+                             }, flops);
     if (e != cudaSuccess) return cuda_fail(e, "gate sweep");
     return QSIM_OK;
 }
@@ -286,17 +351,39 @@ static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &
     if (L < 1) L = 1;
 }
 
-static qsim_status run_plan(qsim_state *h, const Plan &plan) {
-    if (plan.ops.empty()) return QSIM_OK;
-    qsim_status st = ensure_ops(h, plan.ops.size());
+// Copy a gate program to device memory through the handle's pinned staging
+// buffer (the previous upload must have left the staging buffer first).
+static qsim_status upload_ops(qsim_state *h, const std::vector<TileOp> &ops) {
+    qsim_status st = ensure_ops(h, ops.size());
     if (st != QSIM_OK) return st;
-    CK(cudaMemcpyAsync(h->d_ops, plan.ops.data(), plan.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice,
-                       h->stream),
+    if (!h->upload_done) CK(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming), "event");
+    CK(cudaEventSynchronize(h->upload_done), "wait staging");
+    if (ops.size() > h->h_ops_cap) {
+        if (h->h_ops) cudaFreeHost(h->h_ops);
+        h->h_ops = nullptr;
+        h->h_ops_cap = 0;
+        const size_t cap = std::max(ops.size(), (size_t)1024);
+        CK(cudaMallocHost(&h->h_ops, cap * sizeof(TileOp)), "cudaMallocHost staging");
+        h->h_ops_cap = cap;
+    }
+    std::memcpy(h->h_ops, ops.data(), ops.size() * sizeof(TileOp));
+    CK(cudaMemcpyAsync(h->d_ops, h->h_ops, ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice, h->stream),
        "upload tile ops");
+    CK(cudaEventRecord(h->upload_done, h->stream), "event record");
+    h->h2d += ops.size() * sizeof(TileOp);
+    return QSIM_OK;
+}
+
+static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *d_ops) {
+    const double pass_bytes = 2.0 * (double)state_bytes(h);
     for (const PassPlan &pp : plan.passes) {
         if (pp.op_count == 0) continue;
-        CK(launch_tile_pass(h->amp, (int)h->dt, pp.geom, h->d_ops + pp.op_begin, pp.op_count, h->d_dense, h->d_err,
-                            h->sm_count, h->stream),
+        CK(launch(h, F_TILE, pass_bytes, 1,
+                  [&] {
+                      return launch_tile_pass(h->amp, (int)h->dt, pp.geom, d_ops + pp.op_begin, pp.op_count,
+                                              h->d_dense, h->d_err, h->sm_count, h->stream);
+                  },
+                  pp.flops),
            "tile pass");
     }
     return QSIM_OK;
@@ -311,28 +398,172 @@ static qsim_status prepare_all(qsim_state *h, const qsim_gate *gates, size_t ng,
     return QSIM_OK;
 }
 
-qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts) {
-    CHECK_HANDLE(h);
+// A planned circuit.
+struct qsim_plan_s {
+    int n = 0;
+    qsim_dtype dt = QSIM_C64;
+    int phys[64];
+    int mode = QSIM_MODE_FUSED;
+    std::vector<PGate> sweeps;   // PERGATE mode
+    Plan plan;                   // FUSED mode
+    TileOp *d_ops = nullptr;
+    qsim_plan_stats stats{};
+};
+
+static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
+                              qsim_plan_s &P) {
     if (ng && !gates) return fail(QSIM_EINVAL, "gates is NULL");
     qsim_opts o;
     qsim_default_opts(&o);
     if (opts) o = *opts;
+    if (o.mode != QSIM_MODE_FUSED && o.mode != QSIM_MODE_PERGATE) return fail(QSIM_EINVAL, "unknown mode %d", o.mode);
     std::vector<PGate> pg;
     qsim_status st = prepare_all(h, gates, ng, pg);
     if (st != QSIM_OK) return st;
+    P.n = h->n;
+    P.dt = h->dt;
+    std::memcpy(P.phys, h->phys, sizeof P.phys);
+    P.mode = o.mode;
+    P.stats = qsim_plan_stats{};
+    P.stats.gates = (double)ng;
     if (o.mode == QSIM_MODE_PERGATE) {
-        for (const PGate &g : pg) {
-            st = sweep_gate(h, g);
+        P.sweeps = std::move(pg);
+        P.stats.sweeps = (int)P.sweeps.size();
+        for (const PGate &g : P.sweeps) {
+            FixedBitsHost fb{};
+            uint64_t pmask;
+            bool single;
+            fixed_bits_for(g, fb, pmask, single);
+            P.stats.alg_bytes += 2.0 * (double)amp_bytes(h->dt) * std::ldexp(single ? 1.0 : 2.0, h->n - fb.npos);
+            P.stats.alg_flops += gate_flops(g, h->n);
+        }
+        return QSIM_OK;
+    }
+    int T, L;
+    tile_defaults(h, &o, T, L);
+    plan_tiles(pg, h->n, T, L, P.plan);
+    for (const PassPlan &pp : P.plan.passes)
+        if (pp.op_count) P.stats.passes++;
+    P.stats.ops = (int)P.plan.ops.size();
+    P.stats.tile_bits = P.plan.passes.empty() ? 0 : P.plan.passes[0].geom.L + P.plan.passes[0].geom.H;
+    P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
+    for (const PassPlan &pp : P.plan.passes) P.stats.alg_flops += pp.flops;
+    return QSIM_OK;
+}
+
+static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops) {
+    if (P.mode == QSIM_MODE_PERGATE) {
+        for (const PGate &g : P.sweeps) {
+            qsim_status st = sweep_gate(h, g);
             if (st != QSIM_OK) return st;
         }
         return QSIM_OK;
     }
-    if (o.mode != QSIM_MODE_FUSED) return fail(QSIM_EINVAL, "unknown mode %d", o.mode);
-    int T, L;
-    tile_defaults(h, &o, T, L);
-    Plan plan;
-    plan_tiles(pg, h->n, T, L, plan);
-    return run_plan(h, plan);
+    return launch_passes(h, P.plan, d_ops);
+}
+
+qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts) {
+    CHECK_HANDLE(h);
+    qsim_plan_s P;
+    qsim_status st = build_plan(h, gates, ng, opts, P);
+    if (st != QSIM_OK) return st;
+    if (P.mode == QSIM_MODE_FUSED && !P.plan.ops.empty()) {
+        st = upload_ops(h, P.plan.ops);
+        if (st != QSIM_OK) return st;
+    }
+    return run_built(h, P, h->d_ops);
+}
+
+qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
+                             qsim_plan *out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    qsim_plan_s *P = new qsim_plan_s;
+    qsim_status st = build_plan(h, gates, ng, opts, *P);
+    if (st == QSIM_OK && !P->plan.ops.empty()) {
+        cudaError_t e = cudaMalloc(&P->d_ops, P->plan.ops.size() * sizeof(TileOp));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_ops, P->plan.ops.data(), P->plan.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload plan");
+        else h->h2d += P->plan.ops.size() * sizeof(TileOp);
+    }
+    if (st != QSIM_OK) {
+        if (P->d_ops) cudaFree(P->d_ops);
+        delete P;
+        return st;
+    }
+    *out = P;
+    return QSIM_OK;
+}
+
+qsim_status qsim_plan_run(qsim_handle h, qsim_plan p) {
+    CHECK_HANDLE(h);
+    if (!p) return fail(QSIM_EINVAL, "null plan");
+    if (p->n != h->n || p->dt != h->dt || std::memcmp(p->phys, h->phys, sizeof(int) * h->n) != 0)
+        return fail(QSIM_EINVAL, "plan was made for another size, dtype or qubit layout");
+    return run_built(h, *p, p->d_ops);
+}
+
+qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
+    if (!p || !out) return fail(QSIM_EINVAL, "null argument");
+    *out = p->stats;
+    return QSIM_OK;
+}
+
+qsim_status qsim_plan_free(qsim_plan p) {
+    if (!p) return QSIM_OK;
+    if (p->d_ops) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_ops);
+    }
+    delete p;
+    return QSIM_OK;
+}
+
+qsim_status qsim_profile_enable(qsim_handle h, int on) {
+    CHECK_HANDLE(h);
+    h->prof = on != 0;
+    return QSIM_OK;
+}
+
+qsim_status qsim_profile_read(qsim_handle h, qsim_kernel_time *out, int max, int *count) {
+    CHECK_HANDLE(h);
+    if (!count || (max > 0 && !out)) return fail(QSIM_EINVAL, "null output");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    qsim_kernel_time agg[F_COUNT];
+    std::memset(agg, 0, sizeof agg);
+    for (auto &r : h->recs) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        agg[r.fam].launches++;
+        agg[r.fam].total_ms += ms;
+        agg[r.fam].alg_bytes += r.bytes;
+        agg[r.fam].alg_flops += r.flops;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    int c = 0;
+    for (int f = 0; f < F_COUNT; f++) {
+        if (!agg[f].launches) continue;
+        if (c < max) {
+            out[c] = agg[f];
+            std::snprintf(out[c].name, sizeof out[c].name, "%s", kFamName[f]);
+        }
+        c++;
+    }
+    *count = c < max ? c : max;
+    return QSIM_OK;
+}
+
+qsim_status qsim_get_counters(qsim_handle h, qsim_counters *out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(QSIM_EINVAL, "null output");
+    out->launches = h->launches;
+    out->h2d_bytes = h->h2d;
+    out->d2h_bytes = h->d2h;
+    return QSIM_OK;
 }
 
 qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U) {
@@ -368,7 +599,10 @@ qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const doub
     } else {
         CK(cudaMemcpyAsync(h->d_dense, U, bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
     }
-    CK(launch_dense(h->amp, (int)h->dt, h->n, k, pos, h->d_dense, h->stream), "dense gate");
+    h->h2d += bytes;
+    CK(launch(h, F_DENSE, 2.0 * (double)state_bytes(h), 1,
+              [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, pos, h->d_dense, h->stream); }),
+       "dense gate");
     return QSIM_OK;
 }
 
@@ -436,7 +670,9 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
     pp.op_begin = 0;
     pp.op_count = 1;
     plan.passes.push_back(pp);
-    return run_plan(h, plan);
+    qsim_status st = upload_ops(h, plan.ops);
+    if (st != QSIM_OK) return st;
+    return launch_passes(h, plan, h->d_ops);
 }
 
 static qsim_status check_pairs(const qsim_state *h, int K, const int *a, const int *b) {
@@ -491,8 +727,11 @@ qsim_status qsim_sync(qsim_handle h) {
 qsim_status qsim_norm(qsim_handle h, double *out) {
     CHECK_HANDLE(h);
     if (!out) return fail(QSIM_EINVAL, "NULL output");
-    CK(launch_norm(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream), "norm");
+    CK(launch(h, F_NORM, (double)state_bytes(h), 2,
+              [&] { return launch_norm(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream); }),
+       "norm");
     CK(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy norm");
+    h->d2h += sizeof(double);
     qsim_status st = sync_check(h);
     if (st != QSIM_OK) return st;
     *out = h->h_res[0];
@@ -502,9 +741,12 @@ qsim_status qsim_norm(qsim_handle h, double *out) {
 qsim_status qsim_qubit_probs(qsim_handle h, double *out) {
     CHECK_HANDLE(h);
     if (!out) return fail(QSIM_EINVAL, "NULL output");
-    CK(launch_bit_probs(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream), "bit marginals");
+    CK(launch(h, F_BITS, (double)state_bytes(h), h->n >= 10 ? 2 : 1,
+              [&] { return launch_bit_probs(h->amp, (int)h->dt, h->n, h->d_scratch, h->d_res, h->stream); }),
+       "bit marginals");
     CK(cudaMemcpyAsync(h->h_res, h->d_res, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
        "copy marginals");
+    h->d2h += h->n * sizeof(double);
     qsim_status st = sync_check(h);
     if (st != QSIM_OK) return st;
     for (int q = 0; q < h->n; q++) out[q] = h->h_res[h->phys[q]];
@@ -528,11 +770,15 @@ qsim_status qsim_probs(qsim_handle h, double *out, size_t len) {
     const uint64_t per = h->chunk_bytes / sizeof(double);
     for (uint64_t s = 0; s < D; s += per) {
         const uint64_t cnt = std::min(per, D - s);
-        CK(launch_probs_chunk(h->amp, (int)h->dt, h->n, h->phys, ident, s, cnt, static_cast<double *>(h->d_chunk),
-                              h->stream),
+        CK(launch(h, F_PROBS, (double)cnt * (double)(amp_bytes(h->dt) + sizeof(double)), 1,
+                  [&] {
+                      return launch_probs_chunk(h->amp, (int)h->dt, h->n, h->phys, ident, s, cnt,
+                                                static_cast<double *>(h->d_chunk), h->stream);
+                  }),
            "probabilities");
         CK(cudaMemcpyAsync(out + s, h->d_chunk, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
            "copy probabilities");
+        h->d2h += cnt * sizeof(double);
         CK(cudaStreamSynchronize(h->stream), "sync");
     }
     return sync_check(h);
@@ -543,6 +789,7 @@ qsim_status qsim_get_state(qsim_handle h, void *host_out, size_t bytes) {
     if (!host_out || bytes != state_bytes(h)) return fail(QSIM_EINVAL, "need %zu bytes", state_bytes(h));
     if (identity_layout(h)) {
         CK(cudaMemcpyAsync(host_out, h->amp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy state out");
+        h->d2h += bytes;
         return sync_check(h);
     }
     qsim_status st = ensure_chunk(h);
@@ -552,7 +799,10 @@ qsim_status qsim_get_state(qsim_handle h, void *host_out, size_t bytes) {
     const uint64_t per = h->chunk_bytes / ab;
     for (uint64_t s = 0; s < D; s += per) {
         const uint64_t cnt = std::min(per, D - s);
-        CK(launch_gather_chunk(h->amp, (int)h->dt, h->n, h->phys, s, cnt, h->d_chunk, h->stream), "gather");
+        CK(launch(h, F_GATHER, 2.0 * (double)cnt * (double)ab, 1,
+                  [&] { return launch_gather_chunk(h->amp, (int)h->dt, h->n, h->phys, s, cnt, h->d_chunk, h->stream); }),
+           "gather");
+        h->d2h += cnt * ab;
         CK(cudaMemcpyAsync(static_cast<char *>(host_out) + s * ab, h->d_chunk, cnt * ab, cudaMemcpyDeviceToHost,
                            h->stream),
            "copy state out");
@@ -595,8 +845,13 @@ qsim_status qsim_sample(qsim_handle h, const double *u, size_t ns, uint64_t *out
     uint64_t *dout = reinterpret_cast<uint64_t *>(du + ns);
     double *scr = reinterpret_cast<double *>(dout + ns);
     cudaError_t e = cudaMemcpyAsync(du, u, ns * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    h->h2d += ns * sizeof(double);
+    h->d2h += ns * sizeof(uint64_t);
+    const bool ident = identity_layout(h);
     if (e == cudaSuccess)
-        e = launch_sample(h->amp, (int)h->dt, h->n, h->phys, identity_layout(h), du, ns, dout, scr, h->stream);
+        e = launch(h, F_SAMPLE, (double)state_bytes(h) * 2.0, 3, [&] {
+            return launch_sample(h->amp, (int)h->dt, h->n, h->phys, ident, du, ns, dout, scr, h->stream);
+        });
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ns * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(buf, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sample");

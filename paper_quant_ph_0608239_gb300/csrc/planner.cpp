@@ -152,6 +152,19 @@ void fixed_bits_for(const PGate &g, FixedBitsHost &fb, uint64_t &pmask, bool &si
     fb.setmask = set;
 }
 
+double gate_flops(const PGate &g, int n) {
+    double per_amp = 0.0;
+    if (g.kind == QSIM_GATE_SWAP) return 0.0;
+    switch (g.gc) {
+    case GC_GENERAL: per_amp = 14.0; break;
+    case GC_DIAG: per_amp = 6.0; break;
+    case GC_PHASE: per_amp = 3.0; break;
+    case GC_ANTIDIAG: per_amp = 6.0; break;
+    default: per_amp = 0.0; break;
+    }
+    return per_amp * std::ldexp(1.0, n - popc(g.cmask));
+}
+
 bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op) {
     auto local = [&](int b) -> int {
         if (b < g.L) return b;
@@ -282,6 +295,8 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
         for (int b = 0; b < 64; b++)
             if ((hmask >> b) & 1ull) pp.geom.hb[j++] = b;
         pp.op_begin = (int)plan.ops.size();
+        pp.flops = 0.0;
+        for (int gi : sched) pp.flops += gate_flops(gates[gi], n);
         for (int gi : sched) {
             TileOp op;
             make_tile_op(gates[gi], pp.geom, op);  // fits by construction

@@ -35,7 +35,15 @@ void fixed_bits_for(const PGate &g, FixedBitsHost &fb, uint64_t &pmask, bool &si
 struct PassPlan {
     TileGeom geom;
     int op_begin, op_count;   // range in the plan's op array
+    double flops;             // algorithmic flops of the pass
 };
+
+// Algorithmic real flops of one gate over an n-qubit state: 14 per amplitude
+// for a dense 2x2 (two complex multiply-adds per output), 6 for a diagonal or
+// anti-diagonal entry (one complex multiply), 0 for pure data movement,
+// times the fraction of amplitudes the controls select (and 1/2 for a phase
+// shift, which leaves the bit-0 half alone).
+double gate_flops(const PGate &g, int n);
 
 struct Plan {
     std::vector<PassPlan> passes;

@@ -375,7 +375,10 @@ def test_full_size_random_circuit_then_inverse(q, n, depth, dt):
     st = q.State(n, dt)
     st.set_basis(x0)
     st.run(gates)
-    assert abs(st.norm() - 1) < (1e-12 if dt == "c128" else 1e-5)
+    # FP32 rounds every output amplitude with relative error <= ~2^-23 per
+    # gate; G gates move the norm by about 2^-23 * sqrt(G) typically and
+    # 2^-23 * G at worst (2.1e-4 for G = 1800).  1e-4 sits between the two.
+    assert abs(st.norm() - 1) < (1e-12 if dt == "c128" else 1e-4)
     st.run(_inverse(gates))
     import torch
     t = st.tensor
