@@ -385,7 +385,8 @@ def test_full_size_random_circuit_then_inverse(q, n, depth, dt):
     torch.cuda.synchronize()
     a0 = complex(t[x0].item())
     t[x0] = 0
-    rest = float(t.abs().max().item())
+    # max |a_i| over i != x0, in chunks (no full-size temporaries)
+    rest = max(float(t[i:i + (1 << 26)].abs().max().item()) for i in range(0, t.numel(), 1 << 26))
     tol = TOL[dt] * (1 if dt == "c128" else 2.5)
     assert abs(a0 - 1) < tol and rest < tol, (a0, rest)
     st.free()
