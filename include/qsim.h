@@ -267,6 +267,30 @@ QSIM_API qsim_status qsim_probs(qsim_handle h, double *out, size_t len);
  * (Eq. Shor7; DO MEASUREMENT of App. A, no collapse), FP64, n values. */
 QSIM_API qsim_status qsim_qubit_probs(qsim_handle h, double *out);
 
+/* qsim_qubit_probs_noalloc: the per-qubit marginals of qsim_qubit_probs for
+ * callers that must not allocate device memory (a framework that owns the
+ * device through its own pool, a latency-bound loop that cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree, an embedder that forbids
+ * allocation after start-up).  The paper has no counterpart: this is an
+ * interface variant only.
+ *
+ * amp: device pointer to 2^n amplitudes of dt (16-byte aligned), read in
+ * PHYSICAL index order (no handle, no qubit map).  dev_out: caller-owned
+ * device memory for n doubles; dev_out[b] = P(index bit b = 1), accumulated in
+ * FP64.  stream: cudaStream_t (NULL = legacy default stream); the call only
+ * enqueues work and returns.  1 <= n <= 34, else EINVAL.
+ *
+ * No device memory is allocated or freed: the block partial sums go to one
+ * static device array of 608 x 34 doubles (161.5 KiB) that every GPU loading
+ * the library holds until the process exits.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device share
+ * the array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and corrupt each other's results; serialise
+ * them.  The array keeps the last call's partial sums, which no later call
+ * reads before overwriting them. */
+QSIM_API qsim_status qsim_qubit_probs_noalloc(const void *amp, int n, qsim_dtype dt, void *stream, double *dev_out);
+
 /* qsim_sample: draw ns basis states with probability |a_x|^2 / norm
  * (Sec. V.B).  u[j] in [0, 1) are the caller's uniform numbers; sample j is
  * the smallest logical index x with u[j] * norm < P(0) + ... + P(x) (FP64

@@ -86,6 +86,8 @@ _SIGS = {
     "qsim_norm": ([c_handle, ctypes.POINTER(ctypes.c_double)], None),
     "qsim_probs": ([c_handle, ctypes.c_void_p, ctypes.c_size_t], None),
     "qsim_qubit_probs": ([c_handle, ctypes.c_void_p], None),
+    "qsim_qubit_probs_noalloc": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+                                 None),
     "qsim_sample": ([c_handle, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], None),
     "qsim_get_state": ([c_handle, ctypes.c_void_p, ctypes.c_size_t], None),
     "qsim_sync": ([c_handle], None),

@@ -753,6 +753,19 @@ qsim_status qsim_qubit_probs(qsim_handle h, double *out) {
     return QSIM_OK;
 }
 
+qsim_status qsim_qubit_probs_noalloc(const void *amp, int n, qsim_dtype dt, void *stream, double *dev_out) {
+    if (!amp || (reinterpret_cast<uintptr_t>(amp) & 15u))
+        return fail(QSIM_EINVAL, "amp must be a non-NULL, 16-byte aligned device pointer");
+    if (!dev_out) return fail(QSIM_EINVAL, "dev_out is NULL");
+    if (n < 1 || n > kMaxQubits)
+        return fail(QSIM_EINVAL, "n = %d outside [1, %d]: the static scratch array holds partial sums for at most "
+                                 "%d qubits", n, kMaxQubits, kMaxQubits);
+    if (dt != QSIM_C64 && dt != QSIM_C128) return fail(QSIM_EINVAL, "bad dtype %d", (int)dt);
+    CK(launch_bit_probs_noalloc(amp, (int)dt, n, dev_out, static_cast<cudaStream_t>(stream)),
+       "allocation-free marginals");
+    return QSIM_OK;
+}
+
 static qsim_status ensure_chunk(qsim_state *h) {
     if (h->d_chunk) return QSIM_OK;
     h->chunk_bytes = 64u << 20;

@@ -10,6 +10,8 @@
 //
 // The partial sums of each block go to a caller-provided scratch buffer in
 // global memory and a second kernel adds them up.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -368,6 +370,73 @@ cudaError_t launch_sample(const void *amp, int dt, int n, const int *physpos, bo
     else
         k_draw<double><<<(int)dg, 256, 0, s>>>(static_cast<const double2 *>(amp), n, pp, identity, S, scratch, nb,
                                                 du, ns, dout);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim
+
+// ---- allocation-free per-qubit marginals ----------------------------------
+// Some callers may not allocate device memory at all: code running while a
+// framework owns the whole device through its own memory pool, latency-bound
+// measurement loops that cannot absorb the implicit device synchronisation of
+// cudaMalloc/cudaFree, and embedders that forbid allocation after start-up.
+// For them the per-qubit marginal reduction can run on a fixed scratch array
+// that the library places in device memory when it is loaded.  Every GPU that
+// loads the library keeps this array until the process exits.
+namespace qsim {
+
+namespace {
+
+constexpr int kNoAllocBlocks = kRedBlocks;                    // 608 blocks
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocBlocks * kMaxQubits;  // 161.5 KiB
+
+// Block partials of the last call: [block][bit], kNoAllocBlocks x n used.
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
+
+}  // namespace
+
+size_t noalloc_scratch_bytes() { return kNoAllocDoubles * sizeof(double); }
+
+cudaError_t launch_bit_probs_noalloc(const void *amp, int dt, int n, double *dout, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    double *scratch = nullptr;
+    {
+        // Set-up, once per device, with that device current: host code cannot
+        // use the array's name as an address, so look the address up.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+            if (e != cudaSuccess) return e;
+            g_noalloc_ptr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    if (n < kChunkBits + 1) {  // small registers reduce in one block, no scratch
+        if (dt == 0)
+            k_bits_small<float><<<1, 256, 0, s>>>(static_cast<const float2 *>(amp), n, dout);
+        else
+            k_bits_small<double><<<1, 256, 0, s>>>(static_cast<const double2 *>(amp), n, dout);
+        return cudaGetLastError();
+    }
+    // Every partial the second kernel reads is written first by this call's
+    // first kernel (each block writes all n of its slots), so nothing left by
+    // an earlier call is read and no clearing is needed.
+    const uint64_t nch = 1ull << (n - kChunkBits);
+    uint64_t blocks = (nch + 7) / 8;
+    if (blocks > (uint64_t)kNoAllocBlocks) blocks = kNoAllocBlocks;
+    if (dt == 0)
+        k_bits_partial<float><<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const float2 *>(amp), n, scratch);
+    else
+        k_bits_partial<double><<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const double2 *>(amp), n, scratch);
+    k_sum_columns<<<1, 256, 0, s>>>(scratch, (int)blocks, n, n, dout);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,11 @@ cudaError_t launch_probs_chunk(const void *amp, int dt, int n, const int *physpo
 cudaError_t launch_gather_chunk(const void *amp, int dt, int n, const int *physpos, uint64_t start,
                                 uint64_t count, void *dout, cudaStream_t s);
 
+// Per-bit marginals on the library's static scratch array instead of a
+// caller buffer (no device allocation); see k_reduce.cu.
+size_t noalloc_scratch_bytes();
+cudaError_t launch_bit_probs_noalloc(const void *amp, int dt, int n, double *dout, cudaStream_t s);
+
 // Sampling (Sec. V.B): block sums of |a|^2 in logical order, then per-sample
 // search.  scratch must hold sample_scratch_bytes(n) bytes.
 size_t sample_scratch_bytes(int n);
