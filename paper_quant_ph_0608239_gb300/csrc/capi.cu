@@ -69,6 +69,10 @@ struct qsim_state {
     size_t chunk_bytes = 0;
     TileOp *h_ops = nullptr;   // pinned staging of gate programs
     size_t h_ops_cap = 0;
+    TilePhase *d_phases = nullptr;
+    size_t phases_cap = 0;
+    TilePhase *h_phases = nullptr;
+    size_t h_phases_cap = 0;
     cudaEvent_t upload_done = nullptr;
     // instrumentation
     bool prof = false;
@@ -139,6 +143,8 @@ static void release(qsim_state *h) {
     for (auto e : h->pool) cudaEventDestroy(e);
     if (h->upload_done) cudaEventDestroy(h->upload_done);
     if (h->h_ops) cudaFreeHost(h->h_ops);
+    if (h->h_phases) cudaFreeHost(h->h_phases);
+    if (h->d_phases) cudaFree(h->d_phases);
     if (h->owns && h->amp) cudaFree(h->amp);
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_res) cudaFree(h->d_res);
@@ -326,57 +332,77 @@ qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g) {
     return sweep_gate(h, pg);
 }
 
-static qsim_status ensure_ops(qsim_state *h, size_t nops) {
-    if (nops <= h->ops_cap) return QSIM_OK;
-    size_t cap = std::max(nops, (size_t)256);
-    if (h->d_ops) {
-        CK(cudaStreamSynchronize(h->stream), "sync before regrow");
-        cudaFree(h->d_ops);
-        h->d_ops = nullptr;
-        h->ops_cap = 0;
-    }
-    CK(cudaMalloc(&h->d_ops, cap * sizeof(TileOp)), "cudaMalloc ops");
-    h->ops_cap = cap;
-    return QSIM_OK;
-}
-
-static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &L) {
-    T = (o && o->tile_bits > 0) ? o->tile_bits : (h->dt == QSIM_C64 ? 12 : 11);
+// Tile shape: the register-blocked kernel takes T = 12 (or 13 for
+// complex64) when n >= T; other tile sizes use the shared-memory kernel.
+static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &L, int &RB) {
+    T = (o && o->tile_bits > 0) ? o->tile_bits : 12;
     const int Tmax = h->dt == QSIM_C64 ? 14 : 13;
     if (T > Tmax) T = Tmax;
     if (T < 2) T = 2;
-    L = h->dt == QSIM_C64 ? 5 : 4;
+    RB = (tile2_supported((int)h->dt, T) && h->n >= T) ? T - 8 : 0;
+    L = RB ? 5 : (h->dt == QSIM_C64 ? 5 : 4);
     if (T - L > 10) L = T - 10;
     if (L >= T) L = T - 2;
     if (L < 1) L = 1;
 }
 
-// Copy a gate program to device memory through the handle's pinned staging
-// buffer (the previous upload must have left the staging buffer first).
-static qsim_status upload_ops(qsim_state *h, const std::vector<TileOp> &ops) {
-    qsim_status st = ensure_ops(h, ops.size());
-    if (st != QSIM_OK) return st;
-    if (!h->upload_done) CK(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming), "event");
-    CK(cudaEventSynchronize(h->upload_done), "wait staging");
-    if (ops.size() > h->h_ops_cap) {
-        if (h->h_ops) cudaFreeHost(h->h_ops);
-        h->h_ops = nullptr;
-        h->h_ops_cap = 0;
-        const size_t cap = std::max(ops.size(), (size_t)1024);
-        CK(cudaMallocHost(&h->h_ops, cap * sizeof(TileOp)), "cudaMallocHost staging");
-        h->h_ops_cap = cap;
+}  // extern "C"
+
+template <class T>
+static qsim_status stage(qsim_state *h, const std::vector<T> &v, T *&dbuf, size_t &dcap, T *&hbuf, size_t &hcap,
+                         const char *what) {
+    if (v.empty()) return QSIM_OK;
+    if (v.size() > dcap) {
+        if (dbuf) {
+            CK(cudaStreamSynchronize(h->stream), "sync before regrow");
+            cudaFree(dbuf);
+            dbuf = nullptr;
+            dcap = 0;
+        }
+        const size_t cap = std::max(v.size(), (size_t)256);
+        CK(cudaMalloc(&dbuf, cap * sizeof(T)), what);
+        dcap = cap;
     }
-    std::memcpy(h->h_ops, ops.data(), ops.size() * sizeof(TileOp));
-    CK(cudaMemcpyAsync(h->d_ops, h->h_ops, ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice, h->stream),
-       "upload tile ops");
-    CK(cudaEventRecord(h->upload_done, h->stream), "event record");
-    h->h2d += ops.size() * sizeof(TileOp);
+    if (v.size() > hcap) {
+        if (hbuf) cudaFreeHost(hbuf);
+        hbuf = nullptr;
+        hcap = 0;
+        const size_t cap = std::max(v.size(), (size_t)1024);
+        CK(cudaMallocHost(&hbuf, cap * sizeof(T)), "cudaMallocHost staging");
+        hcap = cap;
+    }
+    std::memcpy(hbuf, v.data(), v.size() * sizeof(T));
+    CK(cudaMemcpyAsync(dbuf, hbuf, v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream), what);
+    h->h2d += v.size() * sizeof(T);
     return QSIM_OK;
 }
 
-static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *d_ops) {
+extern "C" {
+
+static qsim_status upload_program(qsim_state *h, const Plan &plan) {
+    if (!h->upload_done) CK(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming), "event");
+    CK(cudaEventSynchronize(h->upload_done), "wait staging");
+    qsim_status st = stage(h, plan.ops, h->d_ops, h->ops_cap, h->h_ops, h->h_ops_cap, "upload tile ops");
+    if (st != QSIM_OK) return st;
+    st = stage(h, plan.phases, h->d_phases, h->phases_cap, h->h_phases, h->h_phases_cap, "upload tile phases");
+    if (st != QSIM_OK) return st;
+    CK(cudaEventRecord(h->upload_done, h->stream), "event record");
+    return QSIM_OK;
+}
+
+static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *d_ops, const TilePhase *d_phases) {
     const double pass_bytes = 2.0 * (double)state_bytes(h);
     for (const PassPlan &pp : plan.passes) {
+        if (pp.phase_count > 0) {
+            CK(launch(h, F_TILE, pass_bytes, 1,
+                      [&] {
+                          return launch_tile_pass2(h->amp, (int)h->dt, pp.geom, d_phases + pp.phase_begin,
+                                                   pp.phase_count, d_ops, h->d_err, h->sm_count, h->stream);
+                      },
+                      pp.flops),
+               "register tile pass");
+            continue;
+        }
         if (pp.op_count == 0) continue;
         CK(launch(h, F_TILE, pass_bytes, 1,
                   [&] {
@@ -407,6 +433,7 @@ struct qsim_plan_s {
     std::vector<PGate> sweeps;   // PERGATE mode
     Plan plan;                   // FUSED mode
     TileOp *d_ops = nullptr;
+    TilePhase *d_phases = nullptr;
     qsim_plan_stats stats{};
 };
 
@@ -439,11 +466,11 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         return QSIM_OK;
     }
-    int T, L;
-    tile_defaults(h, &o, T, L);
-    plan_tiles(pg, h->n, T, L, P.plan);
+    int T, L, RB;
+    tile_defaults(h, &o, T, L, RB);
+    plan_tiles(pg, h->n, T, L, P.plan, RB);
     for (const PassPlan &pp : P.plan.passes)
-        if (pp.op_count) P.stats.passes++;
+        if (pp.op_count || pp.phase_count) P.stats.passes++;
     P.stats.ops = (int)P.plan.ops.size();
     P.stats.tile_bits = P.plan.passes.empty() ? 0 : P.plan.passes[0].geom.L + P.plan.passes[0].geom.H;
     P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
@@ -451,7 +478,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     return QSIM_OK;
 }
 
-static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops) {
+static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops, const TilePhase *d_phases) {
     if (P.mode == QSIM_MODE_PERGATE) {
         for (const PGate &g : P.sweeps) {
             qsim_status st = sweep_gate(h, g);
@@ -459,7 +486,7 @@ static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *
         }
         return QSIM_OK;
     }
-    return launch_passes(h, P.plan, d_ops);
+    return launch_passes(h, P.plan, d_ops, d_phases);
 }
 
 qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts) {
@@ -468,10 +495,10 @@ qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, c
     qsim_status st = build_plan(h, gates, ng, opts, P);
     if (st != QSIM_OK) return st;
     if (P.mode == QSIM_MODE_FUSED && !P.plan.ops.empty()) {
-        st = upload_ops(h, P.plan.ops);
+        st = upload_program(h, P.plan);
         if (st != QSIM_OK) return st;
     }
-    return run_built(h, P, h->d_ops);
+    return run_built(h, P, h->d_ops, h->d_phases);
 }
 
 qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
@@ -485,11 +512,18 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
         cudaError_t e = cudaMalloc(&P->d_ops, P->plan.ops.size() * sizeof(TileOp));
         if (e == cudaSuccess)
             e = cudaMemcpy(P->d_ops, P->plan.ops.data(), P->plan.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !P->plan.phases.empty()) {
+            e = cudaMalloc(&P->d_phases, P->plan.phases.size() * sizeof(TilePhase));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(P->d_phases, P->plan.phases.data(), P->plan.phases.size() * sizeof(TilePhase),
+                               cudaMemcpyHostToDevice);
+        }
         if (e != cudaSuccess) st = cuda_fail(e, "upload plan");
-        else h->h2d += P->plan.ops.size() * sizeof(TileOp);
+        else h->h2d += P->plan.ops.size() * sizeof(TileOp) + P->plan.phases.size() * sizeof(TilePhase);
     }
     if (st != QSIM_OK) {
         if (P->d_ops) cudaFree(P->d_ops);
+        if (P->d_phases) cudaFree(P->d_phases);
         delete P;
         return st;
     }
@@ -502,7 +536,7 @@ qsim_status qsim_plan_run(qsim_handle h, qsim_plan p) {
     if (!p) return fail(QSIM_EINVAL, "null plan");
     if (p->n != h->n || p->dt != h->dt || std::memcmp(p->phys, h->phys, sizeof(int) * h->n) != 0)
         return fail(QSIM_EINVAL, "plan was made for another size, dtype or qubit layout");
-    return run_built(h, *p, p->d_ops);
+    return run_built(h, *p, p->d_ops, p->d_phases);
 }
 
 qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
@@ -513,10 +547,9 @@ qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
 
 qsim_status qsim_plan_free(qsim_plan p) {
     if (!p) return QSIM_OK;
-    if (p->d_ops) {
-        cudaDeviceSynchronize();
-        cudaFree(p->d_ops);
-    }
+    if (p->d_ops || p->d_phases) cudaDeviceSynchronize();
+    if (p->d_ops) cudaFree(p->d_ops);
+    if (p->d_phases) cudaFree(p->d_phases);
     delete p;
     return QSIM_OK;
 }
@@ -618,8 +651,11 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
         return sweep_gate(h, pg);
     }
     // K pairs in one pass: a tile holding all 2K bits, one in-tile permutation.
-    int T, L;
-    tile_defaults(h, nullptr, T, L);
+    int T, L, RB;
+    qsim_opts po;
+    qsim_default_opts(&po);
+    po.tile_bits = h->dt == QSIM_C64 ? 12 : 11;  // shared-memory kernel: one in-tile permutation
+    tile_defaults(h, &po, T, L, RB);
     uint64_t need = 0;
     for (int i = 0; i < K; i++) need |= (1ull << l[i]) | (1ull << hb[i]);
     if (h->n <= T) {
@@ -670,9 +706,9 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
     pp.op_begin = 0;
     pp.op_count = 1;
     plan.passes.push_back(pp);
-    qsim_status st = upload_ops(h, plan.ops);
+    qsim_status st = upload_program(h, plan);
     if (st != QSIM_OK) return st;
-    return launch_passes(h, plan, h->d_ops);
+    return launch_passes(h, plan, h->d_ops, h->d_phases);
 }
 
 static qsim_status check_pairs(const qsim_state *h, int K, const int *a, const int *b) {

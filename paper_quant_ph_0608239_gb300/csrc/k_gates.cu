@@ -43,6 +43,11 @@ __device__ __forceinline__ void pair_update(amp_t<R> &x, amp_t<R> &y, const amp_
         amp_t<R> b = cmul2<R>(u[2], x, u[3], y);
         x = a;
         y = b;
+    } else if (GC == GC_REAL) {
+        amp_t<R> a = mk<R>(fma(u[0].x, x.x, u[1].x * y.x), fma(u[0].x, x.y, u[1].x * y.y));
+        amp_t<R> b = mk<R>(fma(u[2].x, x.x, u[3].x * y.x), fma(u[2].x, x.y, u[3].x * y.y));
+        x = a;
+        y = b;
     } else if (GC == GC_ANTIDIAG) {
         amp_t<R> a = cmul<R>(u[1], y);
         amp_t<R> b = cmul<R>(u[2], x);
@@ -202,6 +207,7 @@ cudaError_t pairs_np(void *amp, uint64_t W, const FixedBits &fb, uint64_t pmask,
     amp_t<R> *a = static_cast<amp_t<R> *>(amp);
     switch (gc) {
     case GC_GENERAL: k_pairs<R, GC_GENERAL, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
+    case GC_REAL: k_pairs<R, GC_REAL, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
     case GC_ANTIDIAG: k_pairs<R, GC_ANTIDIAG, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
     case GC_EXCHANGE: k_pairs<R, GC_EXCHANGE, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, U); break;
     default: return cudaErrorInvalidValue;

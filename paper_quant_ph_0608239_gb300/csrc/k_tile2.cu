@@ -1,0 +1,371 @@
+// k_tile2.cu -- register-blocked tile passes.
+//
+// Same pass structure as k_tile.cu (a tile of 2^T amplitudes = the L low
+// index bits plus H chosen high bits, fetched and written back with bulk
+// asynchronous copies), but the gate program runs in registers:
+//
+//   local bit 0..4          lane bits: a gate on them pairs amplitudes held by
+//                           lanes l and l ^ 2^t of one warp (warp shuffles)
+//   RB of the bits >= 5     register bits: a gate on them pairs two registers
+//                           of one thread
+//   the other 3 bits >= 5   warp bits (8 warps)
+//
+// The program is cut into phases; a phase loads the tile from shared memory
+// into registers under its own choice of register bits, applies its gates,
+// and stores back (optionally to permuted positions, which is how quantum SWAP
+// gates and qubit interchanges are applied).  T = RB + 8.
+//
+// complex64 computes in FP32.  complex128 computes in double-float (FP32
+// pairs, df64.cuh): the tile arrives as IEEE doubles, the first phase converts
+// them with integer operations, later phases keep the double-float form in
+// shared memory, and the last phase converts back.
+#include "common.cuh"
+#include "df64.cuh"
+#include "kernels.hpp"
+#include "ptx.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreads2 = 256;
+constexpr int kMaxH2 = 10;
+constexpr int kMaxCopyShift2 = 14;
+constexpr long long kWaitBudget2 = 4000000000ll;
+
+// ---------------------------------------------------------- amplitude types
+template <bool C128> struct AmpT;
+template <> struct AmpT<false> {
+    using V = float2;
+    using S = float2;  // shared-memory element
+};
+template <> struct AmpT<true> {
+    using V = dcx;
+    using S = double2;
+};
+
+// coefficients of one 2x2 entry
+template <bool C128> struct Coef;
+template <> struct Coef<false> { float2 c; };
+template <> struct Coef<true> { dcx c; };
+
+__device__ __forceinline__ float2 coef64(const TileOp &op, int k) { return make_float2(op.uh[2 * k], op.uh[2 * k + 1]); }
+__device__ __forceinline__ dcx coef128(const TileOp &op, int k) {
+    return dcx{df{op.uh[2 * k], op.ul[2 * k]}, df{op.uh[2 * k + 1], op.ul[2 * k + 1]}};
+}
+
+// ---- arithmetic on one amplitude type
+__device__ __forceinline__ float2 vmul(float2 u, float2 a) { return cmul<float>(u, a); }
+__device__ __forceinline__ float2 vmul2(float2 u, float2 a, float2 v, float2 b) { return cmul2<float>(u, a, v, b); }
+__device__ __forceinline__ float2 vrmul2(float2 u, float2 a, float2 v, float2 b) {
+    return make_float2(fmaf(u.x, a.x, v.x * b.x), fmaf(u.x, a.y, v.x * b.y));
+}
+__device__ __forceinline__ dcx vmul(const dcx &u, const dcx &a) { return dcx_mul(u, a); }
+__device__ __forceinline__ dcx vmul2(const dcx &u, const dcx &a, const dcx &v, const dcx &b) {
+    return dcx_mul2(u, a, v, b);
+}
+__device__ __forceinline__ dcx vrmul2(const dcx &u, const dcx &a, const dcx &v, const dcx &b) {
+    return dcx_rmul2(u.re, a, v.re, b);
+}
+
+__device__ __forceinline__ float2 shfl_x(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ dcx shfl_x(const dcx &v, int m) {
+    return dcx{df{__shfl_xor_sync(0xffffffffu, v.re.h, m), __shfl_xor_sync(0xffffffffu, v.re.l, m)},
+               df{__shfl_xor_sync(0xffffffffu, v.im.h, m), __shfl_xor_sync(0xffffffffu, v.im.l, m)}};
+}
+
+// ---- shared-memory formats
+// complex64: float2.  complex128: IEEE double2 (fmt 0) or double-float
+// (fmt 1: re.h, re.l, im.h, im.l as four floats in the same 16 bytes).
+__device__ __forceinline__ float2 ld_amp(const float2 *t, uint32_t i, int) { return t[i]; }
+__device__ __forceinline__ void st_amp(float2 *t, uint32_t i, float2 v, int) { t[i] = v; }
+__device__ __forceinline__ dcx ld_amp(const double2 *t, uint32_t i, int fmt) {
+    if (fmt == 0) {
+        const double2 d = t[i];
+        return dcx{df_from_double(d.x), df_from_double(d.y)};
+    }
+    const float4 f = reinterpret_cast<const float4 *>(t)[i];
+    return dcx{df{f.x, f.y}, df{f.z, f.w}};
+}
+__device__ __forceinline__ void st_amp(double2 *t, uint32_t i, const dcx &v, int fmt) {
+    if (fmt == 0) {
+        t[i] = make_double2(df_to_double(v.re), df_to_double(v.im));
+    } else {
+        reinterpret_cast<float4 *>(t)[i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+    }
+}
+
+// ---- gate application in registers
+enum { PK_GENERAL = 0, PK_REAL = 1, PK_ANTI = 2, PK_EXCH = 3 };
+
+template <int RB, int K, int PK, typename V>
+__device__ __forceinline__ void pair_reg(V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        if (j & (1 << K)) continue;
+        const int j1 = j | (1 << K);
+        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        const V a = v[j], b = v[j1];
+        if (PK == PK_GENERAL) {
+            v[j] = vmul2(u[0], a, u[1], b);
+            v[j1] = vmul2(u[2], a, u[3], b);
+        } else if (PK == PK_REAL) {
+            v[j] = vrmul2(u[0], a, u[1], b);
+            v[j1] = vrmul2(u[2], a, u[3], b);
+        } else if (PK == PK_ANTI) {
+            v[j] = vmul(u[1], b);
+            v[j1] = vmul(u[2], a);
+        } else {
+            v[j] = b;
+            v[j1] = a;
+        }
+    }
+}
+
+template <int RB, int PK, typename V>
+__device__ __forceinline__ void pair_reg_dispatch(int k, V (&v)[1 << RB], const V (&u)[4], bool thr_ok,
+                                                  uint32_t creg) {
+    switch (k) {
+    case 0: pair_reg<RB, 0, PK>(v, u, thr_ok, creg); break;
+    case 1: pair_reg<RB, 1, PK>(v, u, thr_ok, creg); break;
+    case 2: pair_reg<RB, 2, PK>(v, u, thr_ok, creg); break;
+    case 3: pair_reg<RB, 3, PK>(v, u, thr_ok, creg); break;
+    default:
+        if constexpr (RB > 4) pair_reg<RB, (RB > 4 ? 4 : 0), PK>(v, u, thr_ok, creg);
+        break;
+    }
+}
+
+// target on lane bit t: partner in lane ^ 2^t; each lane computes its own
+// output with the coefficients of its row.
+template <int RB, int PK, typename V>
+__device__ __forceinline__ void pair_lane(int t, V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg,
+                                          int lane) {
+    const bool upper = (lane >> t) & 1;
+    const V c0 = upper ? u[3] : u[0];  // coefficient of the lane's own amplitude
+    const V c1 = upper ? u[2] : u[1];  // coefficient of the partner's amplitude
+    const int m = 1 << t;
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        const V w = shfl_x(v[j], m);
+        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        if (PK == PK_GENERAL) v[j] = vmul2(c0, v[j], c1, w);
+        else if (PK == PK_REAL) v[j] = vrmul2(c0, v[j], c1, w);
+        else if (PK == PK_ANTI) v[j] = vmul(c1, w);
+        else v[j] = w;
+    }
+}
+
+template <bool C128>
+__device__ __forceinline__ typename AmpT<C128>::V coef(const TileOp &op, int k);
+template <> __device__ __forceinline__ float2 coef<false>(const TileOp &op, int k) { return coef64(op, k); }
+template <> __device__ __forceinline__ dcx coef<true>(const TileOp &op, int k) { return coef128(op, k); }
+
+template <bool C128, int RB>
+__device__ __forceinline__ void apply_op2(const TileOp &op, typename AmpT<C128>::V (&v)[1 << RB], uint32_t thr_idx,
+                                          int lane, uint64_t base) {
+    using V = typename AmpT<C128>::V;
+    if ((base & op.gcmask) != op.gcmask) return;
+    const bool thr_ok = (thr_idx & op.lcthr) == op.lcthr;
+    const uint32_t creg = op.creg;
+    const int kind = op.kind;
+    if (kind == TOP_DIAG || kind == TOP_PHASE || kind == TOP_DIAG_G) {
+        const V u0 = coef<C128>(op, 0), u1 = coef<C128>(op, 3);
+        if (kind == TOP_DIAG_G) {
+            const V f = ((base >> op.tl) & 1ull) ? u1 : u0;
+#pragma unroll
+            for (int j = 0; j < (1 << RB); j++)
+                if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
+            return;
+        }
+        const int rk = op.regk;
+        const bool tbit = (thr_idx >> op.tl) & 1u;  // used when the target is a lane or warp bit
+#pragma unroll
+        for (int j = 0; j < (1 << RB); j++) {
+            if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+            const bool bit = rk >= 0 ? ((j >> rk) & 1) : tbit;
+            if (kind == TOP_PHASE) {
+                if (bit) v[j] = vmul(u1, v[j]);
+            } else {
+                v[j] = vmul(bit ? u1 : u0, v[j]);
+            }
+        }
+        return;
+    }
+    V u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) u[k] = coef<C128>(op, k);
+    const int pk = op.pk;  // pair kind chosen by the host
+    if (op.regk >= 0) {
+        switch (pk) {
+        case PK_GENERAL: pair_reg_dispatch<RB, PK_GENERAL>(op.regk, v, u, thr_ok, creg); break;
+        case PK_REAL: pair_reg_dispatch<RB, PK_REAL>(op.regk, v, u, thr_ok, creg); break;
+        case PK_ANTI: pair_reg_dispatch<RB, PK_ANTI>(op.regk, v, u, thr_ok, creg); break;
+        default: pair_reg_dispatch<RB, PK_EXCH>(op.regk, v, u, thr_ok, creg); break;
+        }
+    } else {
+        switch (pk) {
+        case PK_GENERAL: pair_lane<RB, PK_GENERAL>(op.tl, v, u, thr_ok, creg, lane); break;
+        case PK_REAL: pair_lane<RB, PK_REAL>(op.tl, v, u, thr_ok, creg, lane); break;
+        case PK_ANTI: pair_lane<RB, PK_ANTI>(op.tl, v, u, thr_ok, creg, lane); break;
+        default: pair_lane<RB, PK_EXCH>(op.tl, v, u, thr_ok, creg, lane); break;
+        }
+    }
+}
+
+// local index of register j of a thread: its lane/warp bits plus the bits
+// of j scattered onto the register slots
+template <int RB>
+__device__ __forceinline__ uint32_t reg_index(uint32_t thr_idx, const uint32_t (&rbit)[RB], int j) {
+    uint32_t x = thr_idx;
+#pragma unroll
+    for (int k = 0; k < RB; k++)
+        if ((j >> k) & 1) x |= rbit[k];
+    return x;
+}
+
+template <bool C128, int RB>
+__global__ void __launch_bounds__(kThreads2, 2) k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g,
+                                                     const TilePhase *__restrict__ phases, int nphases,
+                                                     const TileOp *__restrict__ ops, uint32_t *err,
+                                                     uint64_t ntiles) {
+    using S = typename AmpT<C128>::S;
+    using V = typename AmpT<C128>::V;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S *t = reinterpret_cast<S *>(smem_raw);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint64_t runoff[1 << kMaxH2];
+    __shared__ int abort_flag;
+    const int L = g.L, H = g.H, T = L + H;
+    const uint32_t TS = 1u << T;
+    const uint32_t nruns = 1u << H;
+    const int amp_shift = sizeof(S) == 8 ? 3 : 4;
+    const int sub_L = L + amp_shift > kMaxCopyShift2 ? kMaxCopyShift2 - amp_shift : L;
+    const int sub_shift = L - sub_L;
+    const uint32_t ncopies = nruns << sub_shift;
+    const uint32_t copy_bytes = 1u << (sub_L + amp_shift);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
+        uint64_t o = 0;
+        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
+        runoff[j] = o;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    uint32_t parity = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint64_t base = tile << L;
+        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, TS * (uint32_t)sizeof(S));
+            __syncwarp();
+            for (uint32_t c = threadIdx.x; c < ncopies; c += 32) {
+                const uint32_t j = c >> sub_shift, s = c & ((1u << sub_shift) - 1u);
+                bulk_g2s(t + ((size_t)j << L) + ((size_t)s << sub_L), a + (base | runoff[j]) + ((size_t)s << sub_L),
+                         copy_bytes, &bar);
+            }
+        }
+        if (!mbar_wait_bounded(&bar, parity, kWaitBudget2)) {
+            atomicExch(err, kErrTimeout);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) {
+            mbar_wait_bounded(&bar, parity, kWaitBudget2);
+            return;
+        }
+        parity ^= 1u;
+
+        for (int p = 0; p < nphases; p++) {
+            const TilePhase &ph = phases[p];
+            uint32_t thr_idx = (uint32_t)lane;
+#pragma unroll
+            for (int k = 0; k < 3; k++) thr_idx |= (uint32_t)((warp >> k) & 1) << ph.wb[k];
+            uint32_t rbit[RB];
+#pragma unroll
+            for (int k = 0; k < RB; k++) rbit[k] = 1u << ph.rb[k];
+            V v[1 << RB];
+            const int lfmt = (C128 && p == 0) ? 0 : 1, sfmt = (C128 && p == nphases - 1) ? 0 : 1;
+#pragma unroll
+            for (int j = 0; j < (1 << RB); j++) v[j] = ld_amp(t, reg_index<RB>(thr_idx, rbit, j), lfmt);
+            for (int o = ph.op_begin; o < ph.op_begin + ph.op_count; o++)
+                apply_op2<C128, RB>(ops[o], v, thr_idx, lane, base);
+            if (ph.nperm) {
+                __syncthreads();  // every thread has read its inputs before any permuted write
+#pragma unroll
+                for (int j = 0; j < (1 << RB); j++) {
+                    const uint32_t x = reg_index<RB>(thr_idx, rbit, j);
+                    uint32_t y = x;
+                    for (int k = 0; k < ph.nperm; k++) {
+                        const uint32_t bl = (x >> ph.pl[k]) & 1u, bh = (x >> ph.ph[k]) & 1u;
+                        y &= ~((1u << ph.pl[k]) | (1u << ph.ph[k]));
+                        y |= (bl << ph.ph[k]) | (bh << ph.pl[k]);
+                    }
+                    st_amp(t, y, v[j], sfmt);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < (1 << RB); j++) st_amp(t, reg_index<RB>(thr_idx, rbit, j), v[j], sfmt);
+            }
+            __syncthreads();
+        }
+
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            for (uint32_t c = threadIdx.x; c < ncopies; c += 32) {
+                const uint32_t j = c >> sub_shift, s = c & ((1u << sub_shift) - 1u);
+                bulk_s2g(a + (base | runoff[j]) + ((size_t)s << sub_L), t + ((size_t)j << L) + ((size_t)s << sub_L),
+                         copy_bytes);
+            }
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) bulk_wait_all();
+}
+
+template <bool C128, int RB>
+cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int nphases, const TileOp *ops,
+                    uint32_t *err, int sm_count, cudaStream_t s) {
+    using S = typename AmpT<C128>::S;
+    const int T = g.L + g.H;
+    const size_t smem = sizeof(S) << T;
+    const uint64_t ntiles = 1ull << (g.n - T);
+    int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    cudaError_t e = cudaFuncSetAttribute(k_tile2<C128, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile2<C128, RB><<<(unsigned)grid, kThreads2, smem, s>>>(static_cast<S *>(amp), g, phases, nphases, ops, err,
+                                                               ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tile2_supported(int dt, int T) { return T == 12 || (dt == 0 && T == 13); }
+
+cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePhase *phases, int nphases,
+                              const TileOp *ops, uint32_t *err, int sm_count, cudaStream_t s) {
+    const int T = g.L + g.H;
+    if (!tile2_supported(dt, T) || g.L < 5 || g.H > kMaxH2 || T > g.n) return cudaErrorInvalidValue;
+    if (dt == 0) {
+        if (T == 13) return launch2<false, 5>(amp, g, phases, nphases, ops, err, sm_count, s);
+        return launch2<false, 4>(amp, g, phases, nphases, ops, err, sm_count, s);
+    }
+    return launch2<true, 4>(amp, g, phases, nphases, ops, err, sm_count, s);
+}
+
+}  // namespace qsim

@@ -18,7 +18,8 @@ enum GateClass : int32_t {
     GC_DIAG = 1,      // diag(u00, u11): every amplitude scaled, no partner
     GC_PHASE = 2,     // diag(1, u11): only the bit-1 half scaled (Eq. NUM5)
     GC_ANTIDIAG = 3,  // a'0 = u01 a1, a'1 = u10 a0
-    GC_EXCHANGE = 4   // a'0 = a1, a'1 = a0 (CNOT / Toffoli flip, Eqs. NUM6, NUM8)
+    GC_EXCHANGE = 4,  // a'0 = a1, a'1 = a0 (CNOT / Toffoli flip, Eqs. NUM6, NUM8)
+    GC_REAL = 5       // dense 2x2 with real entries (H, Y, Ybar): half the multiplies
 };
 
 struct Mat2 {
@@ -53,8 +54,29 @@ struct TileOp {
     double u[8];
     int8_t pl[8];
     int8_t ph[8];
+    // register-blocked kernel (k_tile2.cu), filled by the planner per phase
+    int8_t regk;      // register slot of the target bit; -1 if it is a lane/warp bit (or outside the tile)
+    int8_t pk;        // pair kind: 0 general, 1 real, 2 anti-diagonal, 3 exchange
+    int8_t pad8[2];
+    uint32_t creg;    // controls among the register slots (bit k = slot k)
+    uint32_t lcthr;   // controls among the lane and warp bits (local index mask)
+    uint32_t pad32;
+    float uh[8];      // u[] rounded to float (complex64) ...
+    float ul[8];      // ... and the remainders (complex128 double-float coefficients)
 };
-static_assert(sizeof(TileOp) == 112, "TileOp layout");
+static_assert(sizeof(TileOp) == 192, "TileOp layout");
+
+// One phase of a register-blocked tile program: which local bits are held in
+// registers, the ops it applies, and an optional permutation of local bit
+// pairs applied when the phase stores back (quantum SWAP gates, interchanges).
+struct TilePhase {
+    int32_t op_begin, op_count;
+    int8_t rb[8];     // register slot k -> local bit (>= 5)
+    int8_t wb[8];     // warp bit k -> local bit (>= 5)
+    int32_t nperm;
+    int8_t pl[8];
+    int8_t ph[8];
+};
 
 constexpr int kMaxTileHigh = 16;
 struct TileGeom {
@@ -93,6 +115,13 @@ cudaError_t launch_dense(void *amp, int dt, int n, int k, const int *qpos, const
 cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp *ops, int nops,
                              const void *dmat, uint32_t *err, int sm_count, cudaStream_t s);
 size_t tile_smem_bytes(int dt, int T);
+
+// Register-blocked tile pass (k_tile2.cu): T = 8 + register bits, T = 12
+// (both precisions) or 13 (complex64), L >= 5 (the lane bits are the physical
+// bits 0..4).
+bool tile2_supported(int dt, int T);
+cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePhase *phases, int nphases,
+                              const TileOp *ops, uint32_t *err, int sm_count, cudaStream_t s);
 
 // Reductions (FP64 accumulation).  scratch: device buffer of at least
 // reduce_scratch_bytes(n) bytes.

@@ -66,7 +66,8 @@ int classify(const Mat2 &M) {
     const bool diag0 = M.u[0] == 0 && M.u[1] == 0 && M.u[6] == 0 && M.u[7] == 0;
     if (off0) return (M.u[0] == 1 && M.u[1] == 0) ? GC_PHASE : GC_DIAG;
     if (diag0) return (M.u[2] == 1 && M.u[3] == 0 && M.u[4] == 1 && M.u[5] == 0) ? GC_EXCHANGE : GC_ANTIDIAG;
-    return GC_GENERAL;
+    const bool real = M.u[1] == 0 && M.u[3] == 0 && M.u[5] == 0 && M.u[7] == 0;
+    return real ? GC_REAL : GC_GENERAL;
 }
 
 bool prepare_gate(const qsim_gate &g, int n, const int *phys, PGate &out, std::string &msg) {
@@ -157,6 +158,7 @@ double gate_flops(const PGate &g, int n) {
     if (g.kind == QSIM_GATE_SWAP) return 0.0;
     switch (g.gc) {
     case GC_GENERAL: per_amp = 14.0; break;
+    case GC_REAL: per_amp = 6.0; break;
     case GC_DIAG: per_amp = 6.0; break;
     case GC_PHASE: per_amp = 3.0; break;
     case GC_ANTIDIAG: per_amp = 6.0; break;
@@ -180,7 +182,13 @@ bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op) {
         if (lb >= 0) op.lcmask |= 1u << lb;
         else op.gcmask |= 1ull << b;
     }
-    for (int k = 0; k < 8; k++) op.u[k] = pg.U.u[k];
+    for (int k = 0; k < 8; k++) {
+        op.u[k] = pg.U.u[k];
+        op.uh[k] = (float)pg.U.u[k];
+        op.ul[k] = (float)(pg.U.u[k] - (double)op.uh[k]);
+    }
+    op.regk = -1;
+    op.pk = pg.gc == GC_REAL ? 1 : pg.gc == GC_ANTIDIAG ? 2 : pg.gc == GC_EXCHANGE ? 3 : 0;
     if (pg.kind == QSIM_GATE_SWAP) {
         const int a = local(pg.t0), b = local(pg.t1);
         if (a < 0 || b < 0) return false;
@@ -201,7 +209,8 @@ bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op) {
             op.tl = pg.t0;
         }
         return true;
-    case GC_GENERAL: op.kind = TOP_GENERAL; break;
+    case GC_GENERAL:
+    case GC_REAL: op.kind = TOP_GENERAL; break;
     case GC_ANTIDIAG: op.kind = TOP_ANTIDIAG; break;
     default: op.kind = TOP_EXCHANGE; break;
     }
@@ -227,10 +236,129 @@ uint64_t touched_bits(const PGate &g) {
 
 }  // namespace
 
-void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan) {
+namespace {
+
+// One item of a pass program before phasing: an op, or a permutation of
+// local bit pairs (an uncontrolled SWAP gate or an interchange).
+struct Item {
+    bool perm;
+    TileOp op;
+    int np;
+    int8_t pl[8], ph[8];
+};
+
+bool needs_register(const TileOp &op) {
+    return (op.kind == TOP_GENERAL || op.kind == TOP_ANTIDIAG || op.kind == TOP_EXCHANGE) && op.tl >= 5;
+}
+
+}  // namespace
+
+void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vector<TileOp> &ops_out,
+                  std::vector<TilePhase> &phases_out) {
+    // expand SWAP gates: uncontrolled ones become store permutations, controlled
+    // ones three multi-controlled bit flips (each applied only where the controls
+    // are 1, so the SWAP happens exactly there)
+    std::vector<Item> items;
+    for (const TileOp &o : pass_ops) {
+        if (o.kind == TOP_SWAPGATE && o.lcmask == 0 && o.gcmask == 0) {
+            Item it{};
+            it.perm = true;
+            it.np = 1;
+            it.pl[0] = (int8_t)o.tl;
+            it.ph[0] = (int8_t)o.tl2;
+            items.push_back(it);
+        } else if (o.kind == TOP_SWAPGATE) {
+            const int a = o.tl, b = o.tl2;
+            for (int r = 0; r < 3; r++) {
+                Item it{};
+                it.perm = false;
+                it.op = o;
+                it.op.kind = TOP_EXCHANGE;
+                it.op.pk = 3;
+                const int tgt = (r == 1) ? a : b, ctl = (r == 1) ? b : a;
+                it.op.tl = tgt;
+                it.op.tl2 = -1;
+                it.op.lcmask = o.lcmask | (1u << ctl);
+                items.push_back(it);
+            }
+        } else if (o.kind == TOP_PERM) {
+            Item it{};
+            it.perm = true;
+            it.np = o.nperm;
+            for (int k = 0; k < o.nperm; k++) {
+                it.pl[k] = o.pl[k];
+                it.ph[k] = o.ph[k];
+            }
+            items.push_back(it);
+        } else {
+            Item it{};
+            it.perm = false;
+            it.op = o;
+            items.push_back(it);
+        }
+    }
+    const uint32_t high = ((1u << T) - 1u) & ~31u;  // local bits 5..T-1
+    size_t i = 0;
+    while (i < items.size()) {
+        TilePhase ph{};
+        uint32_t rset = 0;
+        std::vector<TileOp> pops;
+        size_t j = i;
+        for (; j < items.size(); j++) {
+            const Item &it = items[j];
+            if (it.perm) {
+                ph.nperm = it.np;
+                for (int k = 0; k < it.np; k++) {
+                    ph.pl[k] = it.pl[k];
+                    ph.ph[k] = it.ph[k];
+                }
+                j++;
+                break;
+            }
+            const uint32_t need = needs_register(it.op) ? (1u << it.op.tl) : 0u;
+            if (popc(rset | need) <= RB) {
+                rset |= need;
+                pops.push_back(it.op);
+            } else {
+                break;
+            }
+        }
+        // fill the free register slots with the bits the next ops want
+        for (size_t k = j; k < items.size() && popc(rset) < RB; k++) {
+            if (items[k].perm) continue;
+            if (needs_register(items[k].op)) rset |= 1u << items[k].op.tl;
+            if (popc(rset) > RB) rset &= ~(1u << items[k].op.tl);
+        }
+        for (int b = 5; b < T && popc(rset) < RB; b++) rset |= 1u << b;
+        int nr = 0, nw = 0;
+        for (int b = 5; b < T; b++) {
+            if ((rset >> b) & 1u) ph.rb[nr++] = (int8_t)b;
+            else if ((high >> b) & 1u) ph.wb[nw++] = (int8_t)b;
+        }
+        ph.op_begin = (int)ops_out.size();
+        ph.op_count = (int)pops.size();
+        for (TileOp op : pops) {
+            op.regk = -1;
+            const bool local_target = !(op.kind == TOP_DIAG_G);
+            if (local_target && op.tl >= 5)
+                for (int k = 0; k < nr; k++)
+                    if (ph.rb[k] == op.tl) op.regk = (int8_t)k;
+            op.creg = 0;
+            for (int k = 0; k < nr; k++)
+                if ((op.lcmask >> ph.rb[k]) & 1u) op.creg |= 1u << k;
+            op.lcthr = op.lcmask & ~rset;
+            ops_out.push_back(op);
+        }
+        phases_out.push_back(ph);
+        i = j;
+    }
+}
+
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB) {
     plan.passes.clear();
     plan.ops.clear();
     plan.dense.clear();
+    plan.phases.clear();
     if (gates.empty()) return;
     if (T > n) T = n;
     if (n <= T) L = n;
@@ -294,15 +422,23 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
         int j = 0;
         for (int b = 0; b < 64; b++)
             if ((hmask >> b) & 1ull) pp.geom.hb[j++] = b;
-        pp.op_begin = (int)plan.ops.size();
         pp.flops = 0.0;
         for (int gi : sched) pp.flops += gate_flops(gates[gi], n);
+        std::vector<TileOp> pass_ops;
         for (int gi : sched) {
             TileOp op;
             make_tile_op(gates[gi], pp.geom, op);  // fits by construction
-            plan.ops.push_back(op);
+            pass_ops.push_back(op);
         }
-        pp.op_count = (int)sched.size();
+        pp.op_begin = (int)plan.ops.size();
+        pp.phase_begin = (int)plan.phases.size();
+        if (RB > 0 && L + hcount == RB + 8 && L >= 5) {
+            build_phases(pass_ops, L + hcount, RB, plan.ops, plan.phases);
+        } else {
+            plan.ops.insert(plan.ops.end(), pass_ops.begin(), pass_ops.end());
+        }
+        pp.op_count = (int)plan.ops.size() - pp.op_begin;
+        pp.phase_count = (int)plan.phases.size() - pp.phase_begin;
         plan.passes.push_back(pp);
         remaining.swap(rest);
     }

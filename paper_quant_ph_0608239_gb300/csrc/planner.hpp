@@ -34,8 +34,9 @@ void fixed_bits_for(const PGate &g, FixedBitsHost &fb, uint64_t &pmask, bool &si
 
 struct PassPlan {
     TileGeom geom;
-    int op_begin, op_count;   // range in the plan's op array
-    double flops;             // algorithmic flops of the pass
+    int op_begin, op_count;       // range in the plan's op array
+    int phase_begin, phase_count; // range in the plan's phase array (0 phases: shared-memory kernel)
+    double flops;                 // algorithmic flops of the pass
 };
 
 // Algorithmic real flops of one gate over an n-qubit state: 14 per amplitude
@@ -48,6 +49,7 @@ double gate_flops(const PGate &g, int n);
 struct Plan {
     std::vector<PassPlan> passes;
     std::vector<TileOp> ops;
+    std::vector<TilePhase> phases;
     std::vector<double> dense;   // matrix pool for TOP_DENSE (complex, interleaved)
 };
 
@@ -55,7 +57,14 @@ struct Plan {
 // Gates are taken in order; a gate can join the current pass if it commutes
 // with every gate skipped so far (no shared qubit) and its targets fit in the
 // tile's bit set (diagonal gates need no target in the tile).
-void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan);
+// RB > 0: cut each pass with T = RB + 8 bits into register phases for the
+// register-blocked kernel (k_tile2.cu); passes that do not fit that shape
+// keep a flat op list for the shared-memory kernel (k_tile.cu).
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB = 0);
+
+// Cut one pass's op list into register phases (see k_tile2.cu).
+void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vector<TileOp> &ops_out,
+                  std::vector<TilePhase> &phases_out);
 
 // Translate one gate into a tile op for a pass with geometry g.
 bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op);

@@ -192,6 +192,55 @@ def test_adder_exact(q, dt, values, m):
     st.free()
 
 
+# ---------------------------------------------- register-blocked tile kernel
+# Default tiles (T = 12, or 13 for complex64) on n >= T run the register
+# kernel: lane bits 0..4 by warp shuffles, register bits in registers, warp
+# bits through shared-memory phases; complex128 in double-float.
+REG_TILES = [("c128", 12), ("c64", 12), ("c64", 13)]
+
+
+@pytest.mark.parametrize("dt,tile", REG_TILES)
+def test_register_tile_every_kind_every_target(q, dt, tile):
+    n = 15
+    psi = rand_state(n, 4)
+    for kind in ["H", "X", "Y", "XB", "YB", "NOT", "R", "V", "SU2"]:
+        for t in range(n):
+            g = g1(kind, t, (), PARAMS.get(kind, ()))
+            ref = oracle.run(n, [g], state=psi.copy())
+            got = run_gpu(q, n, dt, [g], psi=psi, tile_bits=tile)
+            assert err(got, ref) < TOL[dt], (kind, t)
+
+
+@pytest.mark.parametrize("dt,tile", REG_TILES)
+@pytest.mark.parametrize("n", [13, 16, 21])
+def test_register_tile_circuits_with_controls_and_swaps(q, dt, tile, n):
+    rng = np.random.default_rng(40 + n)
+    gates = inputs.random_circuit(n, 5, seed=n)
+    gates += controlled_gates(rng, n, 40)
+    # uncontrolled quantum SWAPs (applied as store permutations) between layers
+    for _ in range(6):
+        a, b = (int(x) for x in rng.permutation(n)[:2])
+        gates.insert(int(rng.integers(len(gates))), Gate("SWAP", (a, b), (), ()))
+    gates += inputs.random_circuit(n, 3, seed=n + 1)
+    x0 = inputs.random_basis(n, seed=n)
+    ref = oracle.run(n, gates, x0=x0)
+    got = run_gpu(q, n, dt, gates, x0=x0, tile_bits=tile)
+    assert err(got, ref) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt,tile", REG_TILES)
+def test_register_tile_qft_and_inverse(q, dt, tile):
+    n = 17
+    x, gates = inputs.qft_circuit(n, seed=9)
+    ref = oracle.run(n, gates, x0=x)
+    got = run_gpu(q, n, dt, gates, x0=x, tile_bits=tile)
+    assert err(got, ref) < TOL[dt]
+    back = run_gpu(q, n, dt, gates + inputs.iqft(range(n), swaps=True), x0=x, tile_bits=tile)
+    expect = np.zeros(1 << n)
+    expect[x] = 1
+    assert err(back, expect) < TOL[dt]
+
+
 # ------------------------------------------------------------ interchanges
 @pytest.mark.parametrize("table", ["onequbittab.txt", "twoqubittab.txt"])
 def test_permute_bits_matches_paper_tables(q, table):
