@@ -197,6 +197,8 @@ typedef struct {
     int32_t sweeps;      /* whole-state per-gate sweeps per run */
     int32_t ops;         /* gate operations in all tile programs */
     int32_t tile_bits;   /* T of the tile passes (0 if none) */
+    int32_t phases;      /* register phases over all passes (complex64 register kernel) */
+    int32_t reserved;
     double gates;        /* logical gates of the circuit */
     double alg_bytes;    /* algorithmic bytes of one run: 2 * amplitude size * amplitudes
                             each pass or sweep must read and write */

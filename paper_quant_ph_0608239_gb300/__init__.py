@@ -214,7 +214,7 @@ class Plan:
     def stats(self):
         s = QsimPlanStats()
         _capi.call("qsim_plan_get_stats", self.ptr, ctypes.byref(s))
-        return {"passes": s.passes, "sweeps": s.sweeps, "ops": s.ops, "tile_bits": s.tile_bits,
+        return {"passes": s.passes, "sweeps": s.sweeps, "ops": s.ops, "tile_bits": s.tile_bits, "phases": s.phases,
                 "gates": s.gates, "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
 
     def free(self):

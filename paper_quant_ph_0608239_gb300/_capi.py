@@ -40,7 +40,8 @@ class QsimCircuit(ctypes.Structure):
 
 class QsimPlanStats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("ops", ctypes.c_int32),
-                ("tile_bits", ctypes.c_int32), ("gates", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("tile_bits", ctypes.c_int32), ("phases", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gates", ctypes.c_double), ("alg_bytes", ctypes.c_double),
                 ("alg_flops", ctypes.c_double)]
 
 

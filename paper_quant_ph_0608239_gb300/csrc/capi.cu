@@ -336,7 +336,7 @@ qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g) {
 // complex64) when n >= T; other tile sizes use the shared-memory kernel.
 static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &L, int &RB) {
     T = (o && o->tile_bits > 0) ? o->tile_bits : 12;
-    const int Tmax = h->dt == QSIM_C64 ? 14 : 13;
+    const int Tmax = 13;
     if (T > Tmax) T = Tmax;
     if (T < 2) T = 2;
     RB = (tile2_supported((int)h->dt, T) && h->n >= T) ? T - 8 : 0;
@@ -379,6 +379,20 @@ static qsim_status stage(qsim_state *h, const std::vector<T> &v, T *&dbuf, size_
 
 extern "C" {
 
+static qsim_status ensure_dense(qsim_state *h, size_t bytes) {
+    if (bytes <= h->dense_cap) return QSIM_OK;
+    if (h->d_dense) {
+        CK(cudaStreamSynchronize(h->stream), "sync");
+        cudaFree(h->d_dense);
+        h->d_dense = nullptr;
+        h->dense_cap = 0;
+    }
+    const size_t cap = std::max(bytes, (size_t)65536);
+    CK(cudaMalloc(&h->d_dense, cap), "cudaMalloc dense");
+    h->dense_cap = cap;
+    return QSIM_OK;
+}
+
 static qsim_status upload_program(qsim_state *h, const Plan &plan) {
     if (!h->upload_done) CK(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming), "event");
     CK(cudaEventSynchronize(h->upload_done), "wait staging");
@@ -397,13 +411,24 @@ static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *
             CK(launch(h, F_TILE, pass_bytes, 1,
                       [&] {
                           return launch_tile_pass2(h->amp, (int)h->dt, pp.geom, d_phases + pp.phase_begin,
-                                                   pp.phase_count, d_ops, h->d_err, h->sm_count, h->stream);
+                                                   pp.phase_count, d_ops, pp.op_begin, pp.op_count, h->d_err,
+                                                   h->sm_count, h->stream);
                       },
                       pp.flops),
                "register tile pass");
             continue;
         }
         if (pp.op_count == 0) continue;
+        if (h->dt == QSIM_C128) {
+            CK(launch(h, F_TILE, pass_bytes, 1,
+                      [&] {
+                          return launch_tile_pass_df(h->amp, pp.geom, d_ops + pp.op_begin, pp.op_count, pp.arith,
+                                                     h->d_err, h->sm_count, h->stream);
+                      },
+                      pp.flops),
+               "double-float tile pass");
+            continue;
+        }
         CK(launch(h, F_TILE, pass_bytes, 1,
                   [&] {
                       return launch_tile_pass(h->amp, (int)h->dt, pp.geom, d_ops + pp.op_begin, pp.op_count,
@@ -434,6 +459,9 @@ struct qsim_plan_s {
     Plan plan;                   // FUSED mode
     TileOp *d_ops = nullptr;
     TilePhase *d_phases = nullptr;
+    std::vector<FusedBlock> blocks;  // FUSED mode with fuse_k: dense blocks on the tensor cores
+    std::vector<float> bmats;        // their B operands, 2 (2^(k+1))^2 floats each
+    float *d_bmats = nullptr;
     qsim_plan_stats stats{};
 };
 
@@ -466,19 +494,56 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         return QSIM_OK;
     }
+    if (o.fuse_k > 0) {
+        if (!fused_tc_supported((int)h->dt, o.fuse_k, h->n))
+            return fail(QSIM_EUNSUPPORTED, "fused blocks on the tensor cores need complex64, k = 4 or 5, n >= k + 7");
+        plan_fused(pg, h->n, o.fuse_k, P.blocks);
+        const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
+        P.bmats.resize(per * P.blocks.size());
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            TileGeom g;
+            FusedMap fm;
+            if (!fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm))
+                return fail(QSIM_EUNSUPPORTED, "no tile geometry for a fused block");
+            fused_tc_prepare_b(o.fuse_k, P.blocks[b].U.data(), P.bmats.data() + per * b);
+            P.stats.alg_flops += P.blocks[b].flops;
+        }
+        P.stats.passes = (int)P.blocks.size();
+        P.stats.tile_bits = o.fuse_k + 7;
+        P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
+        return QSIM_OK;
+    }
     int T, L, RB;
     tile_defaults(h, &o, T, L, RB);
     plan_tiles(pg, h->n, T, L, P.plan, RB);
     for (const PassPlan &pp : P.plan.passes)
         if (pp.op_count || pp.phase_count) P.stats.passes++;
     P.stats.ops = (int)P.plan.ops.size();
+    P.stats.phases = (int)P.plan.phases.size();
     P.stats.tile_bits = P.plan.passes.empty() ? 0 : P.plan.passes[0].geom.L + P.plan.passes[0].geom.H;
     P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
     for (const PassPlan &pp : P.plan.passes) P.stats.alg_flops += pp.flops;
     return QSIM_OK;
 }
 
+static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *d_bmats) {
+    if (P.blocks.empty()) return QSIM_OK;
+    const int k = P.blocks[0].k;
+    const size_t per = 2 * (size_t)(2 << k) * (size_t)(2 << k);
+    for (size_t b = 0; b < P.blocks.size(); b++) {
+        TileGeom g;
+        FusedMap fm;
+        fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
+        CK(launch(h, F_FUSED_TC, 2.0 * (double)state_bytes(h), 1,
+                  [&] { return launch_fused_tc(h->amp, k, g, fm, d_bmats + per * b, h->d_err, h->sm_count, h->stream); },
+                  P.blocks[b].flops),
+           "fused block (tensor cores)");
+    }
+    return QSIM_OK;
+}
+
 static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops, const TilePhase *d_phases) {
+    if (!P.blocks.empty()) return run_blocks(h, P, P.d_bmats ? P.d_bmats : static_cast<const float *>(h->d_dense));
     if (P.mode == QSIM_MODE_PERGATE) {
         for (const PGate &g : P.sweeps) {
             qsim_status st = sweep_gate(h, g);
@@ -494,6 +559,15 @@ qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, c
     qsim_plan_s P;
     qsim_status st = build_plan(h, gates, ng, opts, P);
     if (st != QSIM_OK) return st;
+    if (!P.blocks.empty()) {
+        const size_t bytes = P.bmats.size() * sizeof(float);
+        st = ensure_dense(h, bytes);
+        if (st != QSIM_OK) return st;
+        CK(cudaMemcpyAsync(h->d_dense, P.bmats.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload blocks");
+        CK(cudaStreamSynchronize(h->stream), "sync");  // the host copy dies with P
+        h->h2d += bytes;
+        return run_built(h, P, nullptr, nullptr);
+    }
     if (P.mode == QSIM_MODE_FUSED && !P.plan.ops.empty()) {
         st = upload_program(h, P.plan);
         if (st != QSIM_OK) return st;
@@ -521,7 +595,15 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
         if (e != cudaSuccess) st = cuda_fail(e, "upload plan");
         else h->h2d += P->plan.ops.size() * sizeof(TileOp) + P->plan.phases.size() * sizeof(TilePhase);
     }
+    if (st == QSIM_OK && !P->bmats.empty()) {
+        cudaError_t e = cudaMalloc(&P->d_bmats, P->bmats.size() * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_bmats, P->bmats.data(), P->bmats.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload fused blocks");
+        else h->h2d += P->bmats.size() * sizeof(float);
+    }
     if (st != QSIM_OK) {
+        if (P->d_bmats) cudaFree(P->d_bmats);
         if (P->d_ops) cudaFree(P->d_ops);
         if (P->d_phases) cudaFree(P->d_phases);
         delete P;
@@ -547,7 +629,8 @@ qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
 
 qsim_status qsim_plan_free(qsim_plan p) {
     if (!p) return QSIM_OK;
-    if (p->d_ops || p->d_phases) cudaDeviceSynchronize();
+    if (p->d_ops || p->d_phases || p->d_bmats) cudaDeviceSynchronize();
+    if (p->d_bmats) cudaFree(p->d_bmats);
     if (p->d_ops) cudaFree(p->d_ops);
     if (p->d_phases) cudaFree(p->d_phases);
     delete p;
@@ -614,27 +697,43 @@ qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const doub
     const size_t ent = (size_t)1 << (2 * k);
     for (size_t i = 0; i < 2 * ent; i++)
         if (!std::isfinite(U[i])) return fail(QSIM_EINVAL, "non-finite matrix entry");
-    const size_t bytes = ent * amp_bytes(h->dt);
-    if (bytes > h->dense_cap) {
-        if (h->d_dense) {
-            CK(cudaStreamSynchronize(h->stream), "sync");
-            cudaFree(h->d_dense);
-            h->d_dense = nullptr;
-            h->dense_cap = 0;
-        }
-        CK(cudaMalloc(&h->d_dense, std::max(bytes, (size_t)65536)), "cudaMalloc dense");
-        h->dense_cap = std::max(bytes, (size_t)65536);
+    const double flops = 8.0 * (double)(1u << k) * std::ldexp(1.0, h->n);
+    TileGeom g;
+    FusedMap fm;
+    if (fused_tc_supported((int)h->dt, k, h->n) && fused_geometry(h->n, k, pos, g, fm)) {
+        // tensor cores: B operand (3xTF32 head and tail) from U
+        std::vector<float> b(2 * (size_t)(2 << k) * (size_t)(2 << k));
+        fused_tc_prepare_b(k, U, b.data());
+        const size_t bytes = b.size() * sizeof(float);
+        qsim_status st = ensure_dense(h, bytes);
+        if (st != QSIM_OK) return st;
+        CK(cudaMemcpyAsync(h->d_dense, b.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+        CK(cudaStreamSynchronize(h->stream), "sync");  // b is freed on return
+        h->h2d += bytes;
+        CK(launch(h, F_FUSED_TC, 2.0 * (double)state_bytes(h), 1,
+                  [&] {
+                      return launch_fused_tc(h->amp, k, g, fm, static_cast<const float *>(h->d_dense), h->d_err,
+                                             h->sm_count, h->stream);
+                  },
+                  flops),
+           "fused gate (tensor cores)");
+        return QSIM_OK;
     }
+    const size_t bytes = ent * amp_bytes(h->dt);
+    qsim_status st = ensure_dense(h, bytes);
+    if (st != QSIM_OK) return st;
     if (h->dt == QSIM_C64) {
         std::vector<float> f(2 * ent);
         for (size_t i = 0; i < 2 * ent; i++) f[i] = (float)U[i];
         CK(cudaMemcpyAsync(h->d_dense, f.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+        CK(cudaStreamSynchronize(h->stream), "sync");
     } else {
         CK(cudaMemcpyAsync(h->d_dense, U, bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+        CK(cudaStreamSynchronize(h->stream), "sync");
     }
     h->h2d += bytes;
     CK(launch(h, F_DENSE, 2.0 * (double)state_bytes(h), 1,
-              [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, pos, h->d_dense, h->stream); }),
+              [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, pos, h->d_dense, h->stream); }, flops),
        "dense gate");
     return QSIM_OK;
 }

@@ -1,0 +1,263 @@
+// k_fused_tc.cu -- dense k-qubit gates (k = 4, 5) on the tensor cores.
+//
+// A fused gate is a 2^k x 2^k unitary U (the FP64 product of the gates it
+// replaces, built on the host).  For every group of 2^k amplitudes that differ
+// only in the k qubits, a' = U a.  With the complex numbers embedded as real
+// 2x2 blocks ([[Re, -Im], [Im, Re]]) this is the real matrix product
+//
+//     D (rows = groups, 2K columns) = A (groups x 2K) * B^T,  K = 2^k,
+//
+// where a row of A is the group's amplitudes in their memory order
+// (re, im, re, im, ...).  Each CTA fetches a tile of 2^(k+7) amplitudes
+// (128 groups) with bulk asynchronous copies, splits every value into a TF32
+// head and an FP32 tail (x = hi + lo), writes A_hi and A_lo in the tensor
+// cores' canonical K-major layout, and one thread issues
+//
+//     D = A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T      (3xTF32, FP32 accumulate)
+//
+// as tcgen05.mma instructions (M = 128, N = 2K, K = 8 per instruction) into
+// tensor memory.  The accumulator is read back with tcgen05.ld, written into
+// shared memory at the groups' positions and stored with bulk copies.
+// B_hi / B_lo (from U) are prepared on the host and loaded once per CTA.
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.hpp"
+#include "ptx.cuh"
+#include "tcgen05.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreadsTC = 256;
+constexpr int kMaxHTC = 10;
+constexpr long long kWaitBudgetTC = 4000000000ll;
+
+// byte offset of element (row, kk) in a canonical K-major no-swizzle operand
+// with `kr` columns: 8 x 16-byte core matrices, K-adjacent ones 128 bytes
+// apart, M-adjacent ones kr * 32 bytes apart
+__host__ __device__ __forceinline__ uint32_t canon_off(uint32_t row, uint32_t kk, uint32_t kr) {
+    return (row & 7u) * 16u + (kk & 3u) * 4u + (kk >> 2) * 128u + (row >> 3) * (kr * 32u);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_fused_tc(float2 *__restrict__ a, TileGeom g, FusedMap fm, const float *__restrict__ bmat, uint32_t *err,
+               uint64_t ntiles) {
+    constexpr int KR = 2 << K;              // real columns = 2 * 2^K
+    constexpr int N = KR;                   // output columns
+    constexpr int T = K + 7;                // 128 groups per tile
+    constexpr uint32_t TS = 1u << T;
+    constexpr uint32_t OPB = 8u << T;       // operand bytes (A_hi, A_lo, tile)
+    constexpr uint32_t BB = (uint32_t)N * KR * 4u;
+    constexpr int PER = TS / kThreadsTC;    // amplitudes per thread
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *s_tile = smem_raw;       // loaded tile, then A_lo
+    unsigned char *s_ahi = smem_raw + OPB;  // A_hi, then the output tile
+    unsigned char *s_bhi = smem_raw + 2 * OPB;
+    unsigned char *s_blo = s_bhi + BB;
+    __shared__ __align__(8) uint64_t bar_ld, bar_mma, bar_b;
+    __shared__ uint32_t tmem_slot;
+    __shared__ uint64_t runoff[1 << kMaxHTC];
+    __shared__ int abort_flag;
+    const int L = g.L, H = g.H;
+    const uint32_t nruns = 1u << H;
+    const uint32_t run_bytes = 8u << L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
+        uint64_t o = 0;
+        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
+        runoff[j] = o;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar_ld, 1);
+        mbar_init(&bar_mma, 1);
+        mbar_init(&bar_b, 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_slot, N < 32 ? 32 : N);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // B_hi, B_lo: 2 x BB bytes from global, once per CTA
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar_b, 2 * BB);
+        bulk_g2s(s_bhi, bmat, BB, &bar_b);
+        bulk_g2s(s_blo, bmat + BB / 4, BB, &bar_b);
+    }
+    if (!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) {
+        atomicExch(err, kErrTimeout);
+        abort_flag = 1;
+    }
+    __syncthreads();
+
+    const uint32_t idesc = umma_idesc_tf32(128, N);
+    uint32_t ld_parity = 0, mma_parity = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+        uint64_t base = tile << L;
+        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        float2 *tin = reinterpret_cast<float2 *>(s_tile);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar_ld, TS * 8u);
+            __syncwarp();
+            for (uint32_t j = threadIdx.x; j < nruns; j += 32)
+                bulk_g2s(tin + ((size_t)j << L), a + (base | runoff[j]), run_bytes, &bar_ld);
+        }
+        if (!mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC)) {
+            atomicExch(err, kErrTimeout);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        ld_parity ^= 1u;
+
+        // split into TF32 head / FP32 tail, scatter into the canonical layouts
+        float2 x[PER];
+#pragma unroll
+        for (int s = 0; s < PER; s++) x[s] = tin[threadIdx.x + s * kThreadsTC];
+        __syncthreads();  // the tile buffer becomes A_lo
+#pragma unroll
+        for (int s = 0; s < PER; s++) {
+            const uint32_t i = threadIdx.x + s * kThreadsTC;
+            uint32_t m = 0, c = 0;
+#pragma unroll
+            for (int b = 0; b < T - K; b++) m |= ((i >> fm.row[b]) & 1u) << b;
+#pragma unroll
+            for (int b = 0; b < K; b++) c |= ((i >> fm.col[b]) & 1u) << b;
+            const float hr = to_tf32(x[s].x), hi_ = to_tf32(x[s].y);
+            const uint32_t off = canon_off(m, 2 * c, KR);  // (re, im) are adjacent in one 16-byte chunk
+            *reinterpret_cast<float2 *>(s_ahi + off) = make_float2(hr, hi_);
+            *reinterpret_cast<float2 *>(s_tile + off) = make_float2(x[s].x - hr, x[s].y - hi_);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes -> tensor-core (async proxy) reads
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+
+        if (threadIdx.x == 0) {
+            const uint32_t ahi = smem_u32(s_ahi), alo = smem_u32(s_tile);
+            const uint32_t bhi = smem_u32(s_bhi), blo = smem_u32(s_blo);
+#pragma unroll
+            for (int ks = 0; ks < KR / 8; ks++) {
+                const uint32_t o = (uint32_t)ks * 256u;  // 8 TF32 along K = two core matrices
+                umma_tf32(tmem, umma_desc(alo + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc,
+                          ks > 0 ? 1u : 0u);
+                umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(blo + o, 128, KR * 32), idesc, 1u);
+                umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc, 1u);
+            }
+            umma_commit(&bar_mma);
+        }
+        if (!mbar_wait_bounded(&bar_mma, mma_parity, kWaitBudgetTC)) {
+            atomicExch(err, kErrTimeout);
+            abort_flag = 1;
+        }
+        mma_parity ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (abort_flag) break;
+
+        // epilogue: warp w reads lanes 32 (w % 4) .. +31 (groups), column chunk w / 4
+        float2 *tout = reinterpret_cast<float2 *>(s_ahi);
+        const int chunk = warp >> 2;
+        if (chunk < N / 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * chunk), r);
+            tmem_ld_wait();
+            const uint32_t m = (uint32_t)(32 * (warp & 3) + lane);
+            uint32_t ibase = 0;
+#pragma unroll
+            for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const uint32_t cidx = (uint32_t)(16 * chunk + q);  // output amplitude of the group
+                uint32_t i = ibase;
+#pragma unroll
+                for (int b = 0; b < K; b++) i |= ((cidx >> b) & 1u) << fm.col[b];
+                tout[i] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+            }
+        }
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            for (uint32_t j = threadIdx.x; j < nruns; j += 32)
+                bulk_s2g(a + (base | runoff[j]), tout + ((size_t)j << L), run_bytes);
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) bulk_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, N < 32 ? 32 : N);
+}
+
+template <int K>
+cudaError_t launch_k(void *amp, const TileGeom &g, const FusedMap &fm, const float *bmat, uint32_t *err,
+                     int sm_count, cudaStream_t s) {
+    constexpr int KR = 2 << K;
+    constexpr int T = K + 7;
+    const size_t smem = 2 * ((size_t)8 << T) + 2 * (size_t)KR * KR * 4;
+    const uint64_t ntiles = 1ull << (g.n - T);
+    uint64_t grid = (uint64_t)sm_count * (smem <= 100 * 1024 ? 2 : 1);
+    if (grid > ntiles) grid = ntiles;
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fused_tc<K><<<(unsigned)grid, kThreadsTC, smem, s>>>(static_cast<float2 *>(amp), g, fm, bmat, err, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Host: B_hi / B_lo of a fused gate in the canonical layout (see above).
+// U: 2^k x 2^k complex, row-major (re, im) FP64.  out: 2 * (2K)^2 floats.
+void fused_tc_prepare_b(int k, const double *U, float *out) {
+    const int K = 1 << k, KR = 2 * K;
+    float *hi = out, *lo = out + KR * KR;
+    for (int i = 0; i < KR * KR; i++) hi[i] = lo[i] = 0.0f;
+    auto tf32 = [](float x) {
+        uint32_t b;
+        std::memcpy(&b, &x, 4);
+        b = (b + 0x1000u) & 0xFFFFE000u;  // nearest, ties away from zero, 10 significand bits
+        float r;
+        std::memcpy(&r, &b, 4);
+        return r;
+    };
+    for (int r = 0; r < K; r++)
+        for (int c = 0; c < K; c++) {
+            const double ur = U[2 * (r * K + c)], ui = U[2 * (r * K + c) + 1];
+            // output column n (2r: re, 2r+1: im) against input element kk (2c: re, 2c+1: im)
+            const double v[4] = {ur, -ui, ui, ur};
+            const int nn[4] = {2 * r, 2 * r, 2 * r + 1, 2 * r + 1};
+            const int kk[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+            for (int e = 0; e < 4; e++) {
+                const float h = tf32((float)v[e]);
+                const float l = (float)(v[e] - (double)h);
+                const uint32_t off = canon_off((uint32_t)nn[e], (uint32_t)kk[e], (uint32_t)KR) / 4u;
+                hi[off] = h;
+                lo[off] = l;
+            }
+        }
+}
+
+bool fused_tc_supported(int dt, int k, int n) { return dt == 0 && (k == 4 || k == 5) && n >= k + 7; }
+
+cudaError_t launch_fused_tc(void *amp, int k, const TileGeom &g, const FusedMap &fm, const float *bmat,
+                            uint32_t *err, int sm_count, cudaStream_t s) {
+    if (g.L + g.H != k + 7 || g.H > kMaxHTC || g.L < 1) return cudaErrorInvalidValue;
+    if (k == 4) return launch_k<4>(amp, g, fm, bmat, err, sm_count, s);
+    if (k == 5) return launch_k<5>(amp, g, fm, bmat, err, sm_count, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qsim

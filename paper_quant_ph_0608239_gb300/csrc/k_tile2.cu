@@ -100,13 +100,13 @@ __device__ __forceinline__ void st_amp(double2 *t, uint32_t i, const dcx &v, int
 // ---- gate application in registers
 enum { PK_GENERAL = 0, PK_REAL = 1, PK_ANTI = 2, PK_EXCH = 3 };
 
-template <int RB, int K, int PK, typename V>
+template <int RB, int K, int PK, bool CT, typename V>
 __device__ __forceinline__ void pair_reg(V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg) {
 #pragma unroll
     for (int j = 0; j < (1 << RB); j++) {
         if (j & (1 << K)) continue;
         const int j1 = j | (1 << K);
-        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        if (CT && !(thr_ok && ((uint32_t)j & creg) == creg)) continue;
         const V a = v[j], b = v[j1];
         if (PK == PK_GENERAL) {
             v[j] = vmul2(u[0], a, u[1], b);
@@ -124,23 +124,23 @@ __device__ __forceinline__ void pair_reg(V (&v)[1 << RB], const V (&u)[4], bool 
     }
 }
 
-template <int RB, int PK, typename V>
+template <int RB, int PK, bool CT, typename V>
 __device__ __forceinline__ void pair_reg_dispatch(int k, V (&v)[1 << RB], const V (&u)[4], bool thr_ok,
                                                   uint32_t creg) {
     switch (k) {
-    case 0: pair_reg<RB, 0, PK>(v, u, thr_ok, creg); break;
-    case 1: pair_reg<RB, 1, PK>(v, u, thr_ok, creg); break;
-    case 2: pair_reg<RB, 2, PK>(v, u, thr_ok, creg); break;
-    case 3: pair_reg<RB, 3, PK>(v, u, thr_ok, creg); break;
+    case 0: pair_reg<RB, 0, PK, CT>(v, u, thr_ok, creg); break;
+    case 1: pair_reg<RB, 1, PK, CT>(v, u, thr_ok, creg); break;
+    case 2: pair_reg<RB, 2, PK, CT>(v, u, thr_ok, creg); break;
+    case 3: pair_reg<RB, 3, PK, CT>(v, u, thr_ok, creg); break;
     default:
-        if constexpr (RB > 4) pair_reg<RB, (RB > 4 ? 4 : 0), PK>(v, u, thr_ok, creg);
+        if constexpr (RB > 4) pair_reg<RB, (RB > 4 ? 4 : 0), PK, CT>(v, u, thr_ok, creg);
         break;
     }
 }
 
 // target on lane bit t: partner in lane ^ 2^t; each lane computes its own
 // output with the coefficients of its row.
-template <int RB, int PK, typename V>
+template <int RB, int PK, bool CT, typename V>
 __device__ __forceinline__ void pair_lane(int t, V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg,
                                           int lane) {
     const bool upper = (lane >> t) & 1;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void pair_lane(int t, V (&v)[1 << RB], const V (&u)[4
 #pragma unroll
     for (int j = 0; j < (1 << RB); j++) {
         const V w = shfl_x(v[j], m);
-        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        if (CT && !(thr_ok && ((uint32_t)j & creg) == creg)) continue;
         if (PK == PK_GENERAL) v[j] = vmul2(c0, v[j], c1, w);
         else if (PK == PK_REAL) v[j] = vrmul2(c0, v[j], c1, w);
         else if (PK == PK_ANTI) v[j] = vmul(c1, w);
@@ -198,19 +198,25 @@ __device__ __forceinline__ void apply_op2(const TileOp &op, typename AmpT<C128>:
 #pragma unroll
     for (int k = 0; k < 4; k++) u[k] = coef<C128>(op, k);
     const int pk = op.pk;  // pair kind chosen by the host
+    // uncontrolled dense gates (the common case) skip the per-register tests
+    const bool ct = (op.lcthr | creg) != 0u;
     if (op.regk >= 0) {
-        switch (pk) {
-        case PK_GENERAL: pair_reg_dispatch<RB, PK_GENERAL>(op.regk, v, u, thr_ok, creg); break;
-        case PK_REAL: pair_reg_dispatch<RB, PK_REAL>(op.regk, v, u, thr_ok, creg); break;
-        case PK_ANTI: pair_reg_dispatch<RB, PK_ANTI>(op.regk, v, u, thr_ok, creg); break;
-        default: pair_reg_dispatch<RB, PK_EXCH>(op.regk, v, u, thr_ok, creg); break;
+        if (!ct && pk == PK_GENERAL) pair_reg_dispatch<RB, PK_GENERAL, false>(op.regk, v, u, true, 0u);
+        else if (!ct && pk == PK_REAL) pair_reg_dispatch<RB, PK_REAL, false>(op.regk, v, u, true, 0u);
+        else switch (pk) {
+        case PK_GENERAL: pair_reg_dispatch<RB, PK_GENERAL, true>(op.regk, v, u, thr_ok, creg); break;
+        case PK_REAL: pair_reg_dispatch<RB, PK_REAL, true>(op.regk, v, u, thr_ok, creg); break;
+        case PK_ANTI: pair_reg_dispatch<RB, PK_ANTI, true>(op.regk, v, u, thr_ok, creg); break;
+        default: pair_reg_dispatch<RB, PK_EXCH, true>(op.regk, v, u, thr_ok, creg); break;
         }
     } else {
-        switch (pk) {
-        case PK_GENERAL: pair_lane<RB, PK_GENERAL>(op.tl, v, u, thr_ok, creg, lane); break;
-        case PK_REAL: pair_lane<RB, PK_REAL>(op.tl, v, u, thr_ok, creg, lane); break;
-        case PK_ANTI: pair_lane<RB, PK_ANTI>(op.tl, v, u, thr_ok, creg, lane); break;
-        default: pair_lane<RB, PK_EXCH>(op.tl, v, u, thr_ok, creg, lane); break;
+        if (!ct && pk == PK_GENERAL) pair_lane<RB, PK_GENERAL, false>(op.tl, v, u, true, 0u, lane);
+        else if (!ct && pk == PK_REAL) pair_lane<RB, PK_REAL, false>(op.tl, v, u, true, 0u, lane);
+        else switch (pk) {
+        case PK_GENERAL: pair_lane<RB, PK_GENERAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
+        case PK_REAL: pair_lane<RB, PK_REAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
+        case PK_ANTI: pair_lane<RB, PK_ANTI, true>(op.tl, v, u, thr_ok, creg, lane); break;
+        default: pair_lane<RB, PK_EXCH, true>(op.tl, v, u, thr_ok, creg, lane); break;
         }
     }
 }
@@ -226,11 +232,12 @@ __device__ __forceinline__ uint32_t reg_index(uint32_t thr_idx, const uint32_t (
     return x;
 }
 
+constexpr int kMaxStagedOps = 96;  // ops of a pass copied to shared memory (18 KiB)
+
 template <bool C128, int RB>
-__global__ void __launch_bounds__(kThreads2, 2) k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g,
-                                                     const TilePhase *__restrict__ phases, int nphases,
-                                                     const TileOp *__restrict__ ops, uint32_t *err,
-                                                     uint64_t ntiles) {
+__global__ void __launch_bounds__(kThreads2, RB == 4 ? 3 : 2)
+    k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases, int nphases,
+            const TileOp *__restrict__ ops_g, int op_base, int op_count, uint32_t *err, uint64_t ntiles) {
     using S = typename AmpT<C128>::S;
     using V = typename AmpT<C128>::V;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -247,6 +254,16 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tile2(typename AmpT<C128>::S *
     const uint32_t ncopies = nruns << sub_shift;
     const uint32_t copy_bytes = 1u << (sub_L + amp_shift);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the pass's ops, read by every thread for every tile: staged in shared
+    // memory after the tile when they fit (phases index them from op_base)
+    TileOp *ops_s = reinterpret_cast<TileOp *>(smem_raw + (sizeof(S) << T));
+    const bool staged = op_count <= kMaxStagedOps;
+    if (staged) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(ops_g + op_base);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(ops_s);
+        for (uint32_t w = threadIdx.x; w < (uint32_t)op_count * (sizeof(TileOp) / 4); w += blockDim.x) dst[w] = src[w];
+    }
+    const TileOp *ops = staged ? ops_s - op_base : ops_g;
 
     for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
         uint64_t o = 0;
@@ -336,36 +353,34 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tile2(typename AmpT<C128>::S *
 
 template <bool C128, int RB>
 cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int nphases, const TileOp *ops,
-                    uint32_t *err, int sm_count, cudaStream_t s) {
+                    int op_base, int op_count, uint32_t *err, int sm_count, cudaStream_t s) {
     using S = typename AmpT<C128>::S;
     const int T = g.L + g.H;
-    const size_t smem = sizeof(S) << T;
+    const size_t smem = (sizeof(S) << T) + (op_count <= kMaxStagedOps ? (size_t)op_count * sizeof(TileOp) : 0);
     const uint64_t ntiles = 1ull << (g.n - T);
     int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
+    if (per_sm > (RB == 4 ? 3 : 2)) per_sm = RB == 4 ? 3 : 2;
     uint64_t grid = (uint64_t)sm_count * per_sm;
     if (grid > ntiles) grid = ntiles;
     cudaError_t e = cudaFuncSetAttribute(k_tile2<C128, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tile2<C128, RB><<<(unsigned)grid, kThreads2, smem, s>>>(static_cast<S *>(amp), g, phases, nphases, ops, err,
-                                                               ntiles);
+    k_tile2<C128, RB><<<(unsigned)grid, kThreads2, smem, s>>>(static_cast<S *>(amp), g, phases, nphases, ops,
+                                                               op_base, op_count, err, ntiles);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool tile2_supported(int dt, int T) { return T == 12 || (dt == 0 && T == 13); }
+bool tile2_supported(int dt, int T) { return dt == 0 && (T == 12 || T == 13); }
 
 cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePhase *phases, int nphases,
-                              const TileOp *ops, uint32_t *err, int sm_count, cudaStream_t s) {
+                              const TileOp *ops, int op_base, int op_count, uint32_t *err, int sm_count,
+                              cudaStream_t s) {
     const int T = g.L + g.H;
     if (!tile2_supported(dt, T) || g.L < 5 || g.H > kMaxH2 || T > g.n) return cudaErrorInvalidValue;
-    if (dt == 0) {
-        if (T == 13) return launch2<false, 5>(amp, g, phases, nphases, ops, err, sm_count, s);
-        return launch2<false, 4>(amp, g, phases, nphases, ops, err, sm_count, s);
-    }
-    return launch2<true, 4>(amp, g, phases, nphases, ops, err, sm_count, s);
+    if (T == 13) return launch2<false, 5>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
+    return launch2<false, 4>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
 }
 
 }  // namespace qsim

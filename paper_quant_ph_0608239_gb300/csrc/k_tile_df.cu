@@ -1,0 +1,252 @@
+// k_tile_df.cu -- complex128 tile passes in double-float arithmetic.
+//
+// Same pass structure as k_tile.cu (bulk asynchronous copies of 2^T
+// amplitudes = the L low index bits plus H chosen high bits; one read and one
+// write of the state per pass), with the gate program applied in shared
+// memory in double-float arithmetic (df64.cuh) instead of FP64: GB300 runs
+// FP64 at about 1/58 of its FP32 rate.  After the tile lands it is converted
+// in place from IEEE double to double-float (two floats per real, integer
+// operations only); before it is stored it is converted back.  A pass whose
+// ops only move data (bit flips, SWAP gates, interchanges) skips both
+// conversions and stays bit-exact.
+//
+// Each op is one sweep over the tile's pairs in shared memory, with the
+// target bit a runtime value, so one compact code path serves every target
+// (the double-float arithmetic per pair is long enough that shared-memory
+// traffic and the barrier between ops are a small share of the time).
+#include "common.cuh"
+#include "df64.cuh"
+#include "kernels.hpp"
+#include "ptx.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreadsDF = 256;
+constexpr int kMaxHDF = 10;
+constexpr int kMaxCopyShiftDF = 14;
+constexpr long long kWaitBudgetDF = 4000000000ll;
+
+__device__ __forceinline__ uint32_t ins0d(uint32_t i, int pos) {
+    return ((i >> pos) << (pos + 1)) | (i & ((1u << pos) - 1u));
+}
+
+__device__ __forceinline__ dcx ldx(const float4 *t, uint32_t i) {
+    const float4 f = t[i];
+    return dcx{df{f.x, f.y}, df{f.z, f.w}};
+}
+__device__ __forceinline__ void stx(float4 *t, uint32_t i, const dcx &v) {
+    t[i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+}
+__device__ __forceinline__ dcx coefx(const TileOp &op, int k) {
+    return dcx{df{op.uh[2 * k], op.ul[2 * k]}, df{op.uh[2 * k + 1], op.ul[2 * k + 1]}};
+}
+
+__device__ void apply_df(float4 *t, int T, const TileOp &op, uint64_t base) {
+    if ((base & op.gcmask) != op.gcmask) return;
+    const uint32_t lc = op.lcmask;
+    const uint32_t TS = 1u << T;
+    const int kind = op.kind;
+    if (kind == TOP_GENERAL || kind == TOP_ANTIDIAG || kind == TOP_EXCHANGE) {
+        const int tl = op.tl;
+        const uint32_t bt = 1u << tl;
+        const int pk = op.pk;
+        const dcx u0 = coefx(op, 0), u1 = coefx(op, 1), u2 = coefx(op, 2), u3 = coefx(op, 3);
+        if (pk == 3) {  // exchange: move the bytes
+            for (uint32_t p = threadIdx.x; p < (TS >> 1); p += blockDim.x) {
+                const uint32_t i0 = ins0d(p, tl);
+                if ((i0 & lc) != lc) continue;
+                const uint32_t i1 = i0 | bt;
+                const float4 x = t[i0];
+                t[i0] = t[i1];
+                t[i1] = x;
+            }
+            return;
+        }
+        // two independent pairs per iteration: the two-sum chains of one pair
+        // fill the latency of the other's
+        const uint32_t half = TS >> 1, step = blockDim.x;
+        for (uint32_t p = threadIdx.x; p < half; p += 2 * step) {
+            const uint32_t q = p + step;
+            const bool has2 = q < half;
+            const uint32_t i0 = ins0d(p, tl), j0 = has2 ? ins0d(q, tl) : i0;
+            const bool ok0 = (i0 & lc) == lc, ok1 = has2 && (j0 & lc) == lc;
+            const dcx a = ldx(t, i0), b = ldx(t, i0 | bt);
+            const dcx c = ldx(t, j0), d = ldx(t, j0 | bt);
+            dcx x0, x1, y0, y1;
+            if (pk == 0) {
+                x0 = dcx_mul2(u0, a, u1, b);
+                y0 = dcx_mul2(u0, c, u1, d);
+                x1 = dcx_mul2(u2, a, u3, b);
+                y1 = dcx_mul2(u2, c, u3, d);
+            } else if (pk == 1) {
+                x0 = dcx_rmul2(u0.re, a, u1.re, b);
+                y0 = dcx_rmul2(u0.re, c, u1.re, d);
+                x1 = dcx_rmul2(u2.re, a, u3.re, b);
+                y1 = dcx_rmul2(u2.re, c, u3.re, d);
+            } else {
+                x0 = dcx_mul(u1, b);
+                y0 = dcx_mul(u1, d);
+                x1 = dcx_mul(u2, a);
+                y1 = dcx_mul(u2, c);
+            }
+            if (ok0) {
+                stx(t, i0, x0);
+                stx(t, i0 | bt, x1);
+            }
+            if (ok1) {
+                stx(t, j0, y0);
+                stx(t, j0 | bt, y1);
+            }
+        }
+    } else if (kind == TOP_PHASE) {
+        const uint32_t bt = 1u << op.tl;
+        const dcx u3 = coefx(op, 3);
+        for (uint32_t p = threadIdx.x; p < (TS >> 1); p += blockDim.x) {
+            const uint32_t i = ins0d(p, op.tl) | bt;
+            if ((i & lc) != lc) continue;
+            stx(t, i, dcx_mul(u3, ldx(t, i)));
+        }
+    } else if (kind == TOP_DIAG || kind == TOP_DIAG_G) {
+        const dcx u0 = coefx(op, 0), u3 = coefx(op, 3);
+        const bool global_one = kind == TOP_DIAG_G && ((base >> op.tl) & 1ull);
+        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
+            if ((i & lc) != lc) continue;
+            const bool one = kind == TOP_DIAG ? ((i >> op.tl) & 1u) : global_one;
+            stx(t, i, dcx_mul(one ? u3 : u0, ldx(t, i)));
+        }
+    } else if (kind == TOP_SWAPGATE) {
+        const uint32_t b0 = 1u << op.tl, b1 = 1u << op.tl2;
+        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
+            if (!(i & b0) || (i & b1) || (i & lc) != lc) continue;
+            const uint32_t j = (i & ~b0) | b1;
+            const float4 x = t[i];
+            t[i] = t[j];
+            t[j] = x;
+        }
+    } else if (kind == TOP_PERM) {
+        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
+            uint32_t j = i;
+            for (int k = 0; k < op.nperm; k++) {
+                const uint32_t bl = (i >> op.pl[k]) & 1u, bh = (i >> op.ph[k]) & 1u;
+                j &= ~((1u << op.pl[k]) | (1u << op.ph[k]));
+                j |= (bl << op.ph[k]) | (bh << op.pl[k]);
+            }
+            if (j > i) {
+                const float4 x = t[i];
+                t[i] = t[j];
+                t[j] = x;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a, TileGeom g,
+                                                        const TileOp *__restrict__ ops, int nops, int convert,
+                                                        uint32_t *err, uint64_t ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double2 *t = reinterpret_cast<double2 *>(smem_raw);
+    float4 *tf = reinterpret_cast<float4 *>(smem_raw);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint64_t runoff[1 << kMaxHDF];
+    __shared__ int abort_flag;
+    const int L = g.L, H = g.H, T = L + H;
+    const uint32_t TS = 1u << T;
+    const uint32_t nruns = 1u << H;
+    const int sub_L = L + 4 > kMaxCopyShiftDF ? kMaxCopyShiftDF - 4 : L;
+    const int sub_shift = L - sub_L;
+    const uint32_t ncopies = nruns << sub_shift;
+    const uint32_t copy_bytes = 1u << (sub_L + 4);
+
+    for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
+        uint64_t o = 0;
+        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
+        runoff[j] = o;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    uint32_t parity = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint64_t base = tile << L;
+        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, TS * 16u);
+            __syncwarp();
+            for (uint32_t c = threadIdx.x; c < ncopies; c += 32) {
+                const uint32_t j = c >> sub_shift, s = c & ((1u << sub_shift) - 1u);
+                bulk_g2s(t + ((size_t)j << L) + ((size_t)s << sub_L), a + (base | runoff[j]) + ((size_t)s << sub_L),
+                         copy_bytes, &bar);
+            }
+        }
+        if (!mbar_wait_bounded(&bar, parity, kWaitBudgetDF)) {
+            atomicExch(err, kErrTimeout);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) {
+            mbar_wait_bounded(&bar, parity, kWaitBudgetDF);
+            return;
+        }
+        parity ^= 1u;
+
+        if (convert) {
+            for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
+                const double2 d = t[i];
+                stx(tf, i, dcx{df_from_double(d.x), df_from_double(d.y)});
+            }
+            __syncthreads();
+        }
+        for (int o = 0; o < nops; o++) {
+            apply_df(tf, T, ops[o], base);
+            __syncthreads();
+        }
+        if (convert) {
+            for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
+                const dcx v = ldx(tf, i);
+                t[i] = make_double2(df_to_double(v.re), df_to_double(v.im));
+            }
+        }
+
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            for (uint32_t c = threadIdx.x; c < ncopies; c += 32) {
+                const uint32_t j = c >> sub_shift, s = c & ((1u << sub_shift) - 1u);
+                bulk_s2g(a + (base | runoff[j]) + ((size_t)s << sub_L), t + ((size_t)j << L) + ((size_t)s << sub_L),
+                         copy_bytes);
+            }
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) bulk_wait_all();
+}
+
+}  // namespace
+
+cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, bool convert,
+                                uint32_t *err, int sm_count, cudaStream_t s) {
+    const int T = g.L + g.H;
+    if (g.H < 0 || g.H > kMaxHDF || T > g.n || T > 13 || g.L < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)16 << T;
+    const uint64_t ntiles = 1ull << (g.n - T);
+    int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    cudaError_t e = cudaFuncSetAttribute(k_tile_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile_df<<<(unsigned)grid, kThreadsDF, smem, s>>>(static_cast<double2 *>(amp), g, ops, nops, convert ? 1 : 0,
+                                                      err, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

@@ -86,6 +86,13 @@ struct TileGeom {
     int32_t hb[kMaxTileHigh];  // physical positions of the high tile bits, ascending, >= L
 };
 
+// Local bit layout of a fused-gate tile (k_fused_tc.cu): row[b] = local bit
+// of row-index bit b (the groups), col[j] = local bit of the gate's qubit j.
+struct FusedMap {
+    int8_t row[16];
+    int8_t col[8];
+};
+
 // ------------------------------------------------------------ launchers
 // dt: 0 = complex64, 1 = complex128.  All return the launch error.
 struct FixedBitsHost {
@@ -116,12 +123,26 @@ cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp 
                              const void *dmat, uint32_t *err, int sm_count, cudaStream_t s);
 size_t tile_smem_bytes(int dt, int T);
 
-// Register-blocked tile pass (k_tile2.cu): T = 8 + register bits, T = 12
-// (both precisions) or 13 (complex64), L >= 5 (the lane bits are the physical
-// bits 0..4).
+// Register-blocked tile pass (k_tile2.cu), complex64: T = 8 + register
+// bits = 12 or 13, L >= 5 (the lane bits are the physical bits 0..4).
 bool tile2_supported(int dt, int T);
+
+// complex128 tile pass in double-float arithmetic (k_tile_df.cu); convert =
+// false for passes that only move data (kept bit-exact).
+cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, bool convert,
+                                uint32_t *err, int sm_count, cudaStream_t s);
+// ops: the plan's op array; the pass's phases use ops[op_base, op_base + op_count).
 cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePhase *phases, int nphases,
-                              const TileOp *ops, uint32_t *err, int sm_count, cudaStream_t s);
+                              const TileOp *ops, int op_base, int op_count, uint32_t *err, int sm_count,
+                              cudaStream_t s);
+
+// Dense k-qubit gate on the tensor cores (k_fused_tc.cu, complex64, k = 4
+// or 5, n >= k + 7): tile T = k + 7 bits containing the k qubits; bmat =
+// device copy of fused_tc_prepare_b's output (2 * (2^(k+1))^2 floats).
+bool fused_tc_supported(int dt, int k, int n);
+void fused_tc_prepare_b(int k, const double *U, float *out);
+cudaError_t launch_fused_tc(void *amp, int k, const TileGeom &g, const FusedMap &fm, const float *bmat,
+                            uint32_t *err, int sm_count, cudaStream_t s);
 
 // Reductions (FP64 accumulation).  scratch: device buffer of at least
 // reduce_scratch_bytes(n) bytes.

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 
 namespace qsim {
@@ -439,9 +440,134 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
         }
         pp.op_count = (int)plan.ops.size() - pp.op_begin;
         pp.phase_count = (int)plan.phases.size() - pp.phase_begin;
+        pp.arith = false;
+        for (int gi : sched)
+            if (gates[gi].kind != QSIM_GATE_SWAP && gates[gi].gc != GC_EXCHANGE) pp.arith = true;
         plan.passes.push_back(pp);
         remaining.swap(rest);
     }
+}
+
+}  // namespace qsim
+
+namespace qsim {
+
+namespace {
+
+// Apply one gate to a 2^k vector in block coordinates (bit j = pos[j]).
+void apply_in_block(const PGate &g, const int *pos, int k, std::complex<double> *v) {
+    auto loc = [&](int b) {
+        for (int j = 0; j < k; j++)
+            if (pos[j] == b) return j;
+        return -1;
+    };
+    uint32_t cm = 0;
+    for (int b = 0; b < 64; b++)
+        if ((g.cmask >> b) & 1ull) cm |= 1u << loc(b);
+    const uint32_t D = 1u << k;
+    if (g.kind == QSIM_GATE_SWAP) {
+        const uint32_t b0 = 1u << loc(g.t0), b1 = 1u << loc(g.t1);
+        for (uint32_t i = 0; i < D; i++) {
+            if (!(i & b0) || (i & b1) || (i & cm) != cm) continue;
+            std::swap(v[i], v[(i & ~b0) | b1]);
+        }
+        return;
+    }
+    const uint32_t bt = 1u << loc(g.t0);
+    const std::complex<double> u00(g.U.u[0], g.U.u[1]), u01(g.U.u[2], g.U.u[3]);
+    const std::complex<double> u10(g.U.u[4], g.U.u[5]), u11(g.U.u[6], g.U.u[7]);
+    for (uint32_t i = 0; i < D; i++) {
+        if ((i & bt) || (i & cm) != cm) continue;
+        const std::complex<double> a0 = v[i], a1 = v[i | bt];
+        v[i] = u00 * a0 + u01 * a1;
+        v[i | bt] = u10 * a0 + u11 * a1;
+    }
+}
+
+uint64_t block_bits(const PGate &g) {
+    uint64_t m = g.cmask | (1ull << g.t0);
+    if (g.t1 >= 0) m |= 1ull << g.t1;
+    return m;
+}
+
+void emit_block(const std::vector<const PGate *> &gs, uint64_t mask, int n, int k, std::vector<FusedBlock> &out) {
+    FusedBlock b;
+    b.k = k;
+    int j = 0;
+    for (int q = 0; q < 64 && j < k; q++)
+        if ((mask >> q) & 1ull) b.pos[j++] = q;
+    for (int q = 0; q < n && j < k; q++)  // pad with the lowest other qubits
+        if (!((mask >> q) & 1ull)) b.pos[j++] = q;
+    std::sort(b.pos, b.pos + k);
+    const uint32_t D = 1u << k;
+    std::vector<std::complex<double>> col(D);
+    b.U.assign(2 * (size_t)D * D, 0.0);
+    for (uint32_t c = 0; c < D; c++) {  // column c of U = the block applied to |c>
+        std::fill(col.begin(), col.end(), std::complex<double>(0.0, 0.0));
+        col[c] = 1.0;
+        for (const PGate *g : gs) apply_in_block(*g, b.pos, k, col.data());
+        for (uint32_t r = 0; r < D; r++) {
+            b.U[2 * (r * D + c)] = col[r].real();
+            b.U[2 * (r * D + c) + 1] = col[r].imag();
+        }
+    }
+    b.flops = 8.0 * D * std::ldexp(1.0, n);
+    out.push_back(std::move(b));
+}
+
+}  // namespace
+
+void plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out) {
+    out.clear();
+    std::vector<const PGate *> cur;
+    uint64_t mask = 0;
+    for (const PGate &g : gates) {
+        const uint64_t m = block_bits(g);
+        if (__builtin_popcountll(mask | m) <= k) {
+            mask |= m;
+            cur.push_back(&g);
+        } else {
+            emit_block(cur, mask, n, k, out);
+            cur.assign(1, &g);
+            mask = m;
+        }
+    }
+    if (!cur.empty()) emit_block(cur, mask, n, k, out);
+}
+
+bool fused_geometry(int n, int k, const int *pos, TileGeom &g, FusedMap &fm) {
+    const int T = k + 7;
+    if (n < T || k > 8) return false;
+    uint64_t F = 0;
+    for (int j = 0; j < k; j++) F |= 1ull << pos[j];
+    int L = T < 11 ? T : 11;  // bulk copies of at most 16 KiB
+    while (L > 1 && L + __builtin_popcountll(F & ~((1ull << L) - 1ull)) > T) L--;
+    uint64_t hm = F & ~((1ull << L) - 1ull);
+    for (int b = L; b < n && __builtin_popcountll(hm) < T - L; b++)
+        if (!((F >> b) & 1ull)) hm |= 1ull << b;
+    if (__builtin_popcountll(hm) != T - L || T - L > 10) return false;
+    g = TileGeom{};
+    g.n = n;
+    g.L = L;
+    g.H = T - L;
+    int h = 0;
+    for (int b = 0; b < 64; b++)
+        if ((hm >> b) & 1ull) g.hb[h++] = b;
+    auto local = [&](int b) {
+        if (b < L) return b;
+        for (int j = 0; j < g.H; j++)
+            if (g.hb[j] == b) return L + j;
+        return -1;
+    };
+    uint32_t colmask = 0;
+    for (int j = 0; j < k; j++) {
+        fm.col[j] = (int8_t)local(pos[j]);
+        colmask |= 1u << fm.col[j];
+    }
+    int r = 0;
+    for (int b = 0; b < T; b++)
+        if (!((colmask >> b) & 1u)) fm.row[r++] = (int8_t)b;
+    return r == T - k;
 }
 
 }  // namespace qsim

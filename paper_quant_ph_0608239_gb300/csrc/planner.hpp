@@ -37,6 +37,7 @@ struct PassPlan {
     int op_begin, op_count;       // range in the plan's op array
     int phase_begin, phase_count; // range in the plan's phase array (0 phases: shared-memory kernel)
     double flops;                 // algorithmic flops of the pass
+    bool arith;                   // some op does arithmetic (not only data movement)
 };
 
 // Algorithmic real flops of one gate over an n-qubit state: 14 per amplitude
@@ -65,6 +66,20 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
 // Cut one pass's op list into register phases (see k_tile2.cu).
 void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vector<TileOp> &ops_out,
                   std::vector<TilePhase> &phases_out);
+
+// Dense fusion: consecutive gates grouped into blocks acting on at most k
+// qubits; each block's 2^k x 2^k unitary is the FP64 product of its gates.
+struct FusedBlock {
+    int k;
+    int pos[8];               // physical bits, bit j of U's index = pos[j]
+    std::vector<double> U;    // 2^k x 2^k complex, row-major (re, im)
+    double flops;             // algorithmic flops: 8 * 2^k per amplitude
+};
+void plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out);
+
+// Tile geometry of a fused block on the tensor cores: T = k + 7 bits holding
+// the block's qubits; false if n is too small.
+bool fused_geometry(int n, int k, const int *pos, TileGeom &g, FusedMap &fm);
 
 // Translate one gate into a tile op for a pass with geometry g.
 bool make_tile_op(const PGate &pg, const TileGeom &g, TileOp &op);

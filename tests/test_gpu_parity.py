@@ -308,6 +308,65 @@ def test_apply_fused_dense(q, dt, k):
     st.free()
 
 
+# ---------------------------------------- fused gates on the tensor cores
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n,where", [(12, "low"), (16, "high"), (16, "mixed"), (20, "mixed")])
+def test_fused_tensor_cores_c64(q, k, n, where):
+    rng = np.random.default_rng(70 + 10 * k + n)
+    if where == "low":
+        qs = list(rng.permutation(k))
+    elif where == "high":
+        qs = [int(x) for x in rng.permutation(np.arange(n - k, n))]
+    else:
+        qs = [int(x) for x in rng.permutation(n)[:k]]
+    Z = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+    U, _ = np.linalg.qr(Z)
+    psi = rand_state(n, 90 + n)
+    ref = oracle.apply_dense(psi.astype(np.complex64).astype(np.complex128), n, qs, U)
+    st = q.State(n, "c64")
+    st.set_state(psi)
+    st.profile(True)
+    st.apply_fused(qs, U)
+    prof = st.profile_read()
+    assert "fused_tensor_core" in prof, prof  # the tcgen05 kernel ran
+    e = err(st.get_state(), ref)
+    # 3xTF32 keeps about 2^-21 relative per product; amplitudes are <= 1
+    assert e < 2e-5, e
+    st.free()
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n", [13, 18])
+def test_fused_blocks_circuit_c64(q, k, n):
+    gates = inputs.random_circuit(n, 6, seed=200 + n)
+    rng = np.random.default_rng(n)
+    gates += [g for g in controlled_gates(rng, n, 12) if len(g.controls) + len(g.targets) <= k]
+    x0 = inputs.random_basis(n, seed=n + 1)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, "c64")
+    st.set_basis(x0)
+    st.profile(True)
+    st.run(gates, fuse_k=k)
+    prof = st.profile_read()
+    assert "fused_tensor_core" in prof and "tile_pass" not in prof
+    e = err(st.get_state(), ref)
+    assert e < 2e-5, e
+    st.free()
+
+
+def test_fused_blocks_adder_exact(q):
+    values, m = [45, 17], 7
+    n = 2 * m
+    gates = inputs.adder_circuit(values, m)
+    st = q.State(n, "c64")
+    st.run(gates, fuse_k=5)
+    qp = st.qubit_probs()
+    want = inputs.adder_expected_index(values, m)
+    assert sum(1 << b for b in range(n) if qp[b] > 0.5) == want
+    assert np.max(np.minimum(qp, 1 - qp)) < 1e-4
+    st.free()
+
+
 # ------------------------------------------------------------- reductions
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [3, 9, 10, 16, 21])
