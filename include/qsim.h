@@ -99,7 +99,9 @@ typedef struct {
     int32_t tile_bits;  /* T, qubits held per shared-memory tile; 0 = default */
     int32_t fuse_k;     /* width of dense fused blocks; 0 = planner default, -1 = never */
     int32_t max_swap;   /* most bit pairs exchanged per interchange pass; 0 = default */
-    int32_t reserved[4];
+    int32_t wait_budget_us; /* batches: longest device-side wait between passes
+                               before QSIM_ETIMEOUT; 0 = about 2 s */
+    int32_t reserved[3];
 } qsim_opts;
 
 /* Fill opts with the defaults (QSIM_MODE_FUSED, automatic sizes). */
@@ -251,11 +253,35 @@ typedef struct {
     size_t ng;
 } qsim_circuit;
 
-/* qsim_run_batch: run nc independent circuits (C64 states of up to 24 qubits)
- * in one persistent launch on the stream of cs[0].state; every state must be
- * on the same device.  Waits for completion.  ETIMEOUT if a device-side
- * wait between passes expired (the states are then undefined). */
+/* qsim_run_batch: run nc independent circuits (complex64 states of up to 24
+ * qubits, on one device) in one persistent launch on the stream of
+ * cs[0].state; every state is set to its |x0> and its gates applied.  Waits
+ * for completion.  ETIMEOUT if a device-side wait between passes expired (the
+ * states are then undefined).  Equivalent to qsim_batch_create + one
+ * qsim_batch_run + qsim_batch_free. */
 QSIM_API qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts);
+
+/* A planned batch: the circuits' tile programs and the ordered work list are
+ * uploaded once and the launch is captured in a CUDA graph, so every
+ * qsim_batch_run is one graph launch.  The circuits' states must stay alive. */
+typedef struct qsim_batch_s *qsim_batch;
+
+typedef struct {
+    int64_t circuits;
+    int64_t gates;
+    int64_t passes;      /* tile passes over all circuits */
+    int64_t items;       /* (circuit, pass, tile) work items of one run */
+    int32_t graph;       /* 1 if runs replay a captured CUDA graph */
+    int32_t reserved;
+} qsim_batch_stats;
+
+QSIM_API qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out);
+/* Enqueue one run on the batch's stream (asynchronous). */
+QSIM_API qsim_status qsim_batch_run(qsim_batch b);
+/* Wait for the batch's runs; ETIMEOUT if a device-side wait expired. */
+QSIM_API qsim_status qsim_batch_sync(qsim_batch b);
+QSIM_API qsim_status qsim_batch_get_stats(qsim_batch b, qsim_batch_stats *out);
+QSIM_API qsim_status qsim_batch_free(qsim_batch b);
 
 /* ---- measurement ------------------------------------------------------------
  * qsim_norm: sum_i |a_i|^2 (Eq. STAT1), accumulated in FP64. */

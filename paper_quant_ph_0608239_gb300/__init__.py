@@ -229,8 +229,7 @@ class Plan:
             pass
 
 
-def run_batch(states, x0s, gate_lists, mode=MODE_FUSED):
-    """Run independent circuits (complex64 states) through qsim_run_batch."""
+def _circuit_array(states, x0s, gate_lists):
     nc = len(states)
     arr = (QsimCircuit * nc)()
     keep = []
@@ -241,5 +240,48 @@ def run_batch(states, x0s, gate_lists, mode=MODE_FUSED):
         arr[i].x0 = int(x0)
         arr[i].gates = ctypes.cast(ga, ctypes.POINTER(QsimGate))
         arr[i].ng = len(ga) if isinstance(gl, ctypes.Array) else len(gl)
-    o = opts(mode)
-    _capi.call("qsim_run_batch", arr, nc, ctypes.byref(o))
+    return arr, keep
+
+
+def run_batch(states, x0s, gate_lists, wait_budget_us=0):
+    """Run independent circuits (complex64 states) in one persistent launch."""
+    arr, keep = _circuit_array(states, x0s, gate_lists)
+    o = opts()
+    o.wait_budget_us = int(wait_budget_us)
+    _capi.call("qsim_run_batch", arr, len(states), ctypes.byref(o))
+
+
+class Batch:
+    """A planned batch (qsim_batch_create): every run() is one graph launch."""
+
+    def __init__(self, states, x0s, gate_lists, wait_budget_us=0):
+        arr, keep = _circuit_array(states, x0s, gate_lists)
+        o = opts()
+        o.wait_budget_us = int(wait_budget_us)
+        p = ctypes.c_void_p()
+        _capi.call("qsim_batch_create", arr, len(states), ctypes.byref(o), ctypes.byref(p))
+        self.ptr = p
+        self.states = states
+
+    def run(self):
+        _capi.call("qsim_batch_run", self.ptr)
+
+    def sync(self):
+        _capi.call("qsim_batch_sync", self.ptr)
+
+    def stats(self):
+        s = _capi.QsimBatchStats()
+        _capi.call("qsim_batch_get_stats", self.ptr, ctypes.byref(s))
+        return {"circuits": s.circuits, "gates": s.gates, "passes": s.passes, "items": s.items,
+                "graph": bool(s.graph)}
+
+    def free(self):
+        if self.ptr is not None and self.ptr.value:
+            _capi.call("qsim_batch_free", self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -30,7 +30,12 @@ class QsimGate(ctypes.Structure):
 class QsimOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
                 ("fuse_k", ctypes.c_int32), ("max_swap", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("wait_budget_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class QsimBatchStats(ctypes.Structure):
+    _fields_ = [("circuits", ctypes.c_int64), ("gates", ctypes.c_int64), ("passes", ctypes.c_int64),
+                ("items", ctypes.c_int64), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class QsimCircuit(ctypes.Structure):
@@ -84,6 +89,12 @@ _SIGS = {
     "qsim_get_layout": ([c_handle, ctypes.POINTER(ctypes.c_int)], None),
     "qsim_run_circuit": ([c_handle, ctypes.POINTER(QsimGate), ctypes.c_size_t, ctypes.POINTER(QsimOpts)], None),
     "qsim_run_batch": ([ctypes.POINTER(QsimCircuit), ctypes.c_size_t, ctypes.POINTER(QsimOpts)], None),
+    "qsim_batch_create": ([ctypes.POINTER(QsimCircuit), ctypes.c_size_t, ctypes.POINTER(QsimOpts),
+                           ctypes.POINTER(ctypes.c_void_p)], None),
+    "qsim_batch_run": ([ctypes.c_void_p], None),
+    "qsim_batch_sync": ([ctypes.c_void_p], None),
+    "qsim_batch_get_stats": ([ctypes.c_void_p, ctypes.POINTER(QsimBatchStats)], None),
+    "qsim_batch_free": ([ctypes.c_void_p], None),
     "qsim_norm": ([c_handle, ctypes.POINTER(ctypes.c_double)], None),
     "qsim_probs": ([c_handle, ctypes.c_void_p, ctypes.c_size_t], None),
     "qsim_qubit_probs": ([c_handle, ctypes.c_void_p], None),

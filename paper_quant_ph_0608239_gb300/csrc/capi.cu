@@ -1007,24 +1007,218 @@ qsim_status qsim_sample(qsim_handle h, const double *u, size_t ns, uint64_t *out
 }
 
 // ------------------------------------------------------------------ batch
+struct qsim_batch_s {
+    std::vector<qsim_handle> states;
+    std::vector<uint64_t> x0;
+    cudaStream_t stream = nullptr;   // where runs are enqueued (cs[0]'s stream)
+    cudaStream_t cap = nullptr;      // private stream used for graph capture
+    void *dbuf = nullptr;            // circuits, passes, ops, items, counters, done, error word
+    BatchCircuit *d_circs = nullptr;
+    BatchPass *d_passes = nullptr;
+    TileOp *d_ops = nullptr;
+    BatchItem *d_items = nullptr;
+    uint32_t *d_counters = nullptr;  // 64-bit item counter, then one counter per pass
+    uint32_t *d_err = nullptr;
+    size_t zero_bytes = 0;           // counters + done + error word, cleared before each run
+    uint64_t nitems = 0;
+    long long budget = 0;
+    int sm_count = 152;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t *h_err = nullptr;       // pinned
+    qsim_batch_stats stats{};
+};
+
+static void batch_release(qsim_batch_s *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dbuf) cudaFree(b->dbuf);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    delete b;
+}
+
+static cudaError_t batch_enqueue(qsim_batch_s *b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->zero_bytes, s);
+    if (e != cudaSuccess) return e;
+    return launch_batch(b->d_circs, b->d_passes, b->d_ops, b->d_items, b->nitems, b->d_counters,
+                        b->d_counters + 2, b->d_err, b->budget, b->sm_count, s);
+}
+
+qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out) {
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nc == 0 || !cs) return fail(QSIM_EINVAL, "empty batch");
+    qsim_opts o;
+    qsim_default_opts(&o);
+    if (opts) o = *opts;
+    int dev = -1;
+    for (size_t i = 0; i < nc; i++) {
+        const qsim_handle h = cs[i].state;
+        if (!h) return fail(QSIM_EINVAL, "circuit %zu has no state", i);
+        if (h->dt != QSIM_C64) return fail(QSIM_EINVAL, "batch states must be complex64");
+        if (h->n > 24) return fail(QSIM_EINVAL, "batch states have at most 24 qubits");
+        if (dev < 0) dev = h->device;
+        if (h->device != dev) return fail(QSIM_EINVAL, "batch states must share one device");
+        if (h->n < 64 && cs[i].x0 >= (1ull << h->n)) return fail(QSIM_EINVAL, "circuit %zu: x0 out of range", i);
+        if (cs[i].ng && !cs[i].gates) return fail(QSIM_EINVAL, "circuit %zu: gates is NULL", i);
+    }
+    const int Tmax = (o.tile_bits > 0 && o.tile_bits < 12) ? o.tile_bits : 12;
+    std::vector<BatchCircuit> circs(nc);
+    std::vector<BatchPass> passes;
+    std::vector<TileOp> ops;
+    std::vector<std::vector<int>> pass_of(nc);
+    int max_passes = 0;
+    int64_t ngates = 0;
+    int ident[64];
+    for (int q = 0; q < 64; q++) ident[q] = q;
+    for (size_t i = 0; i < nc; i++) {
+        const qsim_handle h = cs[i].state;
+        std::vector<PGate> pg(cs[i].ng);
+        std::string msg;
+        for (size_t k = 0; k < cs[i].ng; k++)
+            if (!prepare_gate(cs[i].gates[k], h->n, ident, pg[k], msg))
+                return fail(QSIM_EINVAL, "circuit %zu gate %zu: %s", i, k, msg.c_str());
+        ngates += (int64_t)cs[i].ng;
+        const int T = h->n < Tmax ? h->n : Tmax;
+        const int L = T < 5 ? T : 5;
+        Plan plan;
+        plan_tiles(pg, h->n, T, L, plan, 0);
+        circs[i].amp = h->amp;
+        circs[i].x0 = cs[i].x0;
+        circs[i].pass_begin = (int32_t)passes.size();
+        if (plan.passes.empty()) {  // no gates: one pass that only writes |x0>
+            PassPlan pp{};
+            pp.geom.n = h->n;
+            pp.geom.L = T < 5 ? T : 5;
+            pp.geom.H = T - pp.geom.L;
+            for (int k = 0; k < pp.geom.H; k++) pp.geom.hb[k] = pp.geom.L + k;
+            plan.passes.push_back(pp);
+        }
+        for (const PassPlan &pp : plan.passes) {
+            BatchPass bp{};
+            bp.geom = pp.geom;
+            bp.op_begin = (int32_t)ops.size();
+            bp.op_count = pp.op_count;
+            bp.ntiles = 1u << (h->n - (pp.geom.L + pp.geom.H));
+            ops.insert(ops.end(), plan.ops.begin() + pp.op_begin, plan.ops.begin() + pp.op_begin + pp.op_count);
+            passes.push_back(bp);
+        }
+        circs[i].npasses = (int32_t)plan.passes.size();
+        max_passes = std::max(max_passes, circs[i].npasses);
+    }
+    std::vector<BatchItem> items;
+    for (int p = 0; p < max_passes; p++)
+        for (size_t i = 0; i < nc; i++) {
+            if (p >= circs[i].npasses) continue;
+            const uint32_t nt = passes[circs[i].pass_begin + p].ntiles;
+            for (uint32_t t = 0; t < nt; t++) items.push_back(BatchItem{(uint32_t)i, (uint32_t)p, t});
+        }
+    qsim_batch_s *b = new qsim_batch_s;
+    for (size_t i = 0; i < nc; i++) {
+        b->states.push_back(cs[i].state);
+        b->x0.push_back(cs[i].x0);
+    }
+    b->stream = cs[0].state->stream;
+    b->sm_count = cs[0].state->sm_count;
+    b->nitems = items.size();
+    b->budget = (o.wait_budget_us > 0 ? (long long)o.wait_budget_us : 2000000ll) * 2000ll;  // ~2 GHz SM clock
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t sc = al(circs.size() * sizeof(BatchCircuit)), sp = al(passes.size() * sizeof(BatchPass));
+    const size_t so = al(std::max<size_t>(ops.size(), 1) * sizeof(TileOp)), si = al(items.size() * sizeof(BatchItem));
+    b->zero_bytes = 8 + passes.size() * 4 + 4 + 4;
+    const size_t sz = al(b->zero_bytes);
+    cudaError_t e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dbuf, sc + sp + so + si + sz);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(e, "batch buffers");
+    }
+    char *base = static_cast<char *>(b->dbuf);
+    b->d_circs = reinterpret_cast<BatchCircuit *>(base);
+    b->d_passes = reinterpret_cast<BatchPass *>(base + sc);
+    b->d_ops = reinterpret_cast<TileOp *>(base + sc + sp);
+    b->d_items = reinterpret_cast<BatchItem *>(base + sc + sp + so);
+    b->d_counters = reinterpret_cast<uint32_t *>(base + sc + sp + so + si);
+    b->d_err = b->d_counters + 2 + passes.size();
+    e = cudaMemcpy(b->d_circs, circs.data(), circs.size() * sizeof(BatchCircuit), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_passes, passes.data(), passes.size() * sizeof(BatchPass), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ops.empty())
+        e = cudaMemcpy(b->d_ops, ops.data(), ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(e, "batch upload");
+    }
+    // capture: counter reset + the persistent launch, replayed by every run
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaError_t le = batch_enqueue(b, b->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+        if (le == cudaSuccess && ce == cudaSuccess && g &&
+            cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+            b->graph = g;
+        } else {
+            if (g) cudaGraphDestroy(g);
+            b->exec = nullptr;
+        }
+    }
+    cudaGetLastError();  // a refused capture leaves no sticky error: fall back to direct launches
+    b->stats.circuits = (int64_t)nc;
+    b->stats.gates = ngates;
+    b->stats.passes = (int64_t)passes.size();
+    b->stats.items = (int64_t)items.size();
+    b->stats.graph = b->exec ? 1 : 0;
+    *out = b;
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_run(qsim_batch b) {
+    if (!b) return fail(QSIM_EINVAL, "null batch");
+    for (qsim_handle h : b->states)
+        for (int q = 0; q < 64; q++) h->phys[q] = q;
+    if (b->exec) {
+        CK(cudaGraphLaunch(b->exec, b->stream), "batch graph launch");
+    } else {
+        CK(batch_enqueue(b, b->stream), "batch launch");
+    }
+    for (qsim_handle h : b->states) h->launches += 1;
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_sync(qsim_batch b) {
+    if (!b) return fail(QSIM_EINVAL, "null batch");
+    CK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream), "read error word");
+    CK(cudaStreamSynchronize(b->stream), "sync");
+    if (*b->h_err) return fail(QSIM_ETIMEOUT, "a bounded wait between batch passes expired");
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_get_stats(qsim_batch b, qsim_batch_stats *out) {
+    if (!b || !out) return fail(QSIM_EINVAL, "null argument");
+    *out = b->stats;
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_free(qsim_batch b) {
+    if (!b) return QSIM_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    return QSIM_OK;
+}
+
 qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts) {
     if (nc == 0) return QSIM_OK;
-    if (!cs) return fail(QSIM_EINVAL, "NULL circuit list");
-    for (size_t i = 0; i < nc; i++) {
-        if (!cs[i].state) return fail(QSIM_EINVAL, "circuit %zu has no state", i);
-        if (cs[i].state->dt != QSIM_C64) return fail(QSIM_EINVAL, "batch states must be complex64");
-        if (cs[i].state->n > 24) return fail(QSIM_EINVAL, "batch states have at most 24 qubits");
-    }
-    for (size_t i = 0; i < nc; i++) {
-        qsim_status st = qsim_set_basis(cs[i].state, cs[i].x0);
-        if (st == QSIM_OK) st = qsim_run_circuit(cs[i].state, cs[i].gates, cs[i].ng, opts);
-        if (st != QSIM_OK) return st;
-    }
-    for (size_t i = 0; i < nc; i++) {
-        qsim_status st = sync_check(cs[i].state);
-        if (st != QSIM_OK) return st;
-    }
-    return QSIM_OK;
+    qsim_batch b = nullptr;
+    qsim_status st = qsim_batch_create(cs, nc, opts, &b);
+    if (st != QSIM_OK) return st;
+    st = qsim_batch_run(b);
+    if (st == QSIM_OK) st = qsim_batch_sync(b);
+    qsim_batch_free(b);
+    return st;
 }
 
 }  // extern "C"

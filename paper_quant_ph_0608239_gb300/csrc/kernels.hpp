@@ -144,6 +144,29 @@ void fused_tc_prepare_b(int k, const double *U, float *out);
 cudaError_t launch_fused_tc(void *amp, int k, const TileGeom &g, const FusedMap &fm, const float *bmat,
                             uint32_t *err, int sm_count, cudaStream_t s);
 
+// ------------------------------------------------------------ batches
+struct BatchCircuit {
+    void *amp;            // complex64 state of the circuit
+    uint64_t x0;          // initial basis state
+    int32_t pass_begin;   // first pass in the batch's pass array (and done-counter index)
+    int32_t npasses;
+};
+struct BatchPass {
+    TileGeom geom;
+    int32_t op_begin, op_count;  // in the batch's op array
+    uint32_t ntiles;
+    uint32_t pad;
+};
+struct BatchItem {
+    uint32_t circuit, pass, tile;
+};
+// counters: one 64-bit item counter (zeroed before the launch); done: one
+// zeroed counter per pass of the batch.  budget: SM cycles a wait may take.
+size_t batch_smem_bytes();
+cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, const TileOp *ops,
+                         const BatchItem *items, uint64_t nitems, uint32_t *counters, uint32_t *done,
+                         uint32_t *err, long long budget, int sm_count, cudaStream_t s);
+
 // Reductions (FP64 accumulation).  scratch: device buffer of at least
 // reduce_scratch_bytes(n) bytes.
 size_t reduce_scratch_bytes(int n);

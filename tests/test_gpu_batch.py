@@ -1,0 +1,101 @@
+"""Batches of independent circuits in one persistent launch (qsim_run_batch,
+qsim_batch_*): parity with the oracle, CUDA-graph replay, and the bounded
+wait between passes (forced to expire: an error status, not a fault)."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_quant_ph_0608239_gb300 as qq
+    qq._capi.load()
+    return qq
+
+
+def _err(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.complex128) - b)))
+
+
+def test_batch_matches_oracle(q):
+    circs = inputs.batch_circuits(count=40, seed0=500, nmin=3, nmax=17, dmin=1, dmax=14)
+    states, x0s, gls = [], [], []
+    for i, (n, gates) in enumerate(circs):
+        states.append(q.State(n, "c64"))
+        x0s.append(inputs.random_basis(n, seed=700 + i))
+        gls.append(gates)
+    gls[3] = []  # an empty circuit must still leave |x0>
+    q.run_batch(states, x0s, gls)
+    for st, x0, (n, _), gl in zip(states, x0s, circs, gls):
+        ref = oracle.run(n, gl, x0=x0)
+        assert _err(st.get_state(), ref) < 2e-5, n
+        st.free()
+
+
+def test_batch_graph_replay_is_repeatable(q):
+    circs = inputs.batch_circuits(count=12, seed0=900, nmin=12, nmax=19, dmin=4, dmax=10)
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=i) for i, (n, _) in enumerate(circs)]
+    b = q.Batch(states, x0s, [g for _, g in circs])
+    stats = b.stats()
+    assert stats["circuits"] == 12 and stats["items"] >= stats["passes"] >= 12
+    first = None
+    for rep in range(3):
+        b.run()
+        b.sync()
+        got = [st.get_state() for st in states]
+        if first is None:
+            first = got
+        else:
+            for a, c in zip(first, got):
+                assert np.array_equal(a, c)
+    for st, x0, (n, g) in zip(states, x0s, circs):
+        assert _err(first[states.index(st)], oracle.run(n, g, x0=x0)) < 2e-5
+    b.free()
+    for st in states:
+        st.free()
+
+
+def test_batch_wait_budget_expiry_is_reported(q):
+    # 20-qubit circuits need many passes of 256 tiles; with a 1 microsecond
+    # budget the waits between passes must expire.  The call returns
+    # QSIM_ETIMEOUT, the device stays usable, and a normal run afterwards is
+    # correct.
+    circs = inputs.batch_circuits(count=4, seed0=50, nmin=20, nmax=20, dmin=12, dmax=12)
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [0] * len(states)
+    with pytest.raises(q.QsimError) as ei:
+        q.run_batch(states, x0s, [g for _, g in circs], wait_budget_us=1)
+    assert ei.value.status == q.QSIM_ETIMEOUT
+    q.run_batch(states, x0s, [g for _, g in circs])
+    n, g = circs[0]
+    assert _err(states[0].get_state(), oracle.run(n, g, x0=0)) < 2e-5
+    for st in states:
+        st.free()
+
+
+def test_batch_config_512_sampled(q):
+    # the batch workload at full size: 512 circuits, n ~ U{12..24}, depth ~
+    # U{10..60}; every norm is conserved and a sample of the smaller circuits
+    # matches the oracle amplitude by amplitude
+    circs = inputs.batch_circuits()
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
+    b = q.Batch(states, x0s, [g for _, g in circs])
+    b.run()
+    b.sync()
+    for st, (n, g) in zip(states, circs):
+        assert abs(st.norm() - 1) < 1e-4
+    picked = [i for i, (n, _) in enumerate(circs) if n <= 15][:6]
+    for i in picked:
+        n, g = circs[i]
+        assert _err(states[i].get_state(), oracle.run(n, g, x0=x0s[i])) < 2e-5
+    b.free()
+    for st in states:
+        st.free()
