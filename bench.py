@@ -50,6 +50,9 @@ WORKLOADS = {
                        text="10-qubit QFT with reversal swaps on a seeded basis state, complex128"),
     "hadamard30_c128": dict(kind="hadamard", n=30, dtype="c128",
                             text="Hadamard on every qubit of 30 qubits (the paper's scaling test), complex128"),
+    "batch512_c64": dict(kind="batch", n=24, dtype="c64",
+                         text="batch of 512 seeded random circuits, n ~ U{12..24}, depth ~ U{10..60}, complex64, "
+                              "one persistent graph-captured launch"),
 }
 
 # Peaks: measured copy bandwidth from MEASURED_PEAKS.json; ALU peaks are the
@@ -57,6 +60,11 @@ WORKLOADS = {
 # FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# complex128 runs in double-float on the FP32 pipes: the FP32 issue rate
+# (152 SMs x 128 lanes x 2.07 GHz) over the 6.2 FP32 instructions the
+# double-float formulas spend per algorithmic FP64 flop (dense 2x2: 86
+# instructions for 14 flops per amplitude; real 2x2, phase, diagonal: 6.3)
+DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 6.2 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -261,7 +269,7 @@ def run_ours(args, w, ws, rank, local):
     per_launch_s = ms / nl / 1e3
     gbs = by / nl / per_launch_s / 1e9
     tflops = fl / nl / per_launch_s / 1e12
-    alu_peak = FP64_PEAK_TFLOPS if w["dtype"] == "c128" else FP32_PEAK_TFLOPS
+    alu_peak = DF64_PEAK_TFLOPS if w["dtype"] == "c128" else FP32_PEAK_TFLOPS
     frac_hbm, frac_alu = gbs / hbm_peak, tflops / alu_peak
     traffic = ncu_traffic(fam, args.workload)
     hbm_roof = {"bound": "hbm", "kernel": fam, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -269,7 +277,9 @@ def run_ours(args, w, ws, rank, local):
                 "alg_bytes_per_launch": by / nl, "launches": nl, "avg_launch_ms": ms / nl}
     alu_roof = {"bound": "alu", "kernel": fam, "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": frac_alu, "traffic": traffic,
-                "peak_source": ("nominal GB300 FP64" if w["dtype"] == "c128" else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
+                "peak_source": ("double-float on the FP32 pipes: 152 SM x 128 lanes x 2.07 GHz / 6.2 FP32 "
+                                "instructions per emulated FP64 flop" if w["dtype"] == "c128"
+                                else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
                 "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
     roof, other = (alu_roof, hbm_roof) if frac_alu > frac_hbm else (hbm_roof, alu_roof)
 
@@ -339,6 +349,22 @@ def companions(q, w, gates, x0, args):
         plan.free()
         st.free()
         torch.cuda.empty_cache()
+    # the same circuit fused into 5-qubit blocks on the tensor cores (complex64)
+    st = q.State(n, "c64")
+    plan = st.plan(gates, fuse_k=5)
+    st.set_basis(x0)
+    plan.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.set_basis(x0)
+    plan.run()
+    st.qubit_probs()
+    el = time.perf_counter() - t0
+    res["fused_tensor_core_k5_c64"] = {"gates_per_s": ng / el, "ms_per_step": el * 1e3,
+                                       "blocks": plan.stats()["passes"]}
+    plan.free()
+    st.free()
+    torch.cuda.empty_cache()
     # per-gate FP64 path, timed on the first two layers of the circuit
     sub = gates[: 2 * (n + n // 2)] if w["kind"] == "random" else gates[:64]
     st = q.State(n, "c128")
@@ -354,12 +380,84 @@ def companions(q, w, gates, x0, args):
     return res
 
 
+def run_batch_workload(args, w, ws, rank, local):
+    """Batch config: one step = one replay of the captured persistent launch."""
+    import torch
+    import paper_quant_ph_0608239_gb300 as q
+    torch.cuda.set_device(local)
+    circs = inputs.batch_circuits()
+    ng = sum(len(g) for _, g in circs)
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
+    b = q.Batch(states, x0s, [g for _, g in circs])
+    bst = b.stats()
+    for _ in range(args.warmup):
+        b.run()
+    b.sync()
+    c0 = sum(st.counters()["launches"] for st in states)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.run()
+    e1.record(stream)
+    b.sync()
+    clk = clocks.stop()
+    el = e0.elapsed_time(e1) / 1e3
+    launches = args.steps  # one cooperative launch (graph replay) per step
+    # baseline of the comparison: one planned run per circuit
+    plans = [st.plan(g) for st, (_, g) in zip(states, circs)]
+    for st, p, x0 in zip(states, plans, x0s):
+        st.set_basis(x0)
+        p.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for st, p, x0 in zip(states, plans, x0s):
+        st.set_basis(x0)
+        p.run()
+    torch.cuda.synchronize()
+    per_circuit = ng / (time.perf_counter() - t0)
+    for p in plans:
+        p.free()
+    # e2e: planning, upload and the run through qsim_run_batch, gate lists in host memory
+    arrs = [q.gate_array(g) for _, g in circs]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.run_batch(states, x0s, arrs)
+    e2e = ng * args.steps / (time.perf_counter() - t0)
+    h2d = sum(len(g) for _, g in circs) * 112  # qsim_gate records read by the planner
+    out = {
+        "metric": METRIC, "value": ng * args.steps / el, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
+        "config": {"workload": w["text"], "name": args.workload, "circuits": len(circs), "gates": ng,
+                   "tile_passes": bst["passes"], "work_items": bst["items"], "cuda_graph": bst["graph"],
+                   "l2": "inputs larger than L2 (batch states %d MiB)" % (sum(st.nbytes for st in states) >> 20),
+                   "parallelism": "replicas x%d" % ws},
+        "one_launch_per_circuit_gates_per_s": per_circuit,
+        "e2e": {"value": e2e, "unit": "gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    b.free()
+    for st in states:
+        st.free()
+    return out if rank == 0 else None
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args, w, ws, rank):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     if rank != 0:
         return None
-    gates, x0 = workload_gates(w)
+    if w["kind"] == "batch":  # the oracle on the batch's circuits in order
+        circs = inputs.batch_circuits()
+        w = dict(w, n=circs[0][0])
+        gates, x0 = circs[0][1], 0
+    else:
+        gates, x0 = workload_gates(w)
     budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(w, gates, x0, budget / 4)
@@ -404,6 +502,8 @@ def main():
         args.workload = args.workload + "_n%d" % args.n
     if args.impl == "reference":
         out = run_reference(args, w, ws, rank)
+    elif w["kind"] == "batch":
+        out = run_batch_workload(args, w, ws, rank, local)
     else:
         out = run_ours(args, w, ws, rank, local)
     if rank == 0 and out is not None:

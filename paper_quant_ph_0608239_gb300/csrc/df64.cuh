@@ -169,7 +169,8 @@ DF_HD df df_mul(df a, df b) {
 
 // Sum of n products a[k] * b[k] with one two-sum chain on the leading parts
 // and a plain float sum of all error terms: the building block of a complex
-// 2x2 update (n = 2 or 4).
+// 2x2 update (n = 2 or 4).  Per product: the rounded head, its exact error
+// (FMA) and the two cross terms; per added term one two-sum.
 template <int N>
 DF_HD df df_dot(const df (&a)[N], const df (&b)[N]) {
     float s = 0.0f, err = 0.0f;

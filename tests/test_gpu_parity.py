@@ -498,3 +498,22 @@ def test_full_size_random_circuit_then_inverse(q, n, depth, dt):
     tol = TOL[dt] * (1 if dt == "c128" else 2.5)
     assert abs(a0 - 1) < tol and rest < tol, (a0, rest)
     st.free()
+
+
+# ------------------------------------------------ Shor, Table Shortab (L = 24)
+@pytest.mark.parametrize("dt", DTYPES)
+def test_shor_table_L24_on_gpu(q, dt):
+    import golden_io
+    t = golden_io.shor_table()
+    X, L, G, y = t["X"], t["L"], t["G"], t["y"]
+    f = inputs.shor_initial_support(X, G, y)
+    a = np.zeros(1 << L, dtype=np.complex128)
+    a[np.arange(1 << X) + (f << X)] = 2.0 ** (-X / 2)   # Eq. Shor2
+    st = q.State(L, dt)
+    st.set_state(a)
+    st.run(inputs.qft(range(X), swaps=True))             # QFT on the x-register
+    qp = st.qubit_probs()                                # Eq. Shor7
+    np.testing.assert_allclose(qp[:X], t["Q"], atol=5e-4 + 1e-12)
+    ref = oracle.qubit_probs(oracle.run(L, inputs.qft(range(X), swaps=True), state=a.copy()), L)
+    np.testing.assert_allclose(qp, ref, atol=1e-12 if dt == "c128" else 1e-5)
+    st.free()
