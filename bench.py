@@ -314,6 +314,7 @@ def run_ours(args, w, ws, rank, local):
 
     if rank == 0 and ws == 1 and not args.no_companions and w["kind"] == "random":
         out["companions"] = companions(q, w, gates, x0, args)
+        out["single_gate_sweeps"] = single_gate_sweeps(q)
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, done, thr = oracle_sample(w, gates, x0, args.cpu_budget)
         out["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle",
@@ -323,6 +324,46 @@ def run_ours(args, w, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def single_gate_sweeps(q, n=30, targets=(0, 1, 2, 4, 8, 16, 29)):
+    """Per-gate sweeps of the whole state (the one-gate-per-sweep execution of
+    Sec. III.A), timed with CUDA events: effective GB/s per target bit for H,
+    a Haar SU(2), a phase shift and a CNOT, in complex64 and complex128."""
+    import torch
+    from inputs import Gate
+    hbm, _ = peaks()
+    out = {}
+    v = np.random.default_rng(0).standard_normal(4)
+    v /= np.linalg.norm(v)
+    for dt in ("c64", "c128"):
+        st = q.State(n, dt)
+        S = 8 if dt == "c64" else 16
+        res = {}
+        for name, mk, touched in (
+                ("H", lambda t: Gate("H", (t,), (), ()), 1.0),
+                ("SU2", lambda t: Gate("SU2", (t,), (), tuple(v)), 1.0),
+                ("R", lambda t: Gate("R", (t,), (), (0.3,)), 0.5),
+                ("CNOT", lambda t: Gate("NOT", (t,), ((t + 7) % n,), ()), 0.5)):
+            row = {}
+            for t in targets:
+                g = mk(t)
+                st.apply_gate(g)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream = torch.cuda.current_stream()
+                e0.record(stream)
+                for _ in range(3):
+                    st.apply_gate(g)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 3
+                gbs = 2.0 * S * touched * (1 << n) / (ms / 1e3) / 1e9
+                row[str(t)] = {"ms": round(ms, 3), "GBs": round(gbs, 1), "frac": round(gbs / hbm, 3)}
+            res[name] = row
+        out[dt] = res
+        st.free()
+        torch.cuda.empty_cache()
+    return out
 
 
 def companions(q, w, gates, x0, args):

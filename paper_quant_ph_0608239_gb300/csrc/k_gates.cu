@@ -11,6 +11,7 @@
 // target bit; the low target bits fall inside one 32-byte sector and are
 // merged by L1.
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.hpp"
 
 namespace qsim {
@@ -115,6 +116,120 @@ __global__ void __launch_bounds__(kThreads) k_diag(amp_t<R> *__restrict__ a, uin
         const uint64_t i = expand_n<NP>(p, fb);
         a[i] = cmul<R>(((i >> tbit) & 1) ? u1 : u0, a[i]);
     }
+}
+
+// ---- complex128 sweeps in double-float arithmetic ---------------------------
+// GB300 runs FP64 at about 1/58 of its FP32 rate, which makes an FP64 dense
+// 2x2 sweep arithmetic-bound at well under the memory bandwidth.  The
+// amplitudes stay IEEE double in memory; each sweep converts them to
+// double-float with integer operations (df64.cuh), applies the gate on the
+// FP32 pipes and converts back.  Pure exchanges never get here: they move
+// bytes and stay bit-exact.
+struct DfMat {
+    float h[8], l[8];
+};
+
+__device__ __forceinline__ dcx df_coef(const DfMat &M, int k) {
+    return dcx{df{M.h[2 * k], M.l[2 * k]}, df{M.h[2 * k + 1], M.l[2 * k + 1]}};
+}
+__device__ __forceinline__ dcx to_dcx(double2 v) { return dcx{df_from_double(v.x), df_from_double(v.y)}; }
+__device__ __forceinline__ double2 from_dcx(const dcx &v) {
+    return make_double2(df_to_double(v.re), df_to_double(v.im));
+}
+
+template <int GC, int NP>
+__global__ void __launch_bounds__(kThreads) k_pairs_df(double2 *__restrict__ a, uint64_t W, FixedBits fb,
+                                                       uint64_t pmask, DfMat M) {
+    const dcx u0 = df_coef(M, 0), u1 = df_coef(M, 1), u2 = df_coef(M, 2), u3 = df_coef(M, 3);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t p = (uint64_t)blockIdx.x * kThreads + threadIdx.x; p < W; p += 2 * stride) {
+        const bool two = p + stride < W;
+        const uint64_t i = expand_n<NP>(p, fb), j = two ? expand_n<NP>(p + stride, fb) : i;
+        const double2 ra = a[i], rb = a[i ^ pmask], rc = a[j], rd = a[j ^ pmask];
+        const dcx x0 = to_dcx(ra), y0 = to_dcx(rb), x1 = to_dcx(rc), y1 = to_dcx(rd);
+        dcx o0, o1, o2, o3;
+        if (GC == GC_GENERAL) {
+            o0 = dcx_mul2(u0, x0, u1, y0);
+            o1 = dcx_mul2(u2, x0, u3, y0);
+            o2 = dcx_mul2(u0, x1, u1, y1);
+            o3 = dcx_mul2(u2, x1, u3, y1);
+        } else if (GC == GC_REAL) {
+            o0 = dcx_rmul2(u0.re, x0, u1.re, y0);
+            o1 = dcx_rmul2(u2.re, x0, u3.re, y0);
+            o2 = dcx_rmul2(u0.re, x1, u1.re, y1);
+            o3 = dcx_rmul2(u2.re, x1, u3.re, y1);
+        } else {  // anti-diagonal
+            o0 = dcx_mul(u1, y0);
+            o1 = dcx_mul(u2, x0);
+            o2 = dcx_mul(u1, y1);
+            o3 = dcx_mul(u2, x1);
+        }
+        a[i] = from_dcx(o0);
+        a[i ^ pmask] = from_dcx(o1);
+        if (two) {
+            a[j] = from_dcx(o2);
+            a[j ^ pmask] = from_dcx(o3);
+        }
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_diag_df(double2 *__restrict__ a, uint64_t W, FixedBits fb, int tbit,
+                                                      DfMat M) {
+    const dcx u0 = df_coef(M, 0), u3 = df_coef(M, 3);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t p = (uint64_t)blockIdx.x * kThreads + threadIdx.x; p < W; p += 2 * stride) {
+        const bool two = p + stride < W;
+        const uint64_t i = expand_n<NP>(p, fb), j = two ? expand_n<NP>(p + stride, fb) : i;
+        const double2 ra = a[i], rc = a[j];
+        const dcx x0 = dcx_mul(((i >> tbit) & 1) ? u3 : u0, to_dcx(ra));
+        const dcx x1 = dcx_mul(((j >> tbit) & 1) ? u3 : u0, to_dcx(rc));
+        a[i] = from_dcx(x0);
+        if (two) a[j] = from_dcx(x1);
+    }
+}
+
+DfMat to_dfmat(const Mat2 &U) {
+    DfMat d;
+    for (int k = 0; k < 8; k++) {
+        d.h[k] = (float)U.u[k];
+        d.l[k] = (float)(U.u[k] - (double)d.h[k]);
+    }
+    return d;
+}
+
+template <int NP>
+cudaError_t pairs_df_np(void *amp, uint64_t W, const FixedBits &fb, uint64_t pmask, int gc, const Mat2 &U,
+                        cudaStream_t s) {
+    const int grid = grid_for(W, 2);
+    double2 *a = static_cast<double2 *>(amp);
+    const DfMat M = to_dfmat(U);
+    switch (gc) {
+    case GC_GENERAL: k_pairs_df<GC_GENERAL, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, M); break;
+    case GC_REAL: k_pairs_df<GC_REAL, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, M); break;
+    case GC_ANTIDIAG: k_pairs_df<GC_ANTIDIAG, NP><<<grid, kThreads, 0, s>>>(a, W, fb, pmask, M); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pairs_df(void *amp, uint64_t W, const FixedBits &fb, uint64_t pmask, int gc, const Mat2 &U,
+                     cudaStream_t s) {
+    if (fb.npos <= 2) return pairs_df_np<2>(amp, W, fb, pmask, gc, U, s);
+    if (fb.npos <= 4) return pairs_df_np<4>(amp, W, fb, pmask, gc, U, s);
+    if (fb.npos <= 8) return pairs_df_np<8>(amp, W, fb, pmask, gc, U, s);
+    return pairs_df_np<kMaxFixed>(amp, W, fb, pmask, gc, U, s);
+}
+
+cudaError_t diag_df(void *amp, uint64_t W, const FixedBits &fb, int tbit, const Mat2 &U, cudaStream_t s) {
+    const int grid = grid_for(W, 2);
+    double2 *a = static_cast<double2 *>(amp);
+    const DfMat M = to_dfmat(U);
+    if (fb.npos <= 2) k_diag_df<2><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, M);
+    else if (fb.npos <= 4) k_diag_df<4><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, M);
+    else if (fb.npos <= 8) k_diag_df<8><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, M);
+    else k_diag_df<kMaxFixed><<<grid, kThreads, 0, s>>>(a, W, fb, tbit, M);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -252,6 +367,7 @@ cudaError_t launch_pairs(void *amp, int dt, int n, const FixedBitsHost &fbh, uin
     if (fbh.npos > n || fbh.npos > kMaxFixed) return cudaErrorInvalidValue;
     const uint64_t W = 1ull << (n - fbh.npos);
     const FixedBits fb = to_dev(fbh);
+    if (dt == 1 && gc != GC_EXCHANGE) return pairs_df(amp, W, fb, pmask, gc, U, s);
     return dt == 0 ? pairs_dispatch<float>(amp, W, fb, pmask, gc, U, s)
                    : pairs_dispatch<double>(amp, W, fb, pmask, gc, U, s);
 }
@@ -261,6 +377,7 @@ cudaError_t launch_diag(void *amp, int dt, int n, const FixedBitsHost &fbh, int 
     if (fbh.npos > n || fbh.npos > kMaxFixed) return cudaErrorInvalidValue;
     const uint64_t W = 1ull << (n - fbh.npos);
     const FixedBits fb = to_dev(fbh);
+    if (dt == 1) return diag_df(amp, W, fb, tbit, U, s);
     return dt == 0 ? diag_dispatch<float>(amp, W, fb, tbit, U, s) : diag_dispatch<double>(amp, W, fb, tbit, U, s);
 }
 

@@ -163,61 +163,108 @@ __device__ __forceinline__ typename AmpT<C128>::V coef(const TileOp &op, int k);
 template <> __device__ __forceinline__ float2 coef<false>(const TileOp &op, int k) { return coef64(op, k); }
 template <> __device__ __forceinline__ dcx coef<true>(const TileOp &op, int k) { return coef128(op, k); }
 
-template <bool C128, int RB>
-__device__ __forceinline__ void apply_op2(const TileOp &op, typename AmpT<C128>::V (&v)[1 << RB], uint32_t thr_idx,
-                                          int lane, uint64_t base) {
-    using V = typename AmpT<C128>::V;
-    if ((base & op.gcmask) != op.gcmask) return;
+template <int RB, int K>
+__device__ __forceinline__ void phase_reg(float2 (&v)[1 << RB], float2 u, bool thr_ok, uint32_t creg) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        if (!((j >> K) & 1)) continue;
+        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        v[j] = vmul(u, v[j]);
+    }
+}
+
+template <int RB, int K>
+__device__ __forceinline__ void diag_reg(float2 (&v)[1 << RB], float2 u0, float2 u1, bool thr_ok, uint32_t creg) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
+        v[j] = vmul(((j >> K) & 1) ? u1 : u0, v[j]);
+    }
+}
+
+// bit flip on register slot K where register slot C is 1: a renaming of
+// registers, no arithmetic
+template <int RB, int K, int C>
+__device__ __forceinline__ void exch1(float2 (&v)[1 << RB]) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); j++) {
+        if (!((j >> C) & 1) || ((j >> K) & 1)) continue;
+        const float2 t = v[j];
+        v[j] = v[j | (1 << K)];
+        v[j | (1 << K)] = t;
+    }
+}
+
+template <int RB, int K>
+__device__ __forceinline__ void exch1_c(int c, float2 (&v)[1 << RB]) {
+    switch (c) {
+    case 0: if constexpr (K != 0) exch1<RB, K, 0>(v); break;
+    case 1: if constexpr (K != 1) exch1<RB, K, 1>(v); break;
+    case 2: if constexpr (K != 2) exch1<RB, K, 2>(v); break;
+    case 3: if constexpr (K != 3) exch1<RB, K, 3>(v); break;
+    default: if constexpr (RB > 4 && K != 4) exch1<RB, K, (RB > 4 ? 4 : 0)>(v); break;
+    }
+}
+
+// One op of a phase.  op.code = family * 8 + k selects a code path whose
+// register indices are compile-time constants.
+template <int RB>
+__device__ __forceinline__ void apply_rop(const TileOp &op, float2 (&v)[1 << RB], uint32_t thr_idx, int lane,
+                                          uint64_t base) {
+    if ((base & op.gcmask) != op.gcmask) return;  // a control outside the tile is 0 here
     const bool thr_ok = (thr_idx & op.lcthr) == op.lcthr;
     const uint32_t creg = op.creg;
-    const int kind = op.kind;
-    if (kind == TOP_DIAG || kind == TOP_PHASE || kind == TOP_DIAG_G) {
-        const V u0 = coef<C128>(op, 0), u1 = coef<C128>(op, 3);
-        if (kind == TOP_DIAG_G) {
-            const V f = ((base >> op.tl) & 1ull) ? u1 : u0;
+    const float4 c01 = *reinterpret_cast<const float4 *>(op.uh);
+    const float4 c23 = *reinterpret_cast<const float4 *>(op.uh + 4);
+    const float2 u[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w), make_float2(c23.x, c23.y),
+                         make_float2(c23.z, c23.w)};
+    switch (op.code) {
+#define QSIM_K_CASES(FAM, STMT)                         \
+    case FAM * 8 + 0: { constexpr int K = 0; STMT; } break; \
+    case FAM * 8 + 1: { constexpr int K = 1; STMT; } break; \
+    case FAM * 8 + 2: { constexpr int K = 2; STMT; } break; \
+    case FAM * 8 + 3: { constexpr int K = 3; STMT; } break; \
+    case FAM * 8 + 4: if constexpr (RB > 4) { constexpr int K = RB > 4 ? 4 : 0; STMT; } break;
+        QSIM_K_CASES(RC_GEN, (pair_reg<RB, K, PK_GENERAL, false>(v, u, true, 0u)))
+        QSIM_K_CASES(RC_REAL, (pair_reg<RB, K, PK_REAL, false>(v, u, true, 0u)))
+        QSIM_K_CASES(RC_GENC, (pair_reg<RB, K, PK_GENERAL, true>(v, u, thr_ok, creg)))
+        QSIM_K_CASES(RC_REALC, (pair_reg<RB, K, PK_REAL, true>(v, u, thr_ok, creg)))
+        QSIM_K_CASES(RC_ANTI, (pair_reg<RB, K, PK_ANTI, true>(v, u, thr_ok, creg)))
+        QSIM_K_CASES(RC_EXCHC, (pair_reg<RB, K, PK_EXCH, true>(v, u, thr_ok, creg)))
+        QSIM_K_CASES(RC_PHASE, (phase_reg<RB, K>(v, u[3], thr_ok, creg)))
+        QSIM_K_CASES(RC_DIAG, (diag_reg<RB, K>(v, u[0], u[3], thr_ok, creg)))
+        QSIM_K_CASES(RC_EXCH1, (exch1_c<RB, K>(op.cslot, v)))
+#undef QSIM_K_CASES
+    case RC_LANE * 8 + PK_GENERAL: pair_lane<RB, PK_GENERAL, false>(op.tl, v, u, true, 0u, lane); break;
+    case RC_LANE * 8 + PK_REAL: pair_lane<RB, PK_REAL, false>(op.tl, v, u, true, 0u, lane); break;
+    case RC_LANE * 8 + PK_ANTI: pair_lane<RB, PK_ANTI, false>(op.tl, v, u, true, 0u, lane); break;
+    case RC_LANE * 8 + PK_EXCH: pair_lane<RB, PK_EXCH, false>(op.tl, v, u, true, 0u, lane); break;
+    case RC_LANEC * 8 + PK_GENERAL: pair_lane<RB, PK_GENERAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
+    case RC_LANEC * 8 + PK_REAL: pair_lane<RB, PK_REAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
+    case RC_LANEC * 8 + PK_ANTI: pair_lane<RB, PK_ANTI, true>(op.tl, v, u, thr_ok, creg, lane); break;
+    case RC_LANEC * 8 + PK_EXCH: pair_lane<RB, PK_EXCH, true>(op.tl, v, u, thr_ok, creg, lane); break;
+    case RC_THR * 8 + 0:  // phase on a lane or warp bit: the factor is uniform per thread
+        if ((thr_idx >> op.tl) & 1u) {
 #pragma unroll
             for (int j = 0; j < (1 << RB); j++)
-                if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
-            return;
+                if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(u[3], v[j]);
         }
-        const int rk = op.regk;
-        const bool tbit = (thr_idx >> op.tl) & 1u;  // used when the target is a lane or warp bit
+        break;
+    case RC_THR * 8 + 1: {
+        const float2 f = ((thr_idx >> op.tl) & 1u) ? u[3] : u[0];
 #pragma unroll
-        for (int j = 0; j < (1 << RB); j++) {
-            if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
-            const bool bit = rk >= 0 ? ((j >> rk) & 1) : tbit;
-            if (kind == TOP_PHASE) {
-                if (bit) v[j] = vmul(u1, v[j]);
-            } else {
-                v[j] = vmul(bit ? u1 : u0, v[j]);
-            }
-        }
-        return;
+        for (int j = 0; j < (1 << RB); j++)
+            if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
+        break;
     }
-    V u[4];
+    case RC_GLOB * 8 + 0: {
+        const float2 f = ((base >> op.tl) & 1ull) ? u[3] : u[0];
 #pragma unroll
-    for (int k = 0; k < 4; k++) u[k] = coef<C128>(op, k);
-    const int pk = op.pk;  // pair kind chosen by the host
-    // uncontrolled dense gates (the common case) skip the per-register tests
-    const bool ct = (op.lcthr | creg) != 0u;
-    if (op.regk >= 0) {
-        if (!ct && pk == PK_GENERAL) pair_reg_dispatch<RB, PK_GENERAL, false>(op.regk, v, u, true, 0u);
-        else if (!ct && pk == PK_REAL) pair_reg_dispatch<RB, PK_REAL, false>(op.regk, v, u, true, 0u);
-        else switch (pk) {
-        case PK_GENERAL: pair_reg_dispatch<RB, PK_GENERAL, true>(op.regk, v, u, thr_ok, creg); break;
-        case PK_REAL: pair_reg_dispatch<RB, PK_REAL, true>(op.regk, v, u, thr_ok, creg); break;
-        case PK_ANTI: pair_reg_dispatch<RB, PK_ANTI, true>(op.regk, v, u, thr_ok, creg); break;
-        default: pair_reg_dispatch<RB, PK_EXCH, true>(op.regk, v, u, thr_ok, creg); break;
-        }
-    } else {
-        if (!ct && pk == PK_GENERAL) pair_lane<RB, PK_GENERAL, false>(op.tl, v, u, true, 0u, lane);
-        else if (!ct && pk == PK_REAL) pair_lane<RB, PK_REAL, false>(op.tl, v, u, true, 0u, lane);
-        else switch (pk) {
-        case PK_GENERAL: pair_lane<RB, PK_GENERAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
-        case PK_REAL: pair_lane<RB, PK_REAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
-        case PK_ANTI: pair_lane<RB, PK_ANTI, true>(op.tl, v, u, thr_ok, creg, lane); break;
-        default: pair_lane<RB, PK_EXCH, true>(op.tl, v, u, thr_ok, creg, lane); break;
-        }
+        for (int j = 0; j < (1 << RB); j++)
+            if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
+        break;
+    }
+    default: break;
     }
 }
 
@@ -233,9 +280,13 @@ __device__ __forceinline__ uint32_t reg_index(uint32_t thr_idx, const uint32_t (
 }
 
 constexpr int kMaxStagedOps = 96;  // ops of a pass copied to shared memory (18 KiB)
+#ifndef QSIM_T2_MINB
+#define QSIM_T2_MINB 2
+#endif
+constexpr int kMinBlocks2 = QSIM_T2_MINB;  // resident CTAs per SM the register budget is sized for
 
 template <bool C128, int RB>
-__global__ void __launch_bounds__(kThreads2, RB == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads2, kMinBlocks2)
     k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases, int nphases,
             const TileOp *__restrict__ ops_g, int op_base, int op_count, uint32_t *err, uint64_t ntiles) {
     using S = typename AmpT<C128>::S;
@@ -313,8 +364,7 @@ __global__ void __launch_bounds__(kThreads2, RB == 4 ? 3 : 2)
             const int lfmt = (C128 && p == 0) ? 0 : 1, sfmt = (C128 && p == nphases - 1) ? 0 : 1;
 #pragma unroll
             for (int j = 0; j < (1 << RB); j++) v[j] = ld_amp(t, reg_index<RB>(thr_idx, rbit, j), lfmt);
-            for (int o = ph.op_begin; o < ph.op_begin + ph.op_count; o++)
-                apply_op2<C128, RB>(ops[o], v, thr_idx, lane, base);
+            for (int o = ph.op_begin; o < ph.op_begin + ph.op_count; o++) apply_rop<RB>(ops[o], v, thr_idx, lane, base);
             if (ph.nperm) {
                 __syncthreads();  // every thread has read its inputs before any permuted write
 #pragma unroll
@@ -360,7 +410,7 @@ cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int n
     const uint64_t ntiles = 1ull << (g.n - T);
     int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > (RB == 4 ? 3 : 2)) per_sm = RB == 4 ? 3 : 2;
+    if (per_sm > kMinBlocks2) per_sm = kMinBlocks2;
     uint64_t grid = (uint64_t)sm_count * per_sm;
     if (grid > ntiles) grid = ntiles;
     cudaError_t e = cudaFuncSetAttribute(k_tile2<C128, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -57,7 +57,8 @@ struct TileOp {
     // register-blocked kernel (k_tile2.cu), filled by the planner per phase
     int8_t regk;      // register slot of the target bit; -1 if it is a lane/warp bit (or outside the tile)
     int8_t pk;        // pair kind: 0 general, 1 real, 2 anti-diagonal, 3 exchange
-    int8_t pad8[2];
+    uint8_t code;     // register kernel dispatch: family * 8 + slot (RC_* below)
+    int8_t cslot;     // RC_EXCH1: the register slot of the single control
     uint32_t creg;    // controls among the register slots (bit k = slot k)
     uint32_t lcthr;   // controls among the lane and warp bits (local index mask)
     uint32_t pad32;
@@ -65,6 +66,25 @@ struct TileOp {
     float ul[8];      // ... and the remainders (complex128 double-float coefficients)
 };
 static_assert(sizeof(TileOp) == 192, "TileOp layout");
+
+// Op families of the register kernel (TileOp::code = family * 8 + k, k = the
+// target's register slot unless noted).  The host picks the family so the
+// kernel applies each op with compile-time register indices.
+enum RegFamily : int {
+    RC_GEN = 0,     // dense 2x2, no local controls
+    RC_REAL = 1,    // real 2x2, no local controls
+    RC_GENC = 2,    // dense 2x2 with controls
+    RC_REALC = 3,   // real 2x2 with controls
+    RC_ANTI = 4,    // anti-diagonal, any controls
+    RC_EXCHC = 5,   // bit flip with controls
+    RC_PHASE = 6,   // diag(1, u11) on a register bit, any controls
+    RC_DIAG = 7,    // diag(u00, u11) on a register bit, any controls
+    RC_EXCH1 = 8,   // bit flip controlled by exactly one register bit (cslot): a register renaming
+    RC_LANE = 9,    // pair op on a lane bit (tl), no local controls; k = pair kind
+    RC_LANEC = 10,  // pair op on a lane bit with controls; k = pair kind
+    RC_THR = 11,    // phase (k = 0) or diagonal (k = 1) on a lane/warp bit (tl)
+    RC_GLOB = 12    // diagonal on a bit outside the tile (tl = physical bit)
+};
 
 // One phase of a register-blocked tile program: which local bits are held in
 // registers, the ops it applies, and an optional permutation of local bit

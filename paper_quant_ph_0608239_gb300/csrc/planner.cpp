@@ -348,6 +348,34 @@ void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vecto
             for (int k = 0; k < nr; k++)
                 if ((op.lcmask >> ph.rb[k]) & 1u) op.creg |= 1u << k;
             op.lcthr = op.lcmask & ~rset;
+            op.cslot = -1;
+            const bool noctl = op.lcmask == 0;
+            int fam, k = op.regk;
+            if (op.kind == TOP_DIAG_G) {
+                fam = RC_GLOB;
+                k = 0;
+            } else if (op.kind == TOP_PHASE || op.kind == TOP_DIAG) {
+                if (op.regk >= 0) fam = op.kind == TOP_PHASE ? RC_PHASE : RC_DIAG;
+                else {
+                    fam = RC_THR;
+                    k = op.kind == TOP_PHASE ? 0 : 1;
+                }
+            } else if (op.regk < 0) {  // pair op on a lane bit
+                fam = noctl ? RC_LANE : RC_LANEC;
+                k = op.pk;
+            } else if (op.pk == 0) {
+                fam = noctl ? RC_GEN : RC_GENC;
+            } else if (op.pk == 1) {
+                fam = noctl ? RC_REAL : RC_REALC;
+            } else if (op.pk == 2) {
+                fam = RC_ANTI;
+            } else if (op.lcthr == 0 && __builtin_popcount(op.creg) == 1) {
+                fam = RC_EXCH1;
+                op.cslot = (int8_t)__builtin_ctz(op.creg);
+            } else {
+                fam = RC_EXCHC;
+            }
+            op.code = (uint8_t)(fam * 8 + k);
             ops_out.push_back(op);
         }
         phases_out.push_back(ph);

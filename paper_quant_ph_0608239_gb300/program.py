@@ -19,8 +19,10 @@ App. A prints only ``H q``; the other gate keywords are this library's:
 
     H q  X q  Y q  XB q  YB q       single-qubit gates of Sec. II.B
     R q k                           phase shift R(2 pi / 2^k) (Eq. singlephase)
+    RB q k                          its inverse R(-2 pi / 2^k) (the bar of Sec. II.B)
     CNOT t c                        target t, control c (Eq. CNOT2)
     CR t c k                        controlled phase shift R_tc(2 pi / 2^k) (Eq. COMM5)
+    CRB t c k                       its inverse
     CV t c k                        controlled V(2 pi / 2^k) (Eq. COMM4)
     TOFFOLI t c1 c2                 (Eq. Toffoli)
     SWAPGATE a b                    the quantum SWAP gate
@@ -128,15 +130,17 @@ def _gate(key, args, lineno, L):
     if key in single:
         (t,) = _ints(args, lineno, 1)
         return Gate(single[key], (qb(t),), (), ())
-    if key == "R":
+    if key in ("R", "RB"):
         t, k = _ints(args, lineno, 2)
-        return Gate("R", (qb(t),), (), (2 * math.pi / (1 << k),))
+        sign = 1.0 if key == "R" else -1.0
+        return Gate("R", (qb(t),), (), (sign * 2 * math.pi / (1 << k),))
     if key == "CNOT":
         t, c = _ints(args, lineno, 2)
         return Gate("NOT", (qb(t),), (qb(c),), ())
-    if key in ("CR", "CV"):
+    if key in ("CR", "CV", "CRB"):
         t, c, k = _ints(args, lineno, 3)
-        return Gate("R" if key == "CR" else "V", (qb(t),), (qb(c),), (2 * math.pi / (1 << k),))
+        sign = -1.0 if key == "CRB" else 1.0
+        return Gate("V" if key == "CV" else "R", (qb(t),), (qb(c),), (sign * 2 * math.pi / (1 << k),))
     if key == "TOFFOLI":
         t, c1, c2 = _ints(args, lineno, 3)
         return Gate("NOT", (qb(t),), (qb(c1), qb(c2)), ())

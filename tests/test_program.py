@@ -46,7 +46,8 @@ def test_parse_structure():
 
 
 def test_parse_gate_keywords():
-    text = "QUBITS 4\nINITIAL STATE 5\nR 1 3\nCNOT 2 0\nCR 3 1 4\nCV 0 2 2\nTOFFOLI 3 0 1\nSWAPGATE 0 3\nXB 2\n"
+    text = ("QUBITS 4\nINITIAL STATE 5\nR 1 3\nCNOT 2 0\nCR 3 1 4\nCV 0 2 2\nTOFFOLI 3 0 1\nSWAPGATE 0 3\nXB 2\n"
+            "RB 0 2\nCRB 1 3 5\n")
     L, x0, steps = program.parse(text)
     g = steps[0].args
     assert (L, x0) == (4, 5)
@@ -57,6 +58,8 @@ def test_parse_gate_keywords():
     assert g[4] == Gate("NOT", (3,), (0, 1), ())
     assert g[5] == Gate("SWAP", (0, 3), (), ())
     assert g[6] == Gate("XB", (2,), (), ())
+    assert g[7] == Gate("R", (0,), (), (-2 * math.pi / 4,))
+    assert g[8] == Gate("R", (1,), (3,), (-2 * math.pi / 32,))
 
 
 @pytest.mark.parametrize("bad", [
@@ -80,9 +83,14 @@ def _render(gates):
         if g.kind in ("H", "X", "Y", "XB", "YB") and not g.controls:
             out.append("%s %d" % (g.kind, g.targets[0]))
         elif g.kind == "R":
-            k = round(math.log2(2 * math.pi / g.params[0])) if g.params[0] > 0 else None
-            assert k is not None and abs(2 * math.pi / (1 << k) - g.params[0]) < 1e-15
-            out.append("CR %d %d %d" % (g.targets[0], g.controls[0], k) if g.controls else "R %d %d" % (g.targets[0], k))
+            phi = g.params[0]
+            k = round(math.log2(2 * math.pi / abs(phi)))
+            assert abs(2 * math.pi / (1 << k) - abs(phi)) < 1e-15
+            bar = "" if phi > 0 else "B"
+            if g.controls:
+                out.append("CR%s %d %d %d" % (bar, g.targets[0], g.controls[0], k))
+            else:
+                out.append("R%s %d %d" % (bar, g.targets[0], k))
         else:
             raise ValueError(g)
     return "\n".join(out)
