@@ -66,6 +66,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # instructions for 14 flops per amplitude; real 2x2, phase, diagonal: 6.3)
 DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 6.2 / 1e12
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+# TF32 dense tensor rate = bf16 rate x (1.1 / 2.25), the nominal ratio
+TF32_OVER_BF16 = 1.1 / 2.25
 
 
 def workload_gates(w):
@@ -90,6 +93,17 @@ def peaks():
             d = json.load(f)
         return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def tf32_peak():
+    """TF32 tensor peak: the measured bf16 burst GEMM rate x the nominal ratio."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]) * TF32_OVER_BF16, "measured bf16 burst x 1.1/2.25"
+    return FALLBACK_BF16_TFLOPS * TF32_OVER_BF16, "fallback bf16 x 1.1/2.25"
 
 
 def ncu_traffic(kernel, workload):
@@ -210,7 +224,7 @@ def run_ours(args, w, ws, rank, local):
     gates, x0 = workload_gates(w)
     n, ng = w["n"], len(gates)
     st = q.State(n, w["dtype"])
-    plan = st.plan(gates)
+    plan = st.plan(gates, fuse_k=args.fuse_k)
     pst = plan.stats()
     stream = torch.cuda.current_stream()
 
@@ -249,7 +263,7 @@ def run_ours(args, w, ws, rank, local):
     arr = q.gate_array(gates)
     for _ in range(1):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr)
+        st.run(None, gate_arr=arr, fuse_k=args.fuse_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     c2 = st.counters()
@@ -257,7 +271,7 @@ def run_ours(args, w, ws, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr)
+        st.run(None, gate_arr=arr, fuse_k=args.fuse_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
@@ -281,6 +295,15 @@ def run_ours(args, w, ws, rank, local):
                                 "instructions per emulated FP64 flop" if w["dtype"] == "c128"
                                 else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
                 "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
+    if fam == "fused_tensor_core":
+        # 3xTF32: three TF32 products per algorithmic product; the achieved
+        # figure counts algorithmic flops once
+        tp, tsrc = tf32_peak()
+        alu_roof = {"bound": "tensor", "kernel": fam, "achieved": tflops, "peak": tp, "unit": "TFLOP/s",
+                    "frac": tflops / tp, "traffic": traffic,
+                    "peak_source": "TF32 dense: " + tsrc + "; 3 TF32 products per algorithmic product",
+                    "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
+        frac_alu = tflops / tp
     roof, other = (alu_roof, hbm_roof) if frac_alu > frac_hbm else (hbm_roof, alu_roof)
 
     # effective bandwidth of the whole step (algorithmic bytes / step time)
@@ -294,7 +317,8 @@ def run_ours(args, w, ws, rank, local):
         "dtype": "f64" if w["dtype"] == "c128" else "f32",
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
-                   "path": "planner (tile passes)", "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
+                   "path": ("planner (fused %d-qubit blocks)" % args.fuse_k if args.fuse_k
+                            else "planner (tile passes)"), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
                    "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
                    "parallelism": "replicas x%d" % ws},
         "eff_hbm_gbs": eff_gbs, "eff_hbm_frac": eff_gbs / hbm_peak,
@@ -532,6 +556,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-companions", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the qubit count (smaller cases for profiling)")
+    ap.add_argument("--fuse-k", type=int, default=0,
+                    help="fuse the circuit into dense k-qubit blocks (k = 4, 5 run on the tensor cores for complex64)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -541,6 +567,8 @@ def main():
         w["n"] = args.n
         w["text"] = w["text"].replace("%d qubits" % WORKLOADS[args.workload]["n"], "%d qubits" % args.n)
         args.workload = args.workload + "_n%d" % args.n
+    if args.fuse_k:
+        args.workload = args.workload + "_fused%d" % args.fuse_k
     if args.impl == "reference":
         out = run_reference(args, w, ws, rank)
     elif w["kind"] == "batch":

@@ -60,12 +60,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __shared__ __align__(8) uint64_t bar_ld, bar_mma, bar_b;
     __shared__ uint32_t tmem_slot;
     __shared__ uint64_t runoff[1 << kMaxHTC];
-    __shared__ int abort_flag;
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
     const uint32_t run_bytes = 8u << L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    __shared__ int s_hb[kMaxHTC];  // the high tile bits, indexed at run time
+    if (threadIdx.x < kMaxHTC) s_hb[threadIdx.x] = threadIdx.x < (unsigned)H ? g.hb[threadIdx.x] : 0;
     for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
         uint64_t o = 0;
         for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
@@ -76,7 +77,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(&bar_mma, 1);
         mbar_init(&bar_b, 1);
         fence_mbar_init();
-        abort_flag = 0;
     }
     if (warp == 0) {
         tmem_alloc(&tmem_slot, N < 32 ? 32 : N);
@@ -93,17 +93,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         bulk_g2s(s_bhi, bmat, BB, &bar_b);
         bulk_g2s(s_blo, bmat + BB / 4, BB, &bar_b);
     }
-    if (!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) {
-        atomicExch(err, kErrTimeout);
-        abort_flag = 1;
-    }
-    __syncthreads();
+    // every abort decision goes through a block-wide vote, so all threads
+    // leave the loop at the same barrier
+    bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) != 0;
 
     const uint32_t idesc = umma_idesc_tf32(128, N);
     uint32_t ld_parity = 0, mma_parity = 0;
-    for (uint64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+    for (uint64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
         uint64_t base = tile << L;
-        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
         float2 *tin = reinterpret_cast<float2 *>(s_tile);
         if (threadIdx.x < 32) {
             if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar_ld, TS * 8u);
@@ -111,12 +109,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (uint32_t j = threadIdx.x; j < nruns; j += 32)
                 bulk_g2s(tin + ((size_t)j << L), a + (base | runoff[j]), run_bytes, &bar_ld);
         }
-        if (!mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC)) {
-            atomicExch(err, kErrTimeout);
-            abort_flag = 1;
+        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC)) != 0;
+        if (aborted) {
+            mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC);  // let the copies in flight land
+            break;
         }
-        __syncthreads();
-        if (abort_flag) break;
         ld_parity ^= 1u;
 
         // split into TF32 head / FP32 tail, scatter into the canonical layouts
@@ -155,14 +152,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
             umma_commit(&bar_mma);
         }
-        if (!mbar_wait_bounded(&bar_mma, mma_parity, kWaitBudgetTC)) {
-            atomicExch(err, kErrTimeout);
-            abort_flag = 1;
-        }
+        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_mma, mma_parity, kWaitBudgetTC)) != 0;
         mma_parity ^= 1u;
         tc_fence_after();
-        __syncthreads();
-        if (abort_flag) break;
+        if (aborted) break;
 
         // epilogue: warp w reads lanes 32 (w % 4) .. +31 (groups), column chunk w / 4
         float2 *tout = reinterpret_cast<float2 *>(s_ahi);
@@ -195,6 +188,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         __syncthreads();
     }
+    if (aborted && threadIdx.x == 0) atomicExch(err, kErrTimeout);
     if (threadIdx.x < 32) bulk_wait_all();
     tc_fence_before();
     __syncthreads();

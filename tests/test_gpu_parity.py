@@ -164,6 +164,48 @@ def test_random_circuit_both_paths(q, dt, n, depth, tile):
         assert e < TOL[dt], (m, e)
 
 
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_registers(q, dt, n):
+    # tiles of fewer than three bits: no octet groups, whole-tile conversion
+    rng = np.random.default_rng(40 + n)
+    gates = inputs.random_circuit(n, 8, seed=40 + n)
+    if n >= 2:
+        gates += [g for g in controlled_gates(rng, n, 12) if len(g.controls) + len(g.targets) <= n]
+    psi = rand_state(n, 41 + n)
+    ref = oracle.run(n, gates, state=psi.copy())
+    for m in (q.MODE_PERGATE, q.MODE_FUSED):
+        assert err(run_gpu(q, n, dt, gates, psi=psi, mode=m), ref) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_long_pass_many_ops(q, dt):
+    # one tile holds the whole 10-qubit register, so all 300 gates land in one
+    # pass: several staging chunks of ops, groups with renamings, SWAP gates
+    n = 10
+    rng = np.random.default_rng(77)
+    kinds = ["H", "R", "SU2", "NOT", "V", "X", "YB"]
+    gates = []
+    for i in range(300):
+        k = kinds[int(rng.integers(len(kinds)))]
+        qs = [int(x) for x in rng.permutation(n)]
+        nc = int(rng.integers(0, 3))
+        if i % 37 == 0:
+            gates.append(Gate("SWAP", (qs[0], qs[1]), (), ()))
+            continue
+        gates.append(g1(k, qs[0], qs[1:1 + nc], PARAMS.get(k, ())))
+    psi = rand_state(n, 78)
+    ref = oracle.run(n, gates, state=psi.copy())
+    st = q.State(n, dt)
+    st.set_state(psi)
+    plan = st.plan(gates)
+    assert plan.stats()["passes"] == 1
+    plan.run()
+    assert err(st.get_state(), ref) < TOL[dt] * 4
+    plan.free()
+    st.free()
+
+
 def test_qft_config_c128_and_closed_form(q):
     n = 10
     x, gates = inputs.qft_circuit(n, seed=1)
@@ -310,7 +352,7 @@ def test_apply_fused_dense(q, dt, k):
 
 # ---------------------------------------- fused gates on the tensor cores
 @pytest.mark.parametrize("k", [4, 5])
-@pytest.mark.parametrize("n,where", [(12, "low"), (16, "high"), (16, "mixed"), (20, "mixed")])
+@pytest.mark.parametrize("n,where", [(12, "low"), (16, "high"), (16, "mixed"), (20, "mixed"), (22, "high")])
 def test_fused_tensor_cores_c64(q, k, n, where):
     rng = np.random.default_rng(70 + 10 * k + n)
     if where == "low":
