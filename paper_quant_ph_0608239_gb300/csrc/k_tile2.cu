@@ -279,15 +279,16 @@ __device__ __forceinline__ uint32_t reg_index(uint32_t thr_idx, const uint32_t (
     return x;
 }
 
-constexpr int kMaxStagedOps = 96;  // ops of a pass copied to shared memory (18 KiB)
+constexpr int kMaxStagedOps = 96;     // ops of a pass copied to shared memory (18 KiB)
+constexpr int kMaxStagedPhases = 48;  // phases of a pass copied to shared memory (2.25 KiB)
 #ifndef QSIM_T2_MINB
-#define QSIM_T2_MINB 2
+#define QSIM_T2_MINB 3
 #endif
 constexpr int kMinBlocks2 = QSIM_T2_MINB;  // resident CTAs per SM the register budget is sized for
 
 template <bool C128, int RB>
 __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
-    k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases, int nphases,
+    k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases_g, int nphases,
             const TileOp *__restrict__ ops_g, int op_base, int op_count, uint32_t *err, uint64_t ntiles) {
     using S = typename AmpT<C128>::S;
     using V = typename AmpT<C128>::V;
@@ -315,6 +316,18 @@ __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
         for (uint32_t w = threadIdx.x; w < (uint32_t)op_count * (sizeof(TileOp) / 4); w += blockDim.x) dst[w] = src[w];
     }
     const TileOp *ops = staged ? ops_s - op_base : ops_g;
+    // likewise the phases, after the staged ops
+    TilePhase *phases_s =
+        reinterpret_cast<TilePhase *>(smem_raw + (sizeof(S) << T) + (staged ? (size_t)op_count * sizeof(TileOp) : 0));
+    const bool pstaged = nphases <= kMaxStagedPhases;
+    if (pstaged) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(phases_g);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(phases_s);
+        for (uint32_t w = threadIdx.x; w < (uint32_t)nphases * (sizeof(TilePhase) / 4); w += blockDim.x) dst[w] = src[w];
+    }
+    const TilePhase *phases = pstaged ? phases_s : phases_g;
+    __shared__ int s_hb[kMaxH2];  // the high tile bits, indexed at run time
+    if (threadIdx.x < kMaxH2) s_hb[threadIdx.x] = threadIdx.x < (unsigned)H ? g.hb[threadIdx.x] : 0;
 
     for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
         uint64_t o = 0;
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         uint64_t base = tile << L;
-        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
         if (threadIdx.x < 32) {
             if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, TS * (uint32_t)sizeof(S));
             __syncwarp();
@@ -406,7 +419,8 @@ cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int n
                     int op_base, int op_count, uint32_t *err, int sm_count, cudaStream_t s) {
     using S = typename AmpT<C128>::S;
     const int T = g.L + g.H;
-    const size_t smem = (sizeof(S) << T) + (op_count <= kMaxStagedOps ? (size_t)op_count * sizeof(TileOp) : 0);
+    const size_t smem = (sizeof(S) << T) + (op_count <= kMaxStagedOps ? (size_t)op_count * sizeof(TileOp) : 0) +
+                        (nphases <= kMaxStagedPhases ? (size_t)nphases * sizeof(TilePhase) : 0);
     const uint64_t ntiles = 1ull << (g.n - T);
     int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
     if (per_sm < 1) per_sm = 1;

@@ -39,11 +39,42 @@ __device__ __forceinline__ dcx ldx(const float4 *t, uint32_t i) {
 __device__ __forceinline__ void stx(float4 *t, uint32_t i, const dcx &v) {
     t[i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
 }
-__device__ __forceinline__ dcx coefx(const TileOp &op, int k) {
-    return dcx{df{op.uh[2 * k], op.ul[2 * k]}, df{op.uh[2 * k + 1], op.ul[2 * k + 1]}};
+// An op as staged in shared memory: every thread reads every op of the pass
+// for every tile, so the pass's ops are copied once (or once per chunk) per
+// block instead of being fetched from global memory each time.
+struct __align__(16) DfOp {
+    float4 c[4];      // u00, u01, u10, u11 as (re.h, re.l, im.h, im.l)
+    uint64_t gcmask;
+    uint32_t lcmask;
+    uint8_t kind, tl, pk, tl2;
+};
+static_assert(sizeof(DfOp) == 80, "DfOp layout");
+constexpr int kStageDF = 40;  // ops per staged chunk (3.1 KiB)
+
+__device__ __forceinline__ void stage_df(DfOp *dst, const TileOp *src, int cn) {
+    for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+        const TileOp &op = src[k];
+        DfOp d;
+#pragma unroll
+        for (int j = 0; j < 4; j++) d.c[j] = make_float4(op.uh[2 * j], op.ul[2 * j], op.uh[2 * j + 1], op.ul[2 * j + 1]);
+        d.gcmask = op.gcmask;
+        d.lcmask = op.lcmask;
+        d.kind = (uint8_t)op.kind;
+        d.tl = (uint8_t)op.tl;
+        d.pk = (uint8_t)op.pk;
+        d.tl2 = (uint8_t)op.tl2;
+        dst[k] = d;
+    }
 }
 
-__device__ void apply_df(float4 *t, int T, const TileOp &op, uint64_t base) {
+__device__ __forceinline__ dcx coefx(const DfOp &op, int k) {
+    const float4 c = op.c[k];
+    return dcx{df{c.x, c.y}, df{c.z, c.w}};
+}
+
+// op: the staged copy; gop: the op in global memory (read only for the
+// permutation's bit list)
+__device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, uint64_t base) {
     if ((base & op.gcmask) != op.gcmask) return;
     const uint32_t lc = op.lcmask;
     const uint32_t TS = 1u << T;
@@ -126,12 +157,13 @@ __device__ void apply_df(float4 *t, int T, const TileOp &op, uint64_t base) {
             t[j] = x;
         }
     } else if (kind == TOP_PERM) {
+        const int nperm = gop.nperm;
         for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
             uint32_t j = i;
-            for (int k = 0; k < op.nperm; k++) {
-                const uint32_t bl = (i >> op.pl[k]) & 1u, bh = (i >> op.ph[k]) & 1u;
-                j &= ~((1u << op.pl[k]) | (1u << op.ph[k]));
-                j |= (bl << op.ph[k]) | (bh << op.pl[k]);
+            for (int k = 0; k < nperm; k++) {
+                const uint32_t bl = (i >> gop.pl[k]) & 1u, bh = (i >> gop.ph[k]) & 1u;
+                j &= ~((1u << gop.pl[k]) | (1u << gop.ph[k]));
+                j |= (bl << gop.ph[k]) | (bh << gop.pl[k]);
             }
             if (j > i) {
                 const float4 x = t[i];
@@ -149,9 +181,11 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
     double2 *t = reinterpret_cast<double2 *>(smem_raw);
     float4 *tf = reinterpret_cast<float4 *>(smem_raw);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint64_t runoff[1 << kMaxHDF];
+    __shared__ DfOp s_ops[kStageDF];
     __shared__ int abort_flag;
     const int L = g.L, H = g.H, T = L + H;
+    uint64_t *runoff = reinterpret_cast<uint64_t *>(smem_raw + ((size_t)16 << T));  // 2^H entries
+    const bool one_stage = nops <= kStageDF;
     const uint32_t TS = 1u << T;
     const uint32_t nruns = 1u << H;
     const int sub_L = L + 4 > kMaxCopyShiftDF ? kMaxCopyShiftDF - 4 : L;
@@ -164,6 +198,9 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
         for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
         runoff[j] = o;
     }
+    __shared__ int s_hb[kMaxHDF];  // the high tile bits, indexed at run time
+    if (threadIdx.x < kMaxHDF) s_hb[threadIdx.x] = threadIdx.x < (unsigned)H ? g.hb[threadIdx.x] : 0;
+    if (one_stage) stage_df(s_ops, ops, nops);
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -174,7 +211,7 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         uint64_t base = tile << L;
-        for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
+        for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
         if (threadIdx.x < 32) {
             if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, TS * 16u);
             __syncwarp();
@@ -202,9 +239,16 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
             }
             __syncthreads();
         }
-        for (int o = 0; o < nops; o++) {
-            apply_df(tf, T, ops[o], base);
-            __syncthreads();
+        for (int c0 = 0; c0 < nops; c0 += kStageDF) {
+            const int cn = nops - c0 < kStageDF ? nops - c0 : kStageDF;
+            if (!one_stage) {
+                stage_df(s_ops, ops + c0, cn);  // the previous op ended with a barrier
+                __syncthreads();
+            }
+            for (int o = 0; o < cn; o++) {
+                apply_df(tf, T, s_ops[o], ops[c0 + o], base);
+                __syncthreads();
+            }
         }
         if (convert) {
             for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
@@ -235,15 +279,16 @@ cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops,
                                 uint32_t *err, int sm_count, cudaStream_t s) {
     const int T = g.L + g.H;
     if (g.H < 0 || g.H > kMaxHDF || T > g.n || T > 13 || g.L < 1) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)16 << T;
+    const size_t smem = ((size_t)16 << T) + ((size_t)8 << g.H);  // tile + run offsets
     const uint64_t ntiles = 1ull << (g.n - T);
-    int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
-    uint64_t grid = (uint64_t)sm_count * per_sm;
-    if (grid > ntiles) grid = ntiles;
     cudaError_t e = cudaFuncSetAttribute(k_tile_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_df, kThreadsDF, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    if (grid > ntiles) grid = ntiles;
     k_tile_df<<<(unsigned)grid, kThreadsDF, smem, s>>>(static_cast<double2 *>(amp), g, ops, nops, convert ? 1 : 0,
                                                       err, ntiles);
     return cudaGetLastError();

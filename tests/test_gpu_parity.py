@@ -167,7 +167,7 @@ def test_random_circuit_both_paths(q, dt, n, depth, tile):
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_tiny_registers(q, dt, n):
-    # tiles of fewer than three bits: no octet groups, whole-tile conversion
+    # registers of one to three qubits: the tile is the whole register
     rng = np.random.default_rng(40 + n)
     gates = inputs.random_circuit(n, 8, seed=40 + n)
     if n >= 2:
