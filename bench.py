@@ -46,6 +46,13 @@ WORKLOADS = {
                          text="seeded random circuit, 34 qubits, depth 20 (1020 gates), complex64 (128 GiB)"),
     "adder30_c64": dict(kind="adder", n=30, m=15, seed=3, dtype="c64",
                         text="QFT register adder of two 15-qubit registers (30 qubits), complex64"),
+    # the paper's own adder runs (App. B): same registers, same N_O
+    "adder3x11_c128": dict(kind="adder", n=33, m=11, values=(292, 585, 1170), dtype="c128",
+                           text="the paper's 3-11QBA adder 292+585+1170 (33 qubits, N_O = 286), complex128 (128 GiB)"),
+    "adder2x17_c64": dict(kind="adder", n=34, m=17, values=(26214, 104857), dtype="c64",
+                          text="the paper's 2-17QBA adder 26214+104857 (34 qubits, N_O = 493), complex64 (128 GiB)"),
+    "adder2x17_c128": dict(kind="adder", n=34, m=17, values=(26214, 104857), dtype="c128",
+                           text="the paper's 2-17QBA adder 26214+104857 (34 qubits, N_O = 493), complex128 (256 GiB)"),
     "qft10_c128": dict(kind="qft", n=10, seed=1, dtype="c128",
                        text="10-qubit QFT with reversal swaps on a seeded basis state, complex128"),
     "hadamard30_c128": dict(kind="hadamard", n=30, dtype="c128",
@@ -75,6 +82,8 @@ def workload_gates(w):
     if w["kind"] == "random":
         return inputs.random_circuit(w["n"], w["depth"], w["seed"]), inputs.random_basis(w["n"], w["seed"])
     if w["kind"] == "adder":
+        if "values" in w:
+            return inputs.adder_circuit(list(w["values"]), w["m"]), 0
         rng = np.random.default_rng(w["seed"])
         a, b = (int(v) for v in rng.integers(0, 1 << w["m"], 2))
         return inputs.adder_circuit([a, b], w["m"]), 0
@@ -195,11 +204,27 @@ def barrier(ws):
 
 
 # ------------------------------------------------------------- CPU oracle
+ORACLE_MAX_N = 30  # the oracle's state lives in host memory: 16 GiB at 30 qubits
+
+
 def oracle_sample(w, gates, x0, budget_s=15.0):
     """The oracle, as it stands, on the first gates of the workload until
-    about budget_s seconds of work; returns (gates/s, gates done, threads)."""
+    about budget_s seconds of work; returns (gates/s, gates done, threads,
+    note).  Above ORACLE_MAX_N qubits the state does not fit in host memory:
+    the oracle then runs the workload's gates that act on qubits below
+    ORACLE_MAX_N at ORACLE_MAX_N qubits, and the per-gate time is scaled by
+    2^(n - ORACLE_MAX_N) (an extrapolation, stated in the note)."""
     import oracle
     n = w["n"]
+    note = ""
+    if n > ORACLE_MAX_N:
+        ns = ORACLE_MAX_N
+        gates = [g for g in gates if max(tuple(g.targets) + tuple(g.controls)) < ns]
+        x0 &= (1 << ns) - 1
+        note = " (at %d qubits, per-gate time scaled by 2^%d: extrapolated)" % (ns, n - ns)
+        n, scale = ns, float(1 << (w["n"] - ns))
+    else:
+        scale = 1.0
     a = oracle.basis(n, x0)
     done, t0 = 0, time.perf_counter()
     for g in gates:
@@ -209,7 +234,22 @@ def oracle_sample(w, gates, x0, budget_s=15.0):
             break
     el = time.perf_counter() - t0
     del a
-    return done / el, done, oracle.num_threads()
+    return done / el / scale, done, oracle.num_threads(), note
+
+
+def oracle_batch_sample(circs, x0s, budget_s=15.0):
+    """The oracle on the batch's circuits in order, each run in full, until
+    about budget_s seconds; returns (gates/s, circuits done, gates done, threads)."""
+    import oracle
+    done = gates = 0
+    t0 = time.perf_counter()
+    for (n, g), x0 in zip(circs, x0s):
+        oracle.run(n, g, x0=x0)
+        done += 1
+        gates += len(g)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return gates / (time.perf_counter() - t0), done, gates, oracle.num_threads()
 
 
 # ----------------------------------------------------------------- ours
@@ -224,8 +264,12 @@ def run_ours(args, w, ws, rank, local):
     gates, x0 = workload_gates(w)
     n, ng = w["n"], len(gates)
     st = q.State(n, w["dtype"])
-    plan = st.plan(gates, fuse_k=args.fuse_k)
-    pst = plan.stats()
+    # the plan picks its tile size / fusion width by timing its candidates
+    # (QSIM_MODE_AUTO); --fuse-k pins a fusion width instead
+    if args.fuse_k or args.tile_bits:
+        plan = st.plan(gates, fuse_k=args.fuse_k, tile_bits=args.tile_bits)
+    else:
+        plan = st.plan(gates, mode=q.MODE_AUTO)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -233,8 +277,11 @@ def run_ours(args, w, ws, rank, local):
         plan.run()
         return st.qubit_probs()
 
+    for _ in range(plan.stats()["candidates"]):  # tuning runs (untimed)
+        step()
     for _ in range(args.warmup):
         step()
+    pst = plan.stats()
     torch.cuda.synchronize()
     c0 = st.counters()
     st.profile(True)
@@ -261,9 +308,11 @@ def run_ours(args, w, ws, rank, local):
     # e2e: the gate list in host memory through qsim_run_circuit each step,
     # the expectations read back to host memory.
     arr = q.gate_array(gates)
+    e2e_T = 0 if pst["fuse_k"] else pst["tile_bits"]
+    e2e_k = pst["fuse_k"]
     for _ in range(1):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr, fuse_k=args.fuse_k)
+        st.run(None, gate_arr=arr, tile_bits=e2e_T, fuse_k=e2e_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     c2 = st.counters()
@@ -271,7 +320,7 @@ def run_ours(args, w, ws, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr, fuse_k=args.fuse_k)
+        st.run(None, gate_arr=arr, tile_bits=e2e_T, fuse_k=e2e_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
@@ -317,8 +366,9 @@ def run_ours(args, w, ws, rank, local):
         "dtype": "f64" if w["dtype"] == "c128" else "f32",
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
-                   "path": ("planner (fused %d-qubit blocks)" % args.fuse_k if args.fuse_k
+                   "path": ("planner (fused %d-qubit blocks on the tensor cores)" % pst["fuse_k"] if pst["fuse_k"]
                             else "planner (tile passes)"), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
+                   "autotune": [dict(c, chosen=(i == pst["chosen"])) for i, c in enumerate(pst["autotune"])],
                    "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
                    "parallelism": "replicas x%d" % ws},
         "eff_hbm_gbs": eff_gbs, "eff_hbm_frac": eff_gbs / hbm_peak,
@@ -340,10 +390,10 @@ def run_ours(args, w, ws, rank, local):
         out["companions"] = companions(q, w, gates, x0, args)
         out["single_gate_sweeps"] = single_gate_sweeps(q)
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, done, thr = oracle_sample(w, gates, x0, args.cpu_budget)
+        v, done, thr, note = oracle_sample(w, gates, x0, args.cpu_budget)
         out["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle",
-                               "sample": "first %d of %d gates of the workload at full size (%d qubits, complex128 "
-                                         "oracle), timed on %d host threads" % (done, ng, n, thr)}
+                               "sample": "first %d of %d gates of the workload (%d qubits, complex128 "
+                                         "oracle), timed on %d host threads%s" % (done, ng, n, thr, note)}
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -493,6 +543,18 @@ def run_batch_workload(args, w, ws, rank, local):
         q.run_batch(states, x0s, arrs)
     e2e = ng * args.steps / (time.perf_counter() - t0)
     h2d = sum(len(g) for _, g in circs) * 112  # qsim_gate records read by the planner
+    hbm_peak, peak_src = peaks()
+    per_run = el / args.steps
+    gbs, tfl = bst["alg_bytes"] / per_run / 1e9, bst["alg_flops"] / per_run / 1e12
+    traffic = ncu_traffic("batch", args.workload)
+    hbm_roof = {"bound": "hbm", "kernel": "batch", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": traffic, "peak_source": peak_src + " copy (MEASURED_PEAKS.json)",
+                "alg_bytes_per_launch": bst["alg_bytes"], "launches": args.steps, "avg_launch_ms": per_run * 1e3}
+    alu_roof = {"bound": "alu", "kernel": "batch", "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz",
+                "alg_flops_per_launch": bst["alg_flops"], "launches": args.steps, "avg_launch_ms": per_run * 1e3}
+    roof, other = (alu_roof, hbm_roof) if alu_roof["frac"] > hbm_roof["frac"] else (hbm_roof, alu_roof)
     out = {
         "metric": METRIC, "value": ng * args.steps / el, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
@@ -504,11 +566,16 @@ def run_batch_workload(args, w, ws, rank, local):
                    "parallelism": "replicas x%d" % ws},
         "one_launch_per_circuit_gates_per_s": per_circuit,
         "e2e": {"value": e2e, "unit": "gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_other": other,
     }
     b.free()
     for st in states:
         st.free()
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, nc, ngs, thr = oracle_batch_sample(circs, x0s, args.cpu_budget)
+        out["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle",
+                               "sample": "the first %d of %d circuits of the batch in full (%d gates, complex128 "
+                                         "oracle), timed on %d host threads" % (nc, len(circs), ngs, thr)}
     return out if rank == 0 else None
 
 
@@ -519,21 +586,37 @@ def run_reference(args, w, ws, rank):
         return None
     if w["kind"] == "batch":  # the oracle on the batch's circuits in order
         circs = inputs.batch_circuits()
-        w = dict(w, n=circs[0][0])
-        gates, x0 = circs[0][1], 0
-    else:
-        gates, x0 = workload_gates(w)
+        x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
+        budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
+        oracle_batch_sample(circs, x0s, budget / 4)
+        vals = []
+        for _ in range(args.steps):
+            v, nc, ngs, thr = oracle_batch_sample(circs, x0s, budget)
+            vals.append(v)
+        v = statistics.median(vals)
+        sample = "the first %d of %d circuits of the batch in full per step (%d gates), %d host threads" % (
+            nc, len(circs), ngs, thr)
+        return {
+            "metric": METRIC, "value": v, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * ngs / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded generator (inputs/circuits.py)",
+            "config": {"workload": w["text"], "name": args.workload, "circuits": len(circs)},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+    gates, x0 = workload_gates(w)
     budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(w, gates, x0, budget / 4)
     vals = []
-    thr, done = 1, 0
+    thr, done, note = 1, 0, ""
     for _ in range(args.steps):
-        v, done, thr = oracle_sample(w, gates, x0, budget)
+        v, done, thr, note = oracle_sample(w, gates, x0, budget)
         vals.append(v)
     v = statistics.median(vals)
-    sample = "first %d of %d gates per step at full size (%d qubits, complex128 oracle), %d host threads" % (
-        done, len(gates), w["n"], thr)
+    sample = "first %d of %d gates per step (%d qubits, complex128 oracle), %d host threads%s" % (
+        done, len(gates), w["n"], thr, note)
     return {
         "metric": METRIC, "value": v, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * done / v, "higher_is_better": True, "scaling": "weak",
@@ -556,6 +639,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-companions", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the qubit count (smaller cases for profiling)")
+    ap.add_argument("--tile-bits", type=int, default=0,
+                    help="pin the tile size T of the tile passes (default: autotuned)")
     ap.add_argument("--fuse-k", type=int, default=0,
                     help="fuse the circuit into dense k-qubit blocks (k = 4, 5 run on the tensor cores for complex64)")
     args = ap.parse_args()
@@ -569,6 +654,8 @@ def main():
         args.workload = args.workload + "_n%d" % args.n
     if args.fuse_k:
         args.workload = args.workload + "_fused%d" % args.fuse_k
+    if args.tile_bits:
+        args.workload = args.workload + "_T%d" % args.tile_bits
     if args.impl == "reference":
         out = run_reference(args, w, ws, rank)
     elif w["kind"] == "batch":

@@ -90,8 +90,15 @@ typedef struct {
 /* How qsim_run_circuit executes a gate list. */
 enum {
     QSIM_MODE_PERGATE = 0, /* one sweep of the state per gate (Sec. III.A) */
-    QSIM_MODE_FUSED = 1    /* planner: shared-memory tile passes, qubit
+    QSIM_MODE_FUSED = 1,   /* planner: shared-memory tile passes, qubit
                               interchanges and dense fused blocks */
+    QSIM_MODE_AUTO = 2     /* plans: one candidate per tile size (and, for
+                              complex64, tensor-core fusion width 4 and 5);
+                              the plan's first runs time each candidate with
+                              CUDA events on the handle's stream, every later
+                              run uses the fastest.  Every run applies the
+                              whole circuit.  qsim_run_circuit treats AUTO as
+                              FUSED with the default sizes. */
 };
 
 typedef struct {
@@ -134,6 +141,16 @@ QSIM_API qsim_status qsim_info(qsim_handle h, int *n, qsim_dtype *dt, void **dev
  * qsim_set_basis: INITIAL STATE x (App. A): a_x = 1, all others 0; resets the
  * qubit-to-bit map to the identity.  EINVAL if x >= 2^n. */
 QSIM_API qsim_status qsim_set_basis(qsim_handle h, uint64_t x);
+
+/* qsim_set_shor_state: the state of Eq. Shor2 (Sec. V.B) after the
+ * modular exponentiation: with the x-register on qubits 0..X-1 and the
+ * f-register on qubits X..n-1,
+ *     a_{x + 2^X f(x)} = 2^(-X/2),  f(x) = y^x mod G,  x = 0 .. 2^X - 1,
+ * all other amplitudes 0.  The paper gives no gate network for the modular
+ * exponentiation, so the state is written directly (one device kernel).
+ * Resets the qubit-to-bit map to the identity.  EINVAL unless 1 <= X < n,
+ * 2 <= G <= 2^(n - X), G < 2^32 and 1 <= y < G. */
+QSIM_API qsim_status qsim_set_shor_state(qsim_handle h, int X, uint64_t y, uint64_t G);
 
 /* qsim_set_state: copy 2^n amplitudes (logical order, the state's dtype) from
  * host memory; resets the map to the identity.  bytes must equal the state
@@ -208,6 +225,13 @@ typedef struct {
                             14 per amplitude for a dense 2x2 gate, 6 for a diagonal
                             or anti-diagonal one, 0 for a pure exchange, scaled by
                             the fraction of amplitudes the gate's controls select */
+    int32_t mode;        /* mode of the plan the figures above describe */
+    int32_t fuse_k;      /* its dense-block width (0: tile passes) */
+    int32_t candidates;  /* QSIM_MODE_AUTO: number of candidate plans, else 0 */
+    int32_t chosen;      /* QSIM_MODE_AUTO: the candidate in use, -1 while tuning */
+    int32_t cand_tile_bits[8];  /* per candidate: tile size ... */
+    int32_t cand_fuse_k[8];     /* ... fusion width (0: tile passes) ... */
+    double cand_ms[8];          /* ... and its measured run time (0 until timed) */
 } qsim_plan_stats;
 
 QSIM_API qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
@@ -273,6 +297,8 @@ typedef struct {
     int64_t items;       /* (circuit, pass, tile) work items of one run */
     int32_t graph;       /* 1 if runs replay a captured CUDA graph */
     int32_t reserved;
+    double alg_bytes;    /* algorithmic bytes of one run: each pass reads and writes its state once */
+    double alg_flops;    /* algorithmic real flops of one run (same count as the plan statistics) */
 } qsim_batch_stats;
 
 QSIM_API qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out);

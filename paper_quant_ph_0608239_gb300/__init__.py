@@ -18,7 +18,7 @@ import numpy as np
 from . import _capi
 from ._capi import (QsimError, QsimGate, QsimOpts, QsimCircuit, QsimPlanStats, QsimKernelTime,  # noqa: F401
                     QsimCounters, gate_array, gate_record,
-                    MODE_PERGATE, MODE_FUSED, QSIM_C64, QSIM_C128, QSIM_ETIMEOUT, QSIM_EINVAL)
+                    MODE_PERGATE, MODE_FUSED, MODE_AUTO, QSIM_C64, QSIM_C128, QSIM_ETIMEOUT, QSIM_EINVAL)
 
 _DT = {"c64": QSIM_C64, "complex64": QSIM_C64, "c128": QSIM_C128, "complex128": QSIM_C128}
 _NP = {QSIM_C64: np.complex64, QSIM_C128: np.complex128}
@@ -102,6 +102,10 @@ class State:
     # -- state ------------------------------------------------------------
     def set_basis(self, x=0):
         _capi.call("qsim_set_basis", self.handle, ctypes.c_uint64(int(x)))
+
+    def set_shor_state(self, X, y, G):
+        """Eq. Shor2: x-register on qubits 0..X-1, f-register above it."""
+        _capi.call("qsim_set_shor_state", self.handle, int(X), ctypes.c_uint64(int(y)), ctypes.c_uint64(int(G)))
 
     def set_state(self, psi):
         psi = np.ascontiguousarray(psi, dtype=self.np_dtype)
@@ -214,8 +218,12 @@ class Plan:
     def stats(self):
         s = QsimPlanStats()
         _capi.call("qsim_plan_get_stats", self.ptr, ctypes.byref(s))
-        return {"passes": s.passes, "sweeps": s.sweeps, "ops": s.ops, "tile_bits": s.tile_bits, "phases": s.phases,
-                "gates": s.gates, "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
+        out = {"passes": s.passes, "sweeps": s.sweeps, "ops": s.ops, "tile_bits": s.tile_bits, "phases": s.phases,
+               "gates": s.gates, "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops, "mode": s.mode,
+               "fuse_k": s.fuse_k, "candidates": s.candidates, "chosen": s.chosen}
+        out["autotune"] = [{"tile_bits": s.cand_tile_bits[i], "fuse_k": s.cand_fuse_k[i], "ms": s.cand_ms[i]}
+                           for i in range(min(s.candidates, 8))]
+        return out
 
     def free(self):
         if self.ptr is not None and self.ptr.value:
@@ -273,7 +281,7 @@ class Batch:
         s = _capi.QsimBatchStats()
         _capi.call("qsim_batch_get_stats", self.ptr, ctypes.byref(s))
         return {"circuits": s.circuits, "gates": s.gates, "passes": s.passes, "items": s.items,
-                "graph": bool(s.graph)}
+                "graph": bool(s.graph), "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
 
     def free(self):
         if self.ptr is not None and self.ptr.value:

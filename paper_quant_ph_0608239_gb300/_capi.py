@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libqsim.so")
 
 QSIM_OK, QSIM_EINVAL, QSIM_ENOMEM, QSIM_ECUDA, QSIM_ETIMEOUT, QSIM_EUNSUPPORTED = range(6)
 QSIM_C64, QSIM_C128 = 0, 1
-MODE_PERGATE, MODE_FUSED = 0, 1
+MODE_PERGATE, MODE_FUSED, MODE_AUTO = 0, 1, 2
 
 GATE_KIND = {"H": 0, "X": 1, "Y": 2, "XB": 3, "YB": 4, "NOT": 5, "R": 6, "V": 7,
              "SU2": 8, "U": 9, "SWAP": 10}
@@ -35,7 +35,8 @@ class QsimOpts(ctypes.Structure):
 
 class QsimBatchStats(ctypes.Structure):
     _fields_ = [("circuits", ctypes.c_int64), ("gates", ctypes.c_int64), ("passes", ctypes.c_int64),
-                ("items", ctypes.c_int64), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("items", ctypes.c_int64), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
 
 
 class QsimCircuit(ctypes.Structure):
@@ -47,7 +48,10 @@ class QsimPlanStats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("ops", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("phases", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("gates", ctypes.c_double), ("alg_bytes", ctypes.c_double),
-                ("alg_flops", ctypes.c_double)]
+                ("alg_flops", ctypes.c_double), ("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("cand_tile_bits", ctypes.c_int32 * 8), ("cand_fuse_k", ctypes.c_int32 * 8),
+                ("cand_ms", ctypes.c_double * 8)]
 
 
 class QsimKernelTime(ctypes.Structure):
@@ -77,6 +81,7 @@ _SIGS = {
     "qsim_info": ([c_handle, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                    ctypes.POINTER(ctypes.c_void_p)], None),
     "qsim_set_basis": ([c_handle, ctypes.c_uint64], None),
+    "qsim_set_shor_state": ([c_handle, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64], None),
     "qsim_set_state": ([c_handle, ctypes.c_void_p, ctypes.c_size_t], None),
     "qsim_apply_1q": ([c_handle, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], None),
     "qsim_apply_ctrl": ([c_handle, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], None),

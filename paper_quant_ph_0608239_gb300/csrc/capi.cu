@@ -270,6 +270,19 @@ qsim_status qsim_set_basis(qsim_handle h, uint64_t x) {
     return QSIM_OK;
 }
 
+qsim_status qsim_set_shor_state(qsim_handle h, int X, uint64_t y, uint64_t G) {
+    CHECK_HANDLE(h);
+    if (X < 1 || X >= h->n) return fail(QSIM_EINVAL, "X = %d outside [1, n)", X);
+    if (G < 2 || G >= (1ull << 32) || G > (1ull << (h->n - X)))
+        return fail(QSIM_EINVAL, "G = %llu: need 2 <= G <= 2^(n - X) and G < 2^32", (unsigned long long)G);
+    if (y < 1 || y >= G) return fail(QSIM_EINVAL, "y must lie in [1, G)");
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    CK(launch(h, F_INIT, (double)state_bytes(h), 1,
+              [&] { return launch_shor_state(h->amp, (int)h->dt, h->n, X, y, G, h->stream); }),
+       "Shor initial state");
+    return QSIM_OK;
+}
+
 qsim_status qsim_set_state(qsim_handle h, const void *host_in, size_t bytes) {
     CHECK_HANDLE(h);
     if (!host_in || bytes != state_bytes(h)) return fail(QSIM_EINVAL, "need %zu bytes", state_bytes(h));
@@ -339,7 +352,7 @@ static void tile_defaults(const qsim_state *h, const qsim_opts *o, int &T, int &
     const int Tmax = 13;
     if (T > Tmax) T = Tmax;
     if (T < 2) T = 2;
-    RB = (tile2_supported((int)h->dt, T) && h->n >= T) ? T - 8 : 0;
+    RB = (tile2_supported((int)h->dt, T) && h->n >= T) ? T - 5 - kRegWarpBits : 0;
     L = RB ? 5 : (h->dt == QSIM_C64 ? 5 : 4);
     if (T - L > 10) L = T - 10;
     if (L >= T) L = T - 2;
@@ -463,6 +476,12 @@ struct qsim_plan_s {
     std::vector<float> bmats;        // their B operands, 2 (2^(k+1))^2 floats each
     float *d_bmats = nullptr;
     qsim_plan_stats stats{};
+    // QSIM_MODE_AUTO: one candidate plan per tile size / fusion width; the
+    // first runs time each candidate, later runs use the fastest
+    std::vector<qsim_plan_s *> cands;
+    std::vector<cudaEvent_t> ev;  // start, end per candidate
+    int next = 0;
+    int chosen = -1;
 };
 
 static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
@@ -471,6 +490,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     qsim_opts o;
     qsim_default_opts(&o);
     if (opts) o = *opts;
+    if (o.mode == QSIM_MODE_AUTO) o.mode = QSIM_MODE_FUSED;  // a single run cannot time candidates
     if (o.mode != QSIM_MODE_FUSED && o.mode != QSIM_MODE_PERGATE) return fail(QSIM_EINVAL, "unknown mode %d", o.mode);
     std::vector<PGate> pg;
     qsim_status st = prepare_all(h, gates, ng, pg);
@@ -575,11 +595,19 @@ qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, c
     return run_built(h, P, h->d_ops, h->d_phases);
 }
 
-qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
-                             qsim_plan *out) {
-    CHECK_HANDLE(h);
-    if (!out) return fail(QSIM_EINVAL, "out is NULL");
-    *out = nullptr;
+static void plan_release(qsim_plan_s *P) {
+    if (!P) return;
+    for (qsim_plan_s *c : P->cands) plan_release(c);
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+    if (P->d_bmats) cudaFree(P->d_bmats);
+    if (P->d_ops) cudaFree(P->d_ops);
+    if (P->d_phases) cudaFree(P->d_phases);
+    delete P;
+}
+
+static qsim_status create_one(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
+                              qsim_plan_s *&out) {
+    out = nullptr;
     qsim_plan_s *P = new qsim_plan_s;
     qsim_status st = build_plan(h, gates, ng, opts, *P);
     if (st == QSIM_OK && !P->plan.ops.empty()) {
@@ -603,22 +631,125 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
         else h->h2d += P->bmats.size() * sizeof(float);
     }
     if (st != QSIM_OK) {
-        if (P->d_bmats) cudaFree(P->d_bmats);
-        if (P->d_ops) cudaFree(P->d_ops);
-        if (P->d_phases) cudaFree(P->d_phases);
-        delete P;
+        plan_release(P);
         return st;
     }
-    *out = P;
+    P->stats.mode = P->mode;
+    P->stats.fuse_k = P->blocks.empty() ? 0 : P->blocks[0].k;
+    P->stats.chosen = -1;
+    out = P;
     return QSIM_OK;
+}
+
+// the stats of an AUTO plan: those of the chosen candidate (the first one
+// while tuning) plus the candidate table
+static void auto_stats(qsim_plan_s *P) {
+    const int shown = P->chosen >= 0 ? P->chosen : 0;
+    qsim_plan_stats s = P->cands[shown]->stats;
+    s.candidates = (int32_t)P->cands.size();
+    s.chosen = P->chosen;
+    for (size_t i = 0; i < P->cands.size() && i < 8; i++) {
+        s.cand_tile_bits[i] = P->cands[i]->stats.tile_bits;
+        s.cand_fuse_k[i] = P->cands[i]->stats.fuse_k;
+        s.cand_ms[i] = P->stats.cand_ms[i];
+    }
+    P->stats = s;
+}
+
+qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
+                             qsim_plan *out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!opts || opts->mode != QSIM_MODE_AUTO) {
+        qsim_plan_s *P = nullptr;
+        qsim_status st = create_one(h, gates, ng, opts, P);
+        if (st == QSIM_OK) *out = P;
+        return st;
+    }
+    // candidates: tile sizes (and, for complex64, tensor-core fusion widths)
+    std::vector<std::pair<int, int>> tk;  // (tile_bits, fuse_k)
+    auto add = [&](int T, int k) {
+        if (T > h->n) T = h->n;
+        for (auto &x : tk)
+            if (x.first == T && x.second == k) return;
+        tk.push_back({T, k});
+    };
+    if (h->dt == QSIM_C128) {
+        for (int T : {11, 12, 13}) add(T, 0);
+    } else {
+        for (int T : {12, 13}) add(T, 0);
+        for (int k : {4, 5})
+            if (fused_tc_supported((int)h->dt, k, h->n)) add(0, k);
+    }
+    qsim_plan_s *A = new qsim_plan_s;
+    A->n = h->n;
+    A->dt = h->dt;
+    A->mode = QSIM_MODE_AUTO;
+    std::memcpy(A->phys, h->phys, sizeof(A->phys));
+    for (auto &x : tk) {
+        if (A->cands.size() >= 8) break;
+        qsim_opts o = *opts;
+        o.mode = QSIM_MODE_FUSED;
+        o.tile_bits = x.second ? 0 : x.first;
+        o.fuse_k = x.second;
+        qsim_plan_s *c = nullptr;
+        qsim_status st = create_one(h, gates, ng, &o, c);
+        if (st == QSIM_EUNSUPPORTED) continue;  // e.g. no tile geometry for a fused width
+        if (st != QSIM_OK) {
+            plan_release(A);
+            return st;
+        }
+        A->cands.push_back(c);
+    }
+    if (A->cands.empty()) {
+        plan_release(A);
+        return fail(QSIM_EUNSUPPORTED, "no candidate plan");
+    }
+    for (size_t i = 0; i < 2 * A->cands.size(); i++) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            plan_release(A);
+            return fail(QSIM_ECUDA, "event");
+        }
+        A->ev.push_back(e);
+    }
+    if (A->cands.size() == 1) A->chosen = 0;
+    auto_stats(A);
+    *out = A;
+    return QSIM_OK;
+}
+
+static qsim_status run_one(qsim_state *h, qsim_plan_s *p) {
+    if (p->n != h->n || p->dt != h->dt || std::memcmp(p->phys, h->phys, sizeof(int) * h->n) != 0)
+        return fail(QSIM_EINVAL, "plan was made for another size, dtype or qubit layout");
+    return run_built(h, *p, p->d_ops, p->d_phases);
 }
 
 qsim_status qsim_plan_run(qsim_handle h, qsim_plan p) {
     CHECK_HANDLE(h);
     if (!p) return fail(QSIM_EINVAL, "null plan");
-    if (p->n != h->n || p->dt != h->dt || std::memcmp(p->phys, h->phys, sizeof(int) * h->n) != 0)
-        return fail(QSIM_EINVAL, "plan was made for another size, dtype or qubit layout");
-    return run_built(h, *p, p->d_ops, p->d_phases);
+    if (p->cands.empty()) return run_one(h, p);
+    const int nc = (int)p->cands.size();
+    if (p->chosen < 0 && p->next >= nc) {
+        // every candidate has run once: take the fastest
+        int best = 0;
+        for (int i = 0; i < nc; i++) {
+            float ms = 0.f;
+            CK(cudaEventSynchronize(p->ev[2 * i + 1]), "autotune wait");
+            CK(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]), "autotune time");
+            p->stats.cand_ms[i] = ms;
+            if (ms < p->stats.cand_ms[best]) best = i;
+        }
+        p->chosen = best;
+        auto_stats(p);
+    }
+    if (p->chosen >= 0) return run_one(h, p->cands[p->chosen]);
+    const int i = p->next++;
+    CK(cudaEventRecord(p->ev[2 * i], h->stream), "autotune start");
+    qsim_status st = run_one(h, p->cands[i]);
+    CK(cudaEventRecord(p->ev[2 * i + 1], h->stream), "autotune end");
+    return st;
 }
 
 qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
@@ -629,11 +760,8 @@ qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out) {
 
 qsim_status qsim_plan_free(qsim_plan p) {
     if (!p) return QSIM_OK;
-    if (p->d_ops || p->d_phases || p->d_bmats) cudaDeviceSynchronize();
-    if (p->d_bmats) cudaFree(p->d_bmats);
-    if (p->d_ops) cudaFree(p->d_ops);
-    if (p->d_phases) cudaFree(p->d_phases);
-    delete p;
+    cudaDeviceSynchronize();  // runs in flight may still read the plan's tables
+    plan_release(p);
     return QSIM_OK;
 }
 
@@ -965,27 +1093,6 @@ qsim_status qsim_sample(qsim_handle h, const double *u, size_t ns, uint64_t *out
     if (!u || !out) return fail(QSIM_EINVAL, "NULL buffer");
     for (size_t j = 0; j < ns; j++)
         if (!(u[j] >= 0.0 && u[j] < 1.0)) return fail(QSIM_EINVAL, "u[%zu] outside [0, 1)", j);
-    if (h->n < 5) {  // tiny registers: inverse CDF on the host from the probabilities
-        std::vector<double> p((size_t)1 << h->n);
-        qsim_status st = qsim_probs(h, p.data(), p.size());
-        if (st != QSIM_OK) return st;
-        double tot = 0;
-        for (double x : p) tot += x;
-        for (size_t j = 0; j < ns; j++) {
-            const double target = u[j] * tot;
-            double c = 0;
-            uint64_t pick = p.size() - 1;
-            for (size_t i = 0; i < p.size(); i++) {
-                c += p[i];
-                if (target < c) {
-                    pick = i;
-                    break;
-                }
-            }
-            out[j] = pick;
-        }
-        return QSIM_OK;
-    }
     const size_t need = sample_scratch_bytes(h->n) + ns * (sizeof(double) + sizeof(uint64_t)) + 256;
     void *buf = nullptr;
     CK(cudaMallocAsync(&buf, need, h->stream), "cudaMallocAsync sample buffers");
@@ -1016,6 +1123,7 @@ struct qsim_batch_s {
     BatchCircuit *d_circs = nullptr;
     BatchPass *d_passes = nullptr;
     TileOp *d_ops = nullptr;
+    TilePhase *d_phases = nullptr;
     BatchItem *d_items = nullptr;
     uint32_t *d_counters = nullptr;  // 64-bit item counter, then one counter per pass
     uint32_t *d_err = nullptr;
@@ -1042,7 +1150,7 @@ static void batch_release(qsim_batch_s *b) {
 static cudaError_t batch_enqueue(qsim_batch_s *b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->zero_bytes, s);
     if (e != cudaSuccess) return e;
-    return launch_batch(b->d_circs, b->d_passes, b->d_ops, b->d_items, b->nitems, b->d_counters,
+    return launch_batch(b->d_circs, b->d_passes, b->d_ops, b->d_phases, b->d_items, b->nitems, b->d_counters,
                         b->d_counters + 2, b->d_err, b->budget, b->sm_count, s);
 }
 
@@ -1068,9 +1176,11 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     std::vector<BatchCircuit> circs(nc);
     std::vector<BatchPass> passes;
     std::vector<TileOp> ops;
+    std::vector<TilePhase> phases;
     std::vector<std::vector<int>> pass_of(nc);
     int max_passes = 0;
     int64_t ngates = 0;
+    double alg_bytes = 0.0, alg_flops = 0.0;
     int ident[64];
     for (int q = 0; q < 64; q++) ident[q] = q;
     for (size_t i = 0; i < nc; i++) {
@@ -1084,7 +1194,9 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
         const int T = h->n < Tmax ? h->n : Tmax;
         const int L = T < 5 ? T : 5;
         Plan plan;
-        plan_tiles(pg, h->n, T, L, plan, 0);
+        // 12-bit tiles of complex64 circuits run the register program
+        const int RB = (T == 12 && tile2_supported(0, T)) ? kBatchRB : 0;
+        plan_tiles(pg, h->n, T, L, plan, RB);
         circs[i].amp = h->amp;
         circs[i].x0 = cs[i].x0;
         circs[i].pass_begin = (int32_t)passes.size();
@@ -1097,11 +1209,20 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
             plan.passes.push_back(pp);
         }
         for (const PassPlan &pp : plan.passes) {
+            alg_bytes += 2.0 * (double)state_bytes(h);  // each pass reads and writes the state once
+            alg_flops += pp.flops;
             BatchPass bp{};
             bp.geom = pp.geom;
             bp.op_begin = (int32_t)ops.size();
             bp.op_count = pp.op_count;
             bp.ntiles = 1u << (h->n - (pp.geom.L + pp.geom.H));
+            bp.phase_begin = (int32_t)phases.size();
+            bp.phase_count = pp.phase_count;
+            for (int k = 0; k < pp.phase_count; k++) {  // op indices rebased into the batch's op array
+                TilePhase ph = plan.phases[pp.phase_begin + k];
+                ph.op_begin = ph.op_begin - pp.op_begin + bp.op_begin;
+                phases.push_back(ph);
+            }
             ops.insert(ops.end(), plan.ops.begin() + pp.op_begin, plan.ops.begin() + pp.op_begin + pp.op_count);
             passes.push_back(bp);
         }
@@ -1127,10 +1248,11 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t sc = al(circs.size() * sizeof(BatchCircuit)), sp = al(passes.size() * sizeof(BatchPass));
     const size_t so = al(std::max<size_t>(ops.size(), 1) * sizeof(TileOp)), si = al(items.size() * sizeof(BatchItem));
+    const size_t sh = al(std::max<size_t>(phases.size(), 1) * sizeof(TilePhase));
     b->zero_bytes = 8 + passes.size() * 4 + 4 + 4;
     const size_t sz = al(b->zero_bytes);
     cudaError_t e = cudaSetDevice(dev);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dbuf, sc + sp + so + si + sz);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dbuf, sc + sp + so + si + sz + sh);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(uint32_t));
     if (e != cudaSuccess) {
         batch_release(b);
@@ -1143,11 +1265,14 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     b->d_items = reinterpret_cast<BatchItem *>(base + sc + sp + so);
     b->d_counters = reinterpret_cast<uint32_t *>(base + sc + sp + so + si);
     b->d_err = b->d_counters + 2 + passes.size();
+    b->d_phases = reinterpret_cast<TilePhase *>(base + sc + sp + so + si + sz);
     e = cudaMemcpy(b->d_circs, circs.data(), circs.size() * sizeof(BatchCircuit), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_passes, passes.data(), passes.size() * sizeof(BatchPass), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ops.empty())
         e = cudaMemcpy(b->d_ops, ops.data(), ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !phases.empty())
+        e = cudaMemcpy(b->d_phases, phases.data(), phases.size() * sizeof(TilePhase), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         batch_release(b);
         return cuda_fail(e, "batch upload");
@@ -1171,6 +1296,8 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     b->stats.gates = ngates;
     b->stats.passes = (int64_t)passes.size();
     b->stats.items = (int64_t)items.size();
+    b->stats.alg_bytes = alg_bytes;
+    b->stats.alg_flops = alg_flops;
     b->stats.graph = b->exec ? 1 : 0;
     *out = b;
     return QSIM_OK;

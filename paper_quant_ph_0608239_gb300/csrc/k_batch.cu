@@ -11,10 +11,15 @@
 // entirely in one CTA's shared memory, from a basis state generated there, and
 // touches global memory once, to store its result.
 //
+// A pass with register phases (12-bit tiles) runs the register-blocked
+// program of tile2_engine.cuh on the tile; other passes run the shared-memory
+// program of tile_ops.cuh.
+//
 // A wait that exceeds its budget sets an error word and the kernel returns;
 // the host reports QSIM_ETIMEOUT.
 #include "common.cuh"
 #include "kernels.hpp"
+#include "tile2_engine.cuh"
 #include "tile_ops.cuh"
 
 namespace qsim {
@@ -30,9 +35,12 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-__global__ void __launch_bounds__(kThreadsB) k_batch(const BatchCircuit *__restrict__ circs,
+static_assert(kThreadsB == (32 << kRegWarpBits), "the register program's block shape");
+
+__global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__restrict__ circs,
                                                      const BatchPass *__restrict__ passes,
                                                      const TileOp *__restrict__ ops,
+                                                     const TilePhase *__restrict__ phases,
                                                      const BatchItem *__restrict__ items, uint64_t nitems,
                                                      uint32_t *counters, uint32_t *done, uint32_t *err,
                                                      long long budget) {
@@ -92,9 +100,15 @@ __global__ void __launch_bounds__(kThreadsB) k_batch(const BatchCircuit *__restr
                 t[i] = __ldcg(a + (base | runoff[i >> L] | (i & lowmask)));
         }
         __syncthreads();
-        for (int o = ps.op_begin; o < ps.op_begin + ps.op_count; o++) {
-            tile_apply_op<float>(t, T, ops[o], base, nullptr);
-            __syncthreads();
+        if (ps.phase_count > 0) {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int p = ps.phase_begin; p < ps.phase_begin + ps.phase_count; p++)
+                t2::run_phase<false, kBatchRB>(t, phases[p], ops, base, lane, warp, 1, 1);
+        } else {
+            for (int o = ps.op_begin; o < ps.op_begin + ps.op_count; o++) {
+                tile_apply_op<float>(t, T, ops[o], base, nullptr);
+                __syncthreads();
+            }
         }
         for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) a[base | runoff[i >> L] | (i & lowmask)] = t[i];
         __threadfence();
@@ -108,8 +122,8 @@ __global__ void __launch_bounds__(kThreadsB) k_batch(const BatchCircuit *__restr
 size_t batch_smem_bytes() { return (size_t)8 << 12; }
 
 cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, const TileOp *ops,
-                         const BatchItem *items, uint64_t nitems, uint32_t *counters, uint32_t *done,
-                         uint32_t *err, long long budget, int sm_count, cudaStream_t s) {
+                         const TilePhase *phases, const BatchItem *items, uint64_t nitems, uint32_t *counters,
+                         uint32_t *done, uint32_t *err, long long budget, int sm_count, cudaStream_t s) {
     const size_t smem = batch_smem_bytes();
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreadsB, smem);
@@ -117,8 +131,8 @@ cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, con
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     unsigned grid = (unsigned)(sm_count * per_sm);
     if ((uint64_t)grid > nitems) grid = (unsigned)(nitems ? nitems : 1);
-    void *args[] = {(void *)&circs, (void *)&passes, (void *)&ops, (void *)&items, (void *)&nitems,
-                    (void *)&counters, (void *)&done, (void *)&err, (void *)&budget};
+    void *args[] = {(void *)&circs, (void *)&passes, (void *)&ops, (void *)&phases, (void *)&items,
+                    (void *)&nitems, (void *)&counters, (void *)&done, (void *)&err, (void *)&budget};
     // cooperative: every CTA resident at once, so a waiting CTA never blocks
     // the one it waits for from being scheduled
     return cudaLaunchCooperativeKernel((const void *)k_batch, dim3(grid), dim3(kThreadsB), args, smem, s);

@@ -42,7 +42,7 @@ __host__ __device__ __forceinline__ uint32_t canon_off(uint32_t row, uint32_t kk
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreadsTC, 1)
+__global__ void __launch_bounds__(kThreadsTC, 2)
     k_fused_tc(float2 *__restrict__ a, TileGeom g, FusedMap fm, const float *__restrict__ bmat, uint32_t *err,
                uint64_t ntiles) {
     constexpr int KR = 2 << K;              // real columns = 2 * 2^K
@@ -98,17 +98,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) != 0;
 
     const uint32_t idesc = umma_idesc_tf32(128, N);
+    const uint32_t ibase = [&] {  // epilogue: tile bits of this thread's group (TMEM lane)
+        const uint32_t m = (uint32_t)(32 * (warp & 3) + lane);
+        uint32_t x = 0;
+        for (int b = 0; b < T - K; b++) x |= ((m >> b) & 1u) << fm.row[b];
+        return x;
+    }();
     uint32_t ld_parity = 0, mma_parity = 0;
-    for (uint64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+    float2 *tin = reinterpret_cast<float2 *>(s_tile);
+    auto tile_base = [&](uint64_t tile) {
         uint64_t base = tile << L;
         for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
-        float2 *tin = reinterpret_cast<float2 *>(s_tile);
-        if (threadIdx.x < 32) {
-            if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar_ld, TS * 8u);
-            __syncwarp();
-            for (uint32_t j = threadIdx.x; j < nruns; j += 32)
-                bulk_g2s(tin + ((size_t)j << L), a + (base | runoff[j]), run_bytes, &bar_ld);
-        }
+        return base;
+    };
+    auto issue_load = [&](uint64_t tile) {  // warp 0
+        const uint64_t base = tile_base(tile);
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar_ld, TS * 8u);
+        __syncwarp();
+        for (uint32_t j = threadIdx.x; j < nruns; j += 32)
+            bulk_g2s(tin + ((size_t)j << L), a + (base | runoff[j]), run_bytes, &bar_ld);
+    };
+    // Pipeline: the next tile is fetched into the load buffer as soon as the
+    // MMAs have read A_lo out of it, so the fetch runs under this tile's
+    // epilogue and store; the store's reads of the output buffer are awaited
+    // only when the next split is about to overwrite it.
+    if (warp == 0 && !aborted && blockIdx.x < ntiles) issue_load(blockIdx.x);
+    for (uint64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+        const uint64_t base = tile_base(tile);
         aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC)) != 0;
         if (aborted) {
             mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC);  // let the copies in flight land
@@ -120,7 +136,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         float2 x[PER];
 #pragma unroll
         for (int s = 0; s < PER; s++) x[s] = tin[threadIdx.x + s * kThreadsTC];
-        __syncthreads();  // the tile buffer becomes A_lo
+        if (threadIdx.x < 32) bulk_wait_read_all();  // the previous store has read the output buffer
+        __syncthreads();  // the tile buffer becomes A_lo, the output buffer A_hi
 #pragma unroll
         for (int s = 0; s < PER; s++) {
             const uint32_t i = threadIdx.x + s * kThreadsTC;
@@ -156,6 +173,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mma_parity ^= 1u;
         tc_fence_after();
         if (aborted) break;
+        // A_lo is consumed: fetch the next tile into the load buffer
+        if (warp == 0 && tile + gridDim.x < ntiles) issue_load(tile + gridDim.x);
 
         // epilogue: warp w reads lanes 32 (w % 4) .. +31 (groups), column chunk w / 4
         float2 *tout = reinterpret_cast<float2 *>(s_ahi);
@@ -164,10 +183,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * chunk), r);
             tmem_ld_wait();
-            const uint32_t m = (uint32_t)(32 * (warp & 3) + lane);
-            uint32_t ibase = 0;
-#pragma unroll
-            for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
 #pragma unroll
             for (int q = 0; q < 16; q++) {
                 const uint32_t cidx = (uint32_t)(16 * chunk + q);  // output amplitude of the group
@@ -184,9 +199,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (uint32_t j = threadIdx.x; j < nruns; j += 32)
                 bulk_s2g(a + (base | runoff[j]), tout + ((size_t)j << L), run_bytes);
             bulk_commit();
-            bulk_wait_read_all();
         }
-        __syncthreads();
     }
     if (aborted && threadIdx.x == 0) atomicExch(err, kErrTimeout);
     if (threadIdx.x < 32) bulk_wait_all();
@@ -201,12 +214,25 @@ cudaError_t launch_k(void *amp, const TileGeom &g, const FusedMap &fm, const flo
                      int sm_count, cudaStream_t s) {
     constexpr int KR = 2 << K;
     constexpr int T = K + 7;
+    // tile + operand buffers, B_hi / B_lo
     const size_t smem = 2 * ((size_t)8 << T) + 2 * (size_t)KR * KR * 4;
     const uint64_t ntiles = 1ull << (g.n - T);
-    uint64_t grid = (uint64_t)sm_count * (smem <= 100 * 1024 ? 2 : 1);
-    if (grid > ntiles) grid = ntiles;
     cudaError_t e = cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // resident blocks per SM from the block's shared memory (plus 1 KiB the
+    // system reserves per block, of 228 KiB) and registers (64 Ki per SM),
+    // at most 4 (tensor memory: 4 x 128 columns)
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, k_fused_tc<K>);
+    if (e != cudaSuccess) return e;
+    const size_t per_block = smem + fa.sharedSizeBytes + 1024;
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kThreadsTC;
+    int per_sm = (int)((228u * 1024u) / per_block);
+    if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    if (grid > ntiles) grid = ntiles;
     k_fused_tc<K><<<(unsigned)grid, kThreadsTC, smem, s>>>(static_cast<float2 *>(amp), g, fm, bmat, err, ntiles);
     return cudaGetLastError();
 }

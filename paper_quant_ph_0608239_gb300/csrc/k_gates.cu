@@ -10,6 +10,8 @@
 // so both members of the pair are read with coalesced accesses for every
 // target bit; the low target bits fall inside one 32-byte sector and are
 // merged by L1.
+#include <cmath>
+
 #include "common.cuh"
 #include "df64.cuh"
 #include "kernels.hpp"
@@ -239,6 +241,24 @@ __global__ void k_init_basis(amp_t<R> *__restrict__ a, uint64_t D, uint64_t x) {
         a[i] = mk<R>(i == x ? (R)1 : (R)0, (R)0);
 }
 
+// Eq. Shor2: a_{x + 2^X f(x)} = amp for x < 2^X, f(x) = y^x mod G (square and
+// multiply; G < 2^32, so every product fits in 64 bits).  The other
+// amplitudes are zeroed by the caller.
+template <class R>
+__global__ void k_shor_state(amp_t<R> *__restrict__ a, int X, uint64_t y, uint64_t G, R amp) {
+    const uint64_t D = 1ull << X;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < D; x += stride) {
+        uint64_t f = 1 % G, b = y % G, e = x;
+        while (e) {
+            if (e & 1ull) f = (f * b) % G;
+            b = (b * b) % G;
+            e >>= 1;
+        }
+        a[x | (f << X)] = mk<R>(amp, (R)0);
+    }
+}
+
 struct Qpos {
     int p[8];
 };
@@ -359,6 +379,21 @@ cudaError_t launch_init_basis(void *amp, int dt, int n, uint64_t x, cudaStream_t
         k_init_basis<float><<<grid, kThreads, 0, s>>>(static_cast<float2 *>(amp), D, x);
     else
         k_init_basis<double><<<grid, kThreads, 0, s>>>(static_cast<double2 *>(amp), D, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shor_state(void *amp, int dt, int n, int X, uint64_t y, uint64_t G, cudaStream_t s) {
+    if (X < 1 || X >= n || G < 2 || G >= (1ull << 32) || G > (1ull << (n - X))) return cudaErrorInvalidValue;
+    const size_t bytes = (size_t)(dt == 0 ? 8 : 16) << n;
+    cudaError_t e = cudaMemsetAsync(amp, 0, bytes, s);  // all-zero bits are +0.0
+    if (e != cudaSuccess) return e;
+    const uint64_t D = 1ull << X;
+    const int grid = grid_for(D, 4);
+    const double v = std::sqrt(std::ldexp(1.0, -X));  // 2^(-X/2), correctly rounded
+    if (dt == 0)
+        k_shor_state<float><<<grid, kThreads, 0, s>>>(static_cast<float2 *>(amp), X, y, G, (float)v);
+    else
+        k_shor_state<double><<<grid, kThreads, 0, s>>>(static_cast<double2 *>(amp), X, y, G, v);
     return cudaGetLastError();
 }
 

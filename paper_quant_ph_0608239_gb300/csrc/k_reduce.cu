@@ -240,10 +240,15 @@ __global__ void k_draw(const amp_t<R> *__restrict__ a, int n, PhysPos pp, bool i
             continue;
         }
         double before = lo ? cum[lo - 1] : 0.0;
-        const uint64_t per = (1ull << S) / 32;  // values per lane
-        const uint64_t x0 = (lo << S) + lane * per;
+        // values per lane; blocks of fewer than 32 values (registers of fewer
+        // than 5 qubits) give one value to each of the first 2^S lanes
+        const uint64_t blk = 1ull << S;
+        const uint64_t per = blk >= 32 ? blk / 32 : 1;
+        const int nlanes = blk >= 32 ? 32 : (int)blk;
+        const bool active = lane < nlanes;
+        const uint64_t x0 = (lo << S) + (uint64_t)lane * per;
         double mine = 0.0;
-        for (uint64_t j = 0; j < per; j++) {
+        for (uint64_t j = 0; active && j < per; j++) {
             const amp_t<R> v = a[ident ? (x0 + j) : phys_of(x0 + j, pp, n)];
             mine += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
         }
@@ -254,8 +259,8 @@ __global__ void k_draw(const amp_t<R> *__restrict__ a, int n, PhysPos pp, bool i
             const double t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, target < before + incl);
-        int owner = ball ? __ffs(ball) - 1 : 31;
+        const unsigned ball = __ballot_sync(0xffffffffu, active && target < before + incl);
+        int owner = ball ? __ffs(ball) - 1 : nlanes - 1;
         double c = before + __shfl_sync(0xffffffffu, incl - mine, owner);
         if (lane == owner) {
             uint64_t pick = x0 + per - 1;
@@ -348,9 +353,8 @@ size_t sample_scratch_bytes(int n) {
 
 cudaError_t launch_sample(const void *amp, int dt, int n, const int *physpos, bool identity, const double *du,
                           size_t ns, uint64_t *dout, double *scratch, cudaStream_t s) {
-    // block size 2^S with at least one value per lane
+    // blocks of 2^S values
     const int S = n >= kSampleBlockBits ? kSampleBlockBits : n;
-    if (S < 5) return cudaErrorInvalidValue;  // the host handles n < 5 through probabilities
     const uint64_t nb = 1ull << (n - S);
     const PhysPos pp = to_pp(physpos, n);
     uint64_t g = nb < 152ull * 8 ? nb : 152ull * 8;

@@ -8,290 +8,46 @@
 //                           lanes l and l ^ 2^t of one warp (warp shuffles)
 //   RB of the bits >= 5     register bits: a gate on them pairs two registers
 //                           of one thread
-//   the other 3 bits >= 5   warp bits (8 warps)
+//   the other bits >= 5     warp bits (kRegWarpBits of them: 2^kRegWarpBits warps)
 //
 // The program is cut into phases; a phase loads the tile from shared memory
 // into registers under its own choice of register bits, applies its gates,
 // and stores back (optionally to permuted positions, which is how quantum SWAP
-// gates and qubit interchanges are applied).  T = RB + 8.
+// gates and qubit interchanges are applied).  T = 5 + RB + kRegWarpBits.
 //
 // complex64 computes in FP32.  complex128 computes in double-float (FP32
 // pairs, df64.cuh): the tile arrives as IEEE doubles, the first phase converts
 // them with integer operations, later phases keep the double-float form in
-// shared memory, and the last phase converts back.
+// shared memory, and the last phase converts back.  The per-phase engine is
+// in tile2_engine.cuh (shared with the batch kernel).
 #include "common.cuh"
 #include "df64.cuh"
 #include "kernels.hpp"
 #include "ptx.cuh"
+#include "tile2_engine.cuh"
 
 namespace qsim {
 
 namespace {
 
-constexpr int kThreads2 = 256;
+constexpr int kThreads2 = 32 << kRegWarpBits;
 constexpr int kMaxH2 = 10;
 constexpr int kMaxCopyShift2 = 14;
 constexpr long long kWaitBudget2 = 4000000000ll;
 
-// ---------------------------------------------------------- amplitude types
-template <bool C128> struct AmpT;
-template <> struct AmpT<false> {
-    using V = float2;
-    using S = float2;  // shared-memory element
-};
-template <> struct AmpT<true> {
-    using V = dcx;
-    using S = double2;
-};
-
-// coefficients of one 2x2 entry
-template <bool C128> struct Coef;
-template <> struct Coef<false> { float2 c; };
-template <> struct Coef<true> { dcx c; };
-
-__device__ __forceinline__ float2 coef64(const TileOp &op, int k) { return make_float2(op.uh[2 * k], op.uh[2 * k + 1]); }
-__device__ __forceinline__ dcx coef128(const TileOp &op, int k) {
-    return dcx{df{op.uh[2 * k], op.ul[2 * k]}, df{op.uh[2 * k + 1], op.ul[2 * k + 1]}};
-}
-
-// ---- arithmetic on one amplitude type
-__device__ __forceinline__ float2 vmul(float2 u, float2 a) { return cmul<float>(u, a); }
-__device__ __forceinline__ float2 vmul2(float2 u, float2 a, float2 v, float2 b) { return cmul2<float>(u, a, v, b); }
-__device__ __forceinline__ float2 vrmul2(float2 u, float2 a, float2 v, float2 b) {
-    return make_float2(fmaf(u.x, a.x, v.x * b.x), fmaf(u.x, a.y, v.x * b.y));
-}
-__device__ __forceinline__ dcx vmul(const dcx &u, const dcx &a) { return dcx_mul(u, a); }
-__device__ __forceinline__ dcx vmul2(const dcx &u, const dcx &a, const dcx &v, const dcx &b) {
-    return dcx_mul2(u, a, v, b);
-}
-__device__ __forceinline__ dcx vrmul2(const dcx &u, const dcx &a, const dcx &v, const dcx &b) {
-    return dcx_rmul2(u.re, a, v.re, b);
-}
-
-__device__ __forceinline__ float2 shfl_x(float2 v, int m) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-__device__ __forceinline__ dcx shfl_x(const dcx &v, int m) {
-    return dcx{df{__shfl_xor_sync(0xffffffffu, v.re.h, m), __shfl_xor_sync(0xffffffffu, v.re.l, m)},
-               df{__shfl_xor_sync(0xffffffffu, v.im.h, m), __shfl_xor_sync(0xffffffffu, v.im.l, m)}};
-}
-
-// ---- shared-memory formats
-// complex64: float2.  complex128: IEEE double2 (fmt 0) or double-float
-// (fmt 1: re.h, re.l, im.h, im.l as four floats in the same 16 bytes).
-__device__ __forceinline__ float2 ld_amp(const float2 *t, uint32_t i, int) { return t[i]; }
-__device__ __forceinline__ void st_amp(float2 *t, uint32_t i, float2 v, int) { t[i] = v; }
-__device__ __forceinline__ dcx ld_amp(const double2 *t, uint32_t i, int fmt) {
-    if (fmt == 0) {
-        const double2 d = t[i];
-        return dcx{df_from_double(d.x), df_from_double(d.y)};
-    }
-    const float4 f = reinterpret_cast<const float4 *>(t)[i];
-    return dcx{df{f.x, f.y}, df{f.z, f.w}};
-}
-__device__ __forceinline__ void st_amp(double2 *t, uint32_t i, const dcx &v, int fmt) {
-    if (fmt == 0) {
-        t[i] = make_double2(df_to_double(v.re), df_to_double(v.im));
-    } else {
-        reinterpret_cast<float4 *>(t)[i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
-    }
-}
-
-// ---- gate application in registers
-enum { PK_GENERAL = 0, PK_REAL = 1, PK_ANTI = 2, PK_EXCH = 3 };
-
-template <int RB, int K, int PK, bool CT, typename V>
-__device__ __forceinline__ void pair_reg(V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        if (j & (1 << K)) continue;
-        const int j1 = j | (1 << K);
-        if (CT && !(thr_ok && ((uint32_t)j & creg) == creg)) continue;
-        const V a = v[j], b = v[j1];
-        if (PK == PK_GENERAL) {
-            v[j] = vmul2(u[0], a, u[1], b);
-            v[j1] = vmul2(u[2], a, u[3], b);
-        } else if (PK == PK_REAL) {
-            v[j] = vrmul2(u[0], a, u[1], b);
-            v[j1] = vrmul2(u[2], a, u[3], b);
-        } else if (PK == PK_ANTI) {
-            v[j] = vmul(u[1], b);
-            v[j1] = vmul(u[2], a);
-        } else {
-            v[j] = b;
-            v[j1] = a;
-        }
-    }
-}
-
-template <int RB, int PK, bool CT, typename V>
-__device__ __forceinline__ void pair_reg_dispatch(int k, V (&v)[1 << RB], const V (&u)[4], bool thr_ok,
-                                                  uint32_t creg) {
-    switch (k) {
-    case 0: pair_reg<RB, 0, PK, CT>(v, u, thr_ok, creg); break;
-    case 1: pair_reg<RB, 1, PK, CT>(v, u, thr_ok, creg); break;
-    case 2: pair_reg<RB, 2, PK, CT>(v, u, thr_ok, creg); break;
-    case 3: pair_reg<RB, 3, PK, CT>(v, u, thr_ok, creg); break;
-    default:
-        if constexpr (RB > 4) pair_reg<RB, (RB > 4 ? 4 : 0), PK, CT>(v, u, thr_ok, creg);
-        break;
-    }
-}
-
-// target on lane bit t: partner in lane ^ 2^t; each lane computes its own
-// output with the coefficients of its row.
-template <int RB, int PK, bool CT, typename V>
-__device__ __forceinline__ void pair_lane(int t, V (&v)[1 << RB], const V (&u)[4], bool thr_ok, uint32_t creg,
-                                          int lane) {
-    const bool upper = (lane >> t) & 1;
-    const V c0 = upper ? u[3] : u[0];  // coefficient of the lane's own amplitude
-    const V c1 = upper ? u[2] : u[1];  // coefficient of the partner's amplitude
-    const int m = 1 << t;
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        const V w = shfl_x(v[j], m);
-        if (CT && !(thr_ok && ((uint32_t)j & creg) == creg)) continue;
-        if (PK == PK_GENERAL) v[j] = vmul2(c0, v[j], c1, w);
-        else if (PK == PK_REAL) v[j] = vrmul2(c0, v[j], c1, w);
-        else if (PK == PK_ANTI) v[j] = vmul(c1, w);
-        else v[j] = w;
-    }
-}
-
-template <bool C128>
-__device__ __forceinline__ typename AmpT<C128>::V coef(const TileOp &op, int k);
-template <> __device__ __forceinline__ float2 coef<false>(const TileOp &op, int k) { return coef64(op, k); }
-template <> __device__ __forceinline__ dcx coef<true>(const TileOp &op, int k) { return coef128(op, k); }
-
-template <int RB, int K>
-__device__ __forceinline__ void phase_reg(float2 (&v)[1 << RB], float2 u, bool thr_ok, uint32_t creg) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        if (!((j >> K) & 1)) continue;
-        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
-        v[j] = vmul(u, v[j]);
-    }
-}
-
-template <int RB, int K>
-__device__ __forceinline__ void diag_reg(float2 (&v)[1 << RB], float2 u0, float2 u1, bool thr_ok, uint32_t creg) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        if (!(thr_ok && ((uint32_t)j & creg) == creg)) continue;
-        v[j] = vmul(((j >> K) & 1) ? u1 : u0, v[j]);
-    }
-}
-
-// bit flip on register slot K where register slot C is 1: a renaming of
-// registers, no arithmetic
-template <int RB, int K, int C>
-__device__ __forceinline__ void exch1(float2 (&v)[1 << RB]) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        if (!((j >> C) & 1) || ((j >> K) & 1)) continue;
-        const float2 t = v[j];
-        v[j] = v[j | (1 << K)];
-        v[j | (1 << K)] = t;
-    }
-}
-
-template <int RB, int K>
-__device__ __forceinline__ void exch1_c(int c, float2 (&v)[1 << RB]) {
-    switch (c) {
-    case 0: if constexpr (K != 0) exch1<RB, K, 0>(v); break;
-    case 1: if constexpr (K != 1) exch1<RB, K, 1>(v); break;
-    case 2: if constexpr (K != 2) exch1<RB, K, 2>(v); break;
-    case 3: if constexpr (K != 3) exch1<RB, K, 3>(v); break;
-    default: if constexpr (RB > 4 && K != 4) exch1<RB, K, (RB > 4 ? 4 : 0)>(v); break;
-    }
-}
-
-// One op of a phase.  op.code = family * 8 + k selects a code path whose
-// register indices are compile-time constants.
-template <int RB>
-__device__ __forceinline__ void apply_rop(const TileOp &op, float2 (&v)[1 << RB], uint32_t thr_idx, int lane,
-                                          uint64_t base) {
-    if ((base & op.gcmask) != op.gcmask) return;  // a control outside the tile is 0 here
-    const bool thr_ok = (thr_idx & op.lcthr) == op.lcthr;
-    const uint32_t creg = op.creg;
-    const float4 c01 = *reinterpret_cast<const float4 *>(op.uh);
-    const float4 c23 = *reinterpret_cast<const float4 *>(op.uh + 4);
-    const float2 u[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w), make_float2(c23.x, c23.y),
-                         make_float2(c23.z, c23.w)};
-    switch (op.code) {
-#define QSIM_K_CASES(FAM, STMT)                         \
-    case FAM * 8 + 0: { constexpr int K = 0; STMT; } break; \
-    case FAM * 8 + 1: { constexpr int K = 1; STMT; } break; \
-    case FAM * 8 + 2: { constexpr int K = 2; STMT; } break; \
-    case FAM * 8 + 3: { constexpr int K = 3; STMT; } break; \
-    case FAM * 8 + 4: if constexpr (RB > 4) { constexpr int K = RB > 4 ? 4 : 0; STMT; } break;
-        QSIM_K_CASES(RC_GEN, (pair_reg<RB, K, PK_GENERAL, false>(v, u, true, 0u)))
-        QSIM_K_CASES(RC_REAL, (pair_reg<RB, K, PK_REAL, false>(v, u, true, 0u)))
-        QSIM_K_CASES(RC_GENC, (pair_reg<RB, K, PK_GENERAL, true>(v, u, thr_ok, creg)))
-        QSIM_K_CASES(RC_REALC, (pair_reg<RB, K, PK_REAL, true>(v, u, thr_ok, creg)))
-        QSIM_K_CASES(RC_ANTI, (pair_reg<RB, K, PK_ANTI, true>(v, u, thr_ok, creg)))
-        QSIM_K_CASES(RC_EXCHC, (pair_reg<RB, K, PK_EXCH, true>(v, u, thr_ok, creg)))
-        QSIM_K_CASES(RC_PHASE, (phase_reg<RB, K>(v, u[3], thr_ok, creg)))
-        QSIM_K_CASES(RC_DIAG, (diag_reg<RB, K>(v, u[0], u[3], thr_ok, creg)))
-        QSIM_K_CASES(RC_EXCH1, (exch1_c<RB, K>(op.cslot, v)))
-#undef QSIM_K_CASES
-    case RC_LANE * 8 + PK_GENERAL: pair_lane<RB, PK_GENERAL, false>(op.tl, v, u, true, 0u, lane); break;
-    case RC_LANE * 8 + PK_REAL: pair_lane<RB, PK_REAL, false>(op.tl, v, u, true, 0u, lane); break;
-    case RC_LANE * 8 + PK_ANTI: pair_lane<RB, PK_ANTI, false>(op.tl, v, u, true, 0u, lane); break;
-    case RC_LANE * 8 + PK_EXCH: pair_lane<RB, PK_EXCH, false>(op.tl, v, u, true, 0u, lane); break;
-    case RC_LANEC * 8 + PK_GENERAL: pair_lane<RB, PK_GENERAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
-    case RC_LANEC * 8 + PK_REAL: pair_lane<RB, PK_REAL, true>(op.tl, v, u, thr_ok, creg, lane); break;
-    case RC_LANEC * 8 + PK_ANTI: pair_lane<RB, PK_ANTI, true>(op.tl, v, u, thr_ok, creg, lane); break;
-    case RC_LANEC * 8 + PK_EXCH: pair_lane<RB, PK_EXCH, true>(op.tl, v, u, thr_ok, creg, lane); break;
-    case RC_THR * 8 + 0:  // phase on a lane or warp bit: the factor is uniform per thread
-        if ((thr_idx >> op.tl) & 1u) {
-#pragma unroll
-            for (int j = 0; j < (1 << RB); j++)
-                if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(u[3], v[j]);
-        }
-        break;
-    case RC_THR * 8 + 1: {
-        const float2 f = ((thr_idx >> op.tl) & 1u) ? u[3] : u[0];
-#pragma unroll
-        for (int j = 0; j < (1 << RB); j++)
-            if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
-        break;
-    }
-    case RC_GLOB * 8 + 0: {
-        const float2 f = ((base >> op.tl) & 1ull) ? u[3] : u[0];
-#pragma unroll
-        for (int j = 0; j < (1 << RB); j++)
-            if (thr_ok && ((uint32_t)j & creg) == creg) v[j] = vmul(f, v[j]);
-        break;
-    }
-    default: break;
-    }
-}
-
-// local index of register j of a thread: its lane/warp bits plus the bits
-// of j scattered onto the register slots
-template <int RB>
-__device__ __forceinline__ uint32_t reg_index(uint32_t thr_idx, const uint32_t (&rbit)[RB], int j) {
-    uint32_t x = thr_idx;
-#pragma unroll
-    for (int k = 0; k < RB; k++)
-        if ((j >> k) & 1) x |= rbit[k];
-    return x;
-}
-
 constexpr int kMaxStagedOps = 96;     // ops of a pass copied to shared memory (18 KiB)
 constexpr int kMaxStagedPhases = 48;  // phases of a pass copied to shared memory (2.25 KiB)
 #ifndef QSIM_T2_MINB
-#define QSIM_T2_MINB 3
+#define QSIM_T2_MINB (QSIM_T2_NWB == 4 ? 2 : 3)
 #endif
 constexpr int kMinBlocks2 = QSIM_T2_MINB;  // resident CTAs per SM the register budget is sized for
 
 template <bool C128, int RB>
 __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
-    k_tile2(typename AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases_g, int nphases,
+    k_tile2(typename t2::AmpT<C128>::S *__restrict__ a, TileGeom g, const TilePhase *__restrict__ phases_g, int nphases,
             const TileOp *__restrict__ ops_g, int op_base, int op_count, uint32_t *err, uint64_t ntiles) {
-    using S = typename AmpT<C128>::S;
-    using V = typename AmpT<C128>::V;
+    using S = typename t2::AmpT<C128>::S;
+    using V = typename t2::AmpT<C128>::V;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S *t = reinterpret_cast<S *>(smem_raw);
     __shared__ __align__(8) uint64_t bar;
@@ -366,36 +122,8 @@ __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
         parity ^= 1u;
 
         for (int p = 0; p < nphases; p++) {
-            const TilePhase &ph = phases[p];
-            uint32_t thr_idx = (uint32_t)lane;
-#pragma unroll
-            for (int k = 0; k < 3; k++) thr_idx |= (uint32_t)((warp >> k) & 1) << ph.wb[k];
-            uint32_t rbit[RB];
-#pragma unroll
-            for (int k = 0; k < RB; k++) rbit[k] = 1u << ph.rb[k];
-            V v[1 << RB];
             const int lfmt = (C128 && p == 0) ? 0 : 1, sfmt = (C128 && p == nphases - 1) ? 0 : 1;
-#pragma unroll
-            for (int j = 0; j < (1 << RB); j++) v[j] = ld_amp(t, reg_index<RB>(thr_idx, rbit, j), lfmt);
-            for (int o = ph.op_begin; o < ph.op_begin + ph.op_count; o++) apply_rop<RB>(ops[o], v, thr_idx, lane, base);
-            if (ph.nperm) {
-                __syncthreads();  // every thread has read its inputs before any permuted write
-#pragma unroll
-                for (int j = 0; j < (1 << RB); j++) {
-                    const uint32_t x = reg_index<RB>(thr_idx, rbit, j);
-                    uint32_t y = x;
-                    for (int k = 0; k < ph.nperm; k++) {
-                        const uint32_t bl = (x >> ph.pl[k]) & 1u, bh = (x >> ph.ph[k]) & 1u;
-                        y &= ~((1u << ph.pl[k]) | (1u << ph.ph[k]));
-                        y |= (bl << ph.ph[k]) | (bh << ph.pl[k]);
-                    }
-                    st_amp(t, y, v[j], sfmt);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < (1 << RB); j++) st_amp(t, reg_index<RB>(thr_idx, rbit, j), v[j], sfmt);
-            }
-            __syncthreads();
+            t2::run_phase<C128, RB>(t, phases[p], ops, base, lane, warp, lfmt, sfmt);
         }
 
         fence_proxy_async_smem();
@@ -417,7 +145,7 @@ __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
 template <bool C128, int RB>
 cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int nphases, const TileOp *ops,
                     int op_base, int op_count, uint32_t *err, int sm_count, cudaStream_t s) {
-    using S = typename AmpT<C128>::S;
+    using S = typename t2::AmpT<C128>::S;
     const int T = g.L + g.H;
     const size_t smem = (sizeof(S) << T) + (op_count <= kMaxStagedOps ? (size_t)op_count * sizeof(TileOp) : 0) +
                         (nphases <= kMaxStagedPhases ? (size_t)nphases * sizeof(TilePhase) : 0);
@@ -443,8 +171,9 @@ cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePh
                               cudaStream_t s) {
     const int T = g.L + g.H;
     if (!tile2_supported(dt, T) || g.L < 5 || g.H > kMaxH2 || T > g.n) return cudaErrorInvalidValue;
-    if (T == 13) return launch2<false, 5>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
-    return launch2<false, 4>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
+    constexpr int RB12 = 12 - 5 - kRegWarpBits, RB13 = 13 - 5 - kRegWarpBits;
+    if (T == 13) return launch2<false, RB13>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
+    return launch2<false, RB12>(amp, g, phases, nphases, ops, op_base, op_count, err, sm_count, s);
 }
 
 }  // namespace qsim

@@ -72,22 +72,36 @@ __device__ __forceinline__ dcx coefx(const DfOp &op, int k) {
     return dcx{df{c.x, c.y}, df{c.z, c.w}};
 }
 
+// Index of the p-th element whose bits at the positions in `fixed` are zero:
+// zeros inserted at those positions in ascending order.
+__device__ __forceinline__ uint32_t expand_fixed(uint32_t p, uint32_t fixed) {
+    while (fixed) {
+        p = ins0d(p, __ffs(fixed) - 1);
+        fixed &= fixed - 1u;
+    }
+    return p;
+}
+
 // op: the staged copy; gop: the op in global memory (read only for the
-// permutation's bit list)
+// permutation's bit list).  An op enumerates only the amplitudes its local
+// controls select (the control bits fixed at 1), so a gate with c controls
+// costs 2^-c of a sweep.
 __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, uint64_t base) {
     if ((base & op.gcmask) != op.gcmask) return;
     const uint32_t lc = op.lcmask;
     const uint32_t TS = 1u << T;
     const int kind = op.kind;
+    const int nlc = __popc(lc);
     if (kind == TOP_GENERAL || kind == TOP_ANTIDIAG || kind == TOP_EXCHANGE) {
         const int tl = op.tl;
-        const uint32_t bt = 1u << tl;
+        const uint32_t bt = 1u << tl, fixed = bt | lc;
         const int pk = op.pk;
+        const uint32_t npair = (TS >> 1) >> nlc;
+        auto pair0 = [&](uint32_t p) { return lc ? (expand_fixed(p, fixed) | lc) : ins0d(p, tl); };
         const dcx u0 = coefx(op, 0), u1 = coefx(op, 1), u2 = coefx(op, 2), u3 = coefx(op, 3);
         if (pk == 3) {  // exchange: move the bytes
-            for (uint32_t p = threadIdx.x; p < (TS >> 1); p += blockDim.x) {
-                const uint32_t i0 = ins0d(p, tl);
-                if ((i0 & lc) != lc) continue;
+            for (uint32_t p = threadIdx.x; p < npair; p += blockDim.x) {
+                const uint32_t i0 = pair0(p);
                 const uint32_t i1 = i0 | bt;
                 const float4 x = t[i0];
                 t[i0] = t[i1];
@@ -97,14 +111,15 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
         }
         // two independent pairs per iteration: the two-sum chains of one pair
         // fill the latency of the other's
-        const uint32_t half = TS >> 1, step = blockDim.x;
+        const uint32_t half = npair, step = blockDim.x;
         for (uint32_t p = threadIdx.x; p < half; p += 2 * step) {
             const uint32_t q = p + step;
             const bool has2 = q < half;
-            const uint32_t i0 = ins0d(p, tl), j0 = has2 ? ins0d(q, tl) : i0;
-            const bool ok0 = (i0 & lc) == lc, ok1 = has2 && (j0 & lc) == lc;
-            const dcx a = ldx(t, i0), b = ldx(t, i0 | bt);
-            const dcx c = ldx(t, j0), d = ldx(t, j0 | bt);
+            const uint32_t i0 = pair0(p), j0 = has2 ? pair0(q) : i0;
+            const uint32_t i1 = i0 | bt, j1 = j0 | bt;
+            const bool ok0 = true, ok1 = has2;
+            const dcx a = ldx(t, i0), b = ldx(t, i1);
+            const dcx c = ldx(t, j0), d = ldx(t, j1);
             dcx x0, x1, y0, y1;
             if (pk == 0) {
                 x0 = dcx_mul2(u0, a, u1, b);
@@ -124,26 +139,27 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
             }
             if (ok0) {
                 stx(t, i0, x0);
-                stx(t, i0 | bt, x1);
+                stx(t, i1, x1);
             }
             if (ok1) {
                 stx(t, j0, y0);
-                stx(t, j0 | bt, y1);
+                stx(t, j1, y1);
             }
         }
     } else if (kind == TOP_PHASE) {
-        const uint32_t bt = 1u << op.tl;
+        const uint32_t bt = 1u << op.tl, fixed = bt | lc;
         const dcx u3 = coefx(op, 3);
-        for (uint32_t p = threadIdx.x; p < (TS >> 1); p += blockDim.x) {
-            const uint32_t i = ins0d(p, op.tl) | bt;
-            if ((i & lc) != lc) continue;
+        const uint32_t cnt = (TS >> 1) >> nlc;
+        for (uint32_t p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t i = (lc ? expand_fixed(p, fixed) | lc : ins0d(p, op.tl)) | bt;
             stx(t, i, dcx_mul(u3, ldx(t, i)));
         }
     } else if (kind == TOP_DIAG || kind == TOP_DIAG_G) {
         const dcx u0 = coefx(op, 0), u3 = coefx(op, 3);
         const bool global_one = kind == TOP_DIAG_G && ((base >> op.tl) & 1ull);
-        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
-            if ((i & lc) != lc) continue;
+        const uint32_t cnt = TS >> nlc;
+        for (uint32_t p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t i = lc ? expand_fixed(p, lc) | lc : p;
             const bool one = kind == TOP_DIAG ? ((i >> op.tl) & 1u) : global_one;
             stx(t, i, dcx_mul(one ? u3 : u0, ldx(t, i)));
         }

@@ -86,6 +86,14 @@ enum RegFamily : int {
     RC_GLOB = 12    // diagonal on a bit outside the tile (tl = physical bit)
 };
 
+// Warp bits of the register-blocked kernel (k_tile2.cu): a block has
+// 2^kRegWarpBits warps, and a tile of T bits holds 5 lane bits, kRegWarpBits
+// warp bits and T - 5 - kRegWarpBits register bits.
+#ifndef QSIM_T2_NWB
+#define QSIM_T2_NWB 3
+#endif
+constexpr int kRegWarpBits = QSIM_T2_NWB;
+
 // One phase of a register-blocked tile program: which local bits are held in
 // registers, the ops it applies, and an optional permutation of local bit
 // pairs applied when the phase stores back (quantum SWAP gates, interchanges).
@@ -122,6 +130,9 @@ struct FixedBitsHost {
 };
 
 cudaError_t launch_init_basis(void *amp, int dt, int n, uint64_t x, cudaStream_t s);
+
+// Eq. Shor2 state: zero, then a_{x + 2^X (y^x mod G)} = 2^(-X/2) for x < 2^X.
+cudaError_t launch_shor_state(void *amp, int dt, int n, int X, uint64_t y, uint64_t G, cudaStream_t s);
 
 // Pair sweep: enumerate i0 = expand(p, fb) for p < 2^(n - fb.npos), partner
 // i1 = i0 ^ pmask, apply the gate class gc with matrix U.
@@ -173,9 +184,10 @@ struct BatchCircuit {
 };
 struct BatchPass {
     TileGeom geom;
-    int32_t op_begin, op_count;  // in the batch's op array
+    int32_t op_begin, op_count;        // in the batch's op array
     uint32_t ntiles;
-    uint32_t pad;
+    int32_t phase_begin, phase_count;  // register phases (tile2_engine.cuh) in the batch's
+                                       // phase array; 0 phases: the shared-memory program
 };
 struct BatchItem {
     uint32_t circuit, pass, tile;
@@ -184,8 +196,10 @@ struct BatchItem {
 // zeroed counter per pass of the batch.  budget: SM cycles a wait may take.
 size_t batch_smem_bytes();
 cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, const TileOp *ops,
-                         const BatchItem *items, uint64_t nitems, uint32_t *counters, uint32_t *done,
-                         uint32_t *err, long long budget, int sm_count, cudaStream_t s);
+                         const TilePhase *phases, const BatchItem *items, uint64_t nitems, uint32_t *counters,
+                         uint32_t *done, uint32_t *err, long long budget, int sm_count, cudaStream_t s);
+// register bits of the batch's 12-bit tiles (the register phases' shape)
+constexpr int kBatchRB = 12 - 5 - kRegWarpBits;
 
 // Reductions (FP64 accumulation).  scratch: device buffer of at least
 // reduce_scratch_bytes(n) bytes.

@@ -461,7 +461,7 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
         }
         pp.op_begin = (int)plan.ops.size();
         pp.phase_begin = (int)plan.phases.size();
-        if (RB > 0 && L + hcount == RB + 8 && L >= 5) {
+        if (RB > 0 && L + hcount == RB + 5 + kRegWarpBits && L >= 5) {
             build_phases(pass_ops, L + hcount, RB, plan.ops, plan.phases);
         } else {
             plan.ops.insert(plan.ops.end(), pass_ops.begin(), pass_ops.end());

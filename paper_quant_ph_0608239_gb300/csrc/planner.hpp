@@ -58,7 +58,7 @@ struct Plan {
 // Gates are taken in order; a gate can join the current pass if it commutes
 // with every gate skipped so far (no shared qubit) and its targets fit in the
 // tile's bit set (diagonal gates need no target in the tile).
-// RB > 0: cut each pass with T = RB + 8 bits into register phases for the
+// RB > 0: cut each pass with T = RB + 5 + kRegWarpBits bits into register phases for the
 // register-blocked kernel (k_tile2.cu); passes that do not fit that shape
 // keep a flat op list for the shared-memory kernel (k_tile.cu).
 void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB = 0);

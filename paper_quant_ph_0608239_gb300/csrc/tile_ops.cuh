@@ -13,6 +13,17 @@ __device__ __forceinline__ uint32_t ins0(uint32_t i, int pos) {
     return ((i >> pos) << (pos + 1)) | (i & ((1u << pos) - 1u));
 }
 
+// Index of the p-th element whose bits at the positions in `fixed` are zero.
+// Ops enumerate only the amplitudes their local controls select (control
+// bits fixed at 1): a gate with c controls costs 2^-c of a sweep.
+__device__ __forceinline__ uint32_t expand_fixed(uint32_t p, uint32_t fixed) {
+    while (fixed) {
+        p = ins0(p, __ffs(fixed) - 1);
+        fixed &= fixed - 1u;
+    }
+    return p;
+}
+
 template <typename R>
 __device__ __forceinline__ void op_pairs(amp_t<R> *t, int T, const TileOp &op) {
     const int tl = op.tl;
@@ -22,9 +33,9 @@ __device__ __forceinline__ void op_pairs(amp_t<R> *t, int T, const TileOp &op) {
 #pragma unroll
     for (int k = 0; k < 4; k++) u[k] = mk<R>((R)op.u[2 * k], (R)op.u[2 * k + 1]);
     const int kind = op.kind;
-    for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
-        const uint32_t i0 = ins0(p, tl);
-        if ((i0 & lc) != lc) continue;
+    const uint32_t npair = half >> __popc(lc), fixed = bt | lc;
+    for (uint32_t p = threadIdx.x; p < npair; p += blockDim.x) {
+        const uint32_t i0 = lc ? expand_fixed(p, fixed) | lc : ins0(p, tl);
         const uint32_t i1 = i0 | bt;
         amp_t<R> x = t[i0], y = t[i1];
         if (kind == TOP_GENERAL) {
@@ -46,24 +57,24 @@ __device__ __forceinline__ void op_diag(amp_t<R> *t, int T, const TileOp &op, ui
     const amp_t<R> u0 = mk<R>((R)op.u[0], (R)op.u[1]);
     const amp_t<R> u1 = mk<R>((R)op.u[6], (R)op.u[7]);
     const uint32_t TS = 1u << T;
+    const uint32_t cnt = TS >> __popc(lc);  // amplitudes the controls select
     if (op.kind == TOP_PHASE) {
         const int tl = op.tl;
-        const uint32_t bt = 1u << tl;
-        for (uint32_t p = threadIdx.x; p < (TS >> 1); p += blockDim.x) {
-            const uint32_t i = ins0(p, tl) | bt;
-            if ((i & lc) != lc) continue;
+        const uint32_t bt = 1u << tl, fixed = bt | lc;
+        for (uint32_t p = threadIdx.x; p < (cnt >> 1); p += blockDim.x) {
+            const uint32_t i = (lc ? expand_fixed(p, fixed) | lc : ins0(p, tl)) | bt;
             t[i] = cmul<R>(u1, t[i]);
         }
     } else if (op.kind == TOP_DIAG) {
         const int tl = op.tl;
-        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
-            if ((i & lc) != lc) continue;
+        for (uint32_t p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t i = lc ? expand_fixed(p, lc) | lc : p;
             t[i] = cmul<R>(((i >> tl) & 1u) ? u1 : u0, t[i]);
         }
     } else {  // TOP_DIAG_G: the target bit lies outside the tile
         const amp_t<R> f = ((base >> op.tl) & 1ull) ? u1 : u0;
-        for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
-            if ((i & lc) != lc) continue;
+        for (uint32_t p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const uint32_t i = lc ? expand_fixed(p, lc) | lc : p;
             t[i] = cmul<R>(f, t[i]);
         }
     }

@@ -44,9 +44,9 @@ def layout_table_steps(name):
     return steps, body
 
 
-def shor_table():
+def shor_table(name="shortab_L24.txt"):
     d = {}
-    for tok in _lines("shortab_L24.txt"):
+    for tok in _lines(name):
         if tok[0] == "Q":
             d["Q"] = [float(v) for v in tok[1:]]
         else:

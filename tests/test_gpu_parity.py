@@ -181,7 +181,7 @@ def test_tiny_registers(q, dt, n):
 @pytest.mark.parametrize("dt", DTYPES)
 def test_long_pass_many_ops(q, dt):
     # one tile holds the whole 10-qubit register, so all 300 gates land in one
-    # pass: several staging chunks of ops, groups with renamings, SWAP gates
+    # pass: several staging chunks of ops, controls, SWAP gates
     n = 10
     rng = np.random.default_rng(77)
     kinds = ["H", "R", "SU2", "NOT", "V", "X", "YB"]
@@ -202,6 +202,34 @@ def test_long_pass_many_ops(q, dt):
     assert plan.stats()["passes"] == 1
     plan.run()
     assert err(st.get_state(), ref) < TOL[dt] * 4
+    plan.free()
+    st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_autotuned_plan(q, dt):
+    # QSIM_MODE_AUTO: each of the first runs uses another candidate (tile size,
+    # fusion width); every run applies the whole circuit, so every run must
+    # match the oracle, and afterwards the fastest candidate is in use
+    n = 18
+    gates = inputs.random_circuit(n, 8, seed=91)
+    x0 = inputs.random_basis(n, seed=91)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, dt)
+    plan = st.plan(gates, mode=q.MODE_AUTO)
+    s0 = plan.stats()
+    assert s0["candidates"] >= 2 and s0["chosen"] == -1
+    tol = TOL[dt] * (1 if dt == "c128" else 2)  # fused 3xTF32 blocks round a little more
+    for _ in range(s0["candidates"] + 1):
+        st.set_basis(x0)
+        plan.run()
+        assert err(st.get_state(), ref) < tol
+    s1 = plan.stats()
+    assert 0 <= s1["chosen"] < s1["candidates"]
+    ms = [c["ms"] for c in s1["autotune"]]
+    assert all(m > 0 for m in ms) and ms[s1["chosen"]] == min(ms)
+    if dt == "c64":
+        assert any(c["fuse_k"] for c in s1["autotune"])  # tensor-core widths are candidates
     plan.free()
     st.free()
 
@@ -425,7 +453,7 @@ def test_reductions(q, dt, n):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("n", [3, 8, 14])
+@pytest.mark.parametrize("n", [1, 3, 8, 14])
 def test_sampling_matches_oracle(q, dt, n):
     psi = rand_state(n, 30 + n) * (1.0 + np.arange(1 << n) / (1 << n))  # uneven weights
     psi /= np.linalg.norm(psi)
@@ -442,6 +470,58 @@ def test_sampling_matches_oracle(q, dt, n):
     assert np.all((got == ref) | near)
     assert np.mean(got == ref) > 0.99
     st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_sampling_distribution_chi2(q, dt):
+    # the sampled histogram against the oracle's probabilities (Pearson chi^2
+    # over cells with at least 5 expected counts; fixed seeds, so the outcome
+    # is deterministic)
+    scipy_stats = pytest.importorskip("scipy.stats")
+    n, S = 10, 200000
+    psi = rand_state(n, 61) * (1.0 + 3.0 * np.arange(1 << n) / (1 << n))
+    psi /= np.linalg.norm(psi)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    got = st.sample(np.random.default_rng(62).random(S))
+    st.free()
+    p = oracle.probs(psi, n)
+    counts = np.bincount(got, minlength=1 << n)
+    exp = S * p / p.sum()
+    keep = exp >= 5
+    chi2 = float(np.sum((counts[keep] - exp[keep]) ** 2 / exp[keep]))
+    dof = int(keep.sum()) - 1
+    assert scipy_stats.chi2.sf(chi2, dof) > 1e-4, (chi2, dof)
+    assert counts[~keep].sum() <= max(20, 3 * exp[~keep].sum())
+
+
+# ------------------------------------- complex64: relative error and fidelity
+def rel_and_fidelity(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    rel = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    fid = float(abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real))
+    return rel, fid
+
+
+@pytest.mark.parametrize("n,depth,seed", [(20, 20, 7), (24, 20, 4)])
+def test_c64_relative_error_and_fidelity(q, n, depth, seed):
+    # At n qubits a random state's amplitudes are ~2^(-n/2), so the absolute
+    # 2e-5 bound says little; the relative error max|da| / max|a_ref| and the
+    # fidelity |<ref|got>|^2 are checked as well.  (24, 20, 4) is the 34-qubit
+    # configuration's generator (depth 20, seed 4) at 24 qubits, where the
+    # oracle still runs.  Bound: FP32 rounds each amplitude by <= 2^-23
+    # relative per gate; over G gates the error walks as ~2^-23 sqrt(G) times a
+    # few roundings per update (G = 600-720: ~1e-5); 1e-4 leaves a margin and
+    # still fails any wrong gate.
+    gates = inputs.random_circuit(n, depth, seed=seed)
+    x0 = inputs.random_basis(n, seed=seed)
+    ref = oracle.run(n, gates, x0=x0)
+    got = run_gpu(q, n, "c64", gates, x0=x0)
+    assert err(got, ref) < TOL["c64"]
+    rel, fid = rel_and_fidelity(got, ref)
+    print("n=%d gates=%d  max-abs %.3g  relative %.3g  1-fidelity %.3g" % (n, len(gates), err(got, ref), rel, 1 - fid))
+    assert rel < 1e-4, rel
+    assert 1 - fid < 1e-8, fid
 
 
 # ------------------------------------------------------------- edge cases
@@ -558,4 +638,34 @@ def test_shor_table_L24_on_gpu(q, dt):
     np.testing.assert_allclose(qp[:X], t["Q"], atol=5e-4 + 1e-12)
     ref = oracle.qubit_probs(oracle.run(L, inputs.qft(range(X), swaps=True), state=a.copy()), L)
     np.testing.assert_allclose(qp, ref, atol=1e-12 if dt == "c128" else 1e-5)
+    # the device-written Eq. Shor2 state equals the host-built one exactly
+    st.set_shor_state(X, y, G)
+    assert np.array_equal(st.get_state(), a.astype(st.get_state().dtype))
+    st.free()
+
+
+# ------------------------------------------------ Shor, Table Shortab (L = 33)
+@pytest.mark.parametrize("name,dt", [("shortab_L33_G1961.txt", "c64"), ("shortab_L33_G2047.txt", "c64"),
+                                     ("shortab_L33_G2047.txt", "c128")])
+def test_shor_table_L33_on_gpu(q, name, dt):
+    # 33 qubits: 64 GiB (complex64) / 128 GiB (complex128), beyond the
+    # oracle's host memory; checked against the paper's column and against
+    # the closed form of the QFT'd Eq. Shor2 state
+    import golden_io
+    from test_oracle_pins import shor_closed_form_Q
+    t = golden_io.shor_table(name)
+    X, L, G, y, r = t["X"], t["L"], t["G"], t["y"], t["r"]
+    st = q.State(L, dt)
+    st.set_shor_state(X, y, G)
+    st.run(inputs.qft(range(X), swaps=True))
+    qp = st.qubit_probs()
+    st.free()
+    np.testing.assert_allclose(qp[:X], t["Q"], atol=5e-4 + 1e-9)
+    Q, _ = shor_closed_form_Q(X, r)
+    np.testing.assert_allclose(qp[:X], Q, atol=1e-10 if dt == "c128" else 5e-5)
+    # the f-register: y^x mod G over a whole number of periods and a remainder,
+    # <Q_i> for i >= X follow from the values f(x) directly
+    f = inputs.shor_initial_support(X, G, y)
+    fb = np.array([np.mean((f >> (i - X)) & 1) for i in range(X, L)])
+    np.testing.assert_allclose(qp[X:], fb, atol=1e-10 if dt == "c128" else 5e-5)
     st.free()
