@@ -58,7 +58,7 @@ struct TileOp {
     int8_t regk;      // register slot of the target bit; -1 if it is a lane/warp bit (or outside the tile)
     int8_t pk;        // pair kind: 0 general, 1 real, 2 anti-diagonal, 3 exchange
     uint8_t code;     // register kernel dispatch: family * 8 + slot (RC_* below)
-    int8_t cslot;     // RC_EXCH1: the register slot of the single control
+    int8_t cslot;     // unused (0)
     uint32_t creg;    // controls among the register slots (bit k = slot k)
     uint32_t lcthr;   // controls among the lane and warp bits (local index mask)
     uint32_t pad32;
@@ -79,7 +79,6 @@ enum RegFamily : int {
     RC_EXCHC = 5,   // bit flip with controls
     RC_PHASE = 6,   // diag(1, u11) on a register bit, any controls
     RC_DIAG = 7,    // diag(u00, u11) on a register bit, any controls
-    RC_EXCH1 = 8,   // bit flip controlled by exactly one register bit (cslot): a register renaming
     RC_LANE = 9,    // pair op on a lane bit (tl), no local controls; k = pair kind
     RC_LANEC = 10,  // pair op on a lane bit with controls; k = pair kind
     RC_THR = 11,    // phase (k = 0) or diagonal (k = 1) on a lane/warp bit (tl)

@@ -348,7 +348,7 @@ void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vecto
             for (int k = 0; k < nr; k++)
                 if ((op.lcmask >> ph.rb[k]) & 1u) op.creg |= 1u << k;
             op.lcthr = op.lcmask & ~rset;
-            op.cslot = -1;
+            op.cslot = 0;
             const bool noctl = op.lcmask == 0;
             int fam, k = op.regk;
             if (op.kind == TOP_DIAG_G) {
@@ -369,9 +369,6 @@ void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vecto
                 fam = noctl ? RC_REAL : RC_REALC;
             } else if (op.pk == 2) {
                 fam = RC_ANTI;
-            } else if (op.lcthr == 0 && __builtin_popcount(op.creg) == 1) {
-                fam = RC_EXCH1;
-                op.cslot = (int8_t)__builtin_ctz(op.creg);
             } else {
                 fam = RC_EXCHC;
             }

@@ -165,30 +165,6 @@ __device__ __forceinline__ void diag_reg(float2 (&v)[1 << RB], float2 u0, float2
     }
 }
 
-// bit flip on register slot K where register slot C is 1: a renaming of
-// registers, no arithmetic
-template <int RB, int K, int C>
-__device__ __forceinline__ void exch1(float2 (&v)[1 << RB]) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); j++) {
-        if (!((j >> C) & 1) || ((j >> K) & 1)) continue;
-        const float2 t = v[j];
-        v[j] = v[j | (1 << K)];
-        v[j | (1 << K)] = t;
-    }
-}
-
-template <int RB, int K>
-__device__ __forceinline__ void exch1_c(int c, float2 (&v)[1 << RB]) {
-    switch (c) {
-    case 0: if constexpr (K != 0) exch1<RB, K, 0>(v); break;
-    case 1: if constexpr (K != 1) exch1<RB, K, 1>(v); break;
-    case 2: if constexpr (K != 2) exch1<RB, K, 2>(v); break;
-    case 3: if constexpr (K != 3) exch1<RB, K, 3>(v); break;
-    default: if constexpr (RB > 4 && K != 4) exch1<RB, K, (RB > 4 ? 4 : 0)>(v); break;
-    }
-}
-
 // One op of a phase.  op.code = family * 8 + k selects a code path whose
 // register indices are compile-time constants.
 template <int RB>
@@ -216,7 +192,6 @@ __device__ __forceinline__ void apply_rop(const TileOp &op, float2 (&v)[1 << RB]
         QSIM_K_CASES(RC_EXCHC, (pair_reg<RB, K, PK_EXCH, true>(v, u, thr_ok, creg)))
         QSIM_K_CASES(RC_PHASE, (phase_reg<RB, K>(v, u[3], thr_ok, creg)))
         QSIM_K_CASES(RC_DIAG, (diag_reg<RB, K>(v, u[0], u[3], thr_ok, creg)))
-        QSIM_K_CASES(RC_EXCH1, (exch1_c<RB, K>(op.cslot, v)))
 #undef QSIM_K_CASES
     case RC_LANE * 8 + PK_GENERAL: pair_lane<RB, PK_GENERAL, false>(op.tl, v, u, true, 0u, lane); break;
     case RC_LANE * 8 + PK_REAL: pair_lane<RB, PK_REAL, false>(op.tl, v, u, true, 0u, lane); break;
