@@ -266,7 +266,9 @@ def run_ours(args, w, ws, rank, local):
     st = q.State(n, w["dtype"])
     # the plan picks its tile size / fusion width by timing its candidates
     # (QSIM_MODE_AUTO); --fuse-k pins a fusion width instead
-    if args.fuse_k or args.tile_bits:
+    if args.pergate:  # one sweep of the state per gate (Sec. III.A)
+        plan = st.plan(gates, mode=q.MODE_PERGATE)
+    elif args.fuse_k or args.tile_bits:
         plan = st.plan(gates, fuse_k=args.fuse_k, tile_bits=args.tile_bits)
     else:
         plan = st.plan(gates, mode=q.MODE_AUTO)
@@ -310,9 +312,10 @@ def run_ours(args, w, ws, rank, local):
     arr = q.gate_array(gates)
     e2e_T = 0 if pst["fuse_k"] else pst["tile_bits"]
     e2e_k = pst["fuse_k"]
+    e2e_mode = q.MODE_PERGATE if args.pergate else q.MODE_FUSED
     for _ in range(1):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr, tile_bits=e2e_T, fuse_k=e2e_k)
+        st.run(None, gate_arr=arr, mode=e2e_mode, tile_bits=e2e_T, fuse_k=e2e_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     c2 = st.counters()
@@ -320,7 +323,7 @@ def run_ours(args, w, ws, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         st.set_basis(x0)
-        st.run(None, gate_arr=arr, tile_bits=e2e_T, fuse_k=e2e_k)
+        st.run(None, gate_arr=arr, mode=e2e_mode, tile_bits=e2e_T, fuse_k=e2e_k)
         st.qubit_probs()
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
@@ -366,7 +369,8 @@ def run_ours(args, w, ws, rank, local):
         "dtype": "f64" if w["dtype"] == "c128" else "f32",
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
-                   "path": ("planner (fused %d-qubit blocks on the tensor cores)" % pst["fuse_k"] if pst["fuse_k"]
+                   "path": ("one sweep per gate" if args.pergate else
+                            "planner (fused %d-qubit blocks on the tensor cores)" % pst["fuse_k"] if pst["fuse_k"]
                             else "planner (tile passes)"), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
                    "autotune": [dict(c, chosen=(i == pst["chosen"])) for i, c in enumerate(pst["autotune"])],
                    "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
@@ -501,6 +505,8 @@ def run_batch_workload(args, w, ws, rank, local):
     import paper_quant_ph_0608239_gb300 as q
     torch.cuda.set_device(local)
     circs = inputs.batch_circuits()
+    if args.batch_count:
+        circs = circs[:args.batch_count]
     ng = sum(len(g) for _, g in circs)
     states = [q.State(n, "c64") for n, _ in circs]
     x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
@@ -639,6 +645,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-companions", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the qubit count (smaller cases for profiling)")
+    ap.add_argument("--pergate", action="store_true", help="one sweep of the state per gate (no tile passes)")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's precision")
+    ap.add_argument("--batch-count", type=int, default=0, help="batch workload: only the first N circuits")
     ap.add_argument("--tile-bits", type=int, default=0,
                     help="pin the tile size T of the tile passes (default: autotuned)")
     ap.add_argument("--fuse-k", type=int, default=0,
@@ -652,6 +661,15 @@ def main():
         w["n"] = args.n
         w["text"] = w["text"].replace("%d qubits" % WORKLOADS[args.workload]["n"], "%d qubits" % args.n)
         args.workload = args.workload + "_n%d" % args.n
+    if args.dtype and args.dtype != w["dtype"] and w["kind"] != "batch":
+        w["dtype"] = args.dtype
+        w["text"] = w["text"].replace("complex128", args.dtype).replace("complex64", args.dtype)
+        args.workload = args.workload + "_" + args.dtype
+    if args.pergate:
+        args.workload = args.workload + "_pergate"
+    if args.batch_count and w["kind"] == "batch":
+        w["text"] = w["text"].replace("batch of 512", "batch of the first %d of 512" % args.batch_count)
+        args.workload = args.workload + "_first%d" % args.batch_count
     if args.fuse_k:
         args.workload = args.workload + "_fused%d" % args.fuse_k
     if args.tile_bits:
