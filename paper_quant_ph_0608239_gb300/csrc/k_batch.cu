@@ -28,6 +28,10 @@ namespace {
 
 constexpr int kThreadsB = 256;
 constexpr int kMaxHB = 10;
+constexpr int kMaxTB = 12;                            // tiles of at most 2^12 amplitudes
+constexpr int kLoadIt = (1 << kMaxTB) / kThreadsB;    // amplitudes a thread loads per tile
+constexpr int kStageOpsB = 64;                        // ops of one pass staged in shared memory (12 KiB)
+constexpr int kStagePhB = 32;                         // phases of one pass staged (1.4 KiB)
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
@@ -47,8 +51,14 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *t = reinterpret_cast<float2 *>(smem_raw);
     __shared__ uint64_t runoff[1 << kMaxHB];
+    __shared__ __align__(16) TileOp s_ops[kStageOpsB];
+    __shared__ TilePhase s_ph[kStagePhB];
     __shared__ uint64_t sh_item;
     __shared__ int sh_abort;
+    // The pass whose run offsets, ops and phases are in shared memory: items
+    // of one pass follow one another, so a block mostly reuses them.  Every
+    // thread tracks the same value.
+    uint32_t staged_pass = 0xffffffffu;
     for (;;) {
         if (threadIdx.x == 0) {
             sh_item = atomicAdd(reinterpret_cast<unsigned long long *>(counters), 1ull);
@@ -81,11 +91,31 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
         const TileGeom &g = ps.geom;
         const int L = g.L, H = g.H, T = L + H;
         const uint32_t TS = 1u << T, lowmask = (1u << L) - 1u;
-        for (uint32_t j = threadIdx.x; j < (1u << H); j += blockDim.x) {
-            uint64_t o = 0;
-            for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
-            runoff[j] = o;
+        const uint32_t pass_id = (uint32_t)(c.pass_begin + item.pass);
+        const bool ops_staged = ps.op_count <= kStageOpsB, ph_staged = ps.phase_count <= kStagePhB;
+        if (pass_id != staged_pass) {
+            // (the previous item ended with a barrier: nobody reads the old copies)
+            for (uint32_t j = threadIdx.x; j < (1u << H); j += blockDim.x) {
+                uint64_t o = 0;
+                for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
+                runoff[j] = o;
+            }
+            if (ops_staged) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(ops + ps.op_begin);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(s_ops);
+                for (uint32_t w = threadIdx.x; w < (uint32_t)ps.op_count * (sizeof(TileOp) / 4); w += blockDim.x)
+                    dst[w] = src[w];
+            }
+            if (ph_staged) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(phases + ps.phase_begin);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(s_ph);
+                for (uint32_t w = threadIdx.x; w < (uint32_t)ps.phase_count * (sizeof(TilePhase) / 4); w += blockDim.x)
+                    dst[w] = src[w];
+            }
+            staged_pass = pass_id;
         }
+        // ops indexed by their position in the batch's op array
+        const TileOp *ops_p = ops_staged ? s_ops - ps.op_begin : ops;
         uint64_t base = (uint64_t)item.tile << L;
         for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
         __syncthreads();
@@ -95,18 +125,30 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
                 const uint64_t gi = base | runoff[i >> L] | (i & lowmask);
                 t[i] = make_float2(gi == c.x0 ? 1.0f : 0.0f, 0.0f);
             }
-        } else {  // written by other CTAs: read through L2
-            for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x)
-                t[i] = __ldcg(a + (base | runoff[i >> L] | (i & lowmask)));
+        } else {  // written by other CTAs: read through L2, four loads of a thread in flight at once
+            for (int k0 = 0; k0 < kLoadIt; k0 += 4) {
+                float2 buf[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t i = threadIdx.x + (uint32_t)(k0 + k) * kThreadsB;
+                    if (i < TS) buf[k] = __ldcg(a + (base | runoff[i >> L] | (i & lowmask)));
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t i = threadIdx.x + (uint32_t)(k0 + k) * kThreadsB;
+                    if (i < TS) t[i] = buf[k];
+                }
+            }
         }
         __syncthreads();
         if (ps.phase_count > 0) {
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            for (int p = ps.phase_begin; p < ps.phase_begin + ps.phase_count; p++)
-                t2::run_phase<false, kBatchRB>(t, phases[p], ops, base, lane, warp, 1, 1);
+            for (int p = 0; p < ps.phase_count; p++)
+                t2::run_phase<false, kBatchRB>(t, ph_staged ? s_ph[p] : phases[ps.phase_begin + p], ops_p, base, lane,
+                                               warp, 1, 1);
         } else {
             for (int o = ps.op_begin; o < ps.op_begin + ps.op_count; o++) {
-                tile_apply_op<float>(t, T, ops[o], base, nullptr);
+                tile_apply_op<float>(t, T, ops_p[o], base, nullptr);
                 __syncthreads();
             }
         }
@@ -125,8 +167,12 @@ cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, con
                          const TilePhase *phases, const BatchItem *items, uint64_t nitems, uint32_t *counters,
                          uint32_t *done, uint32_t *err, long long budget, int sm_count, cudaStream_t s) {
     const size_t smem = batch_smem_bytes();
+    // the staged programs sit in static shared memory, so the tile needs the
+    // opt-in beyond the default 48 KiB per block
+    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreadsB, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreadsB, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     unsigned grid = (unsigned)(sm_count * per_sm);

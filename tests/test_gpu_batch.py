@@ -38,6 +38,35 @@ def test_batch_matches_oracle(q):
         st.free()
 
 
+def test_batch_long_passes_with_controls_and_swaps(q):
+    # one 12-qubit tile per circuit, so every gate lands in one pass: more ops
+    # and phases than a block keeps in shared memory (read from global memory
+    # instead), controlled gates and SWAP gates; plus a 14-qubit circuit that
+    # needs several passes of the same shape
+    from inputs import Gate
+    rng = np.random.default_rng(11)
+    kinds = ["H", "R", "SU2", "NOT", "V", "X", "YB"]
+    params = {"R": (0.7,), "V": (0.785398,), "SU2": (0.5, -0.1, 0.7, (1 - 0.25 - 0.01 - 0.49) ** 0.5)}
+    circs = []
+    for n in (12, 12, 14):
+        gl = []
+        for i in range(220):
+            qs = [int(x) for x in rng.permutation(n)]
+            if i % 29 == 0:
+                gl.append(Gate("SWAP", (qs[0], qs[1]), tuple(qs[2:2 + int(rng.integers(0, 2))]), ()))
+                continue
+            k = kinds[int(rng.integers(len(kinds)))]
+            gl.append(Gate(k, (qs[0],), tuple(qs[1:1 + int(rng.integers(0, 3))]), params.get(k, ())))
+        circs.append((n, gl))
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=40 + i) for i, (n, _) in enumerate(circs)]
+    q.run_batch(states, x0s, [g for _, g in circs])
+    for st, x0, (n, gl) in zip(states, x0s, circs):
+        ref = oracle.run(n, gl, x0=x0)
+        assert _err(st.get_state(), ref) < 4e-5, n
+        st.free()
+
+
 def test_batch_graph_replay_is_repeatable(q):
     circs = inputs.batch_circuits(count=12, seed0=900, nmin=12, nmax=19, dmin=4, dmax=10)
     states = [q.State(n, "c64") for n, _ in circs]
