@@ -963,7 +963,7 @@ qsim_status qsim_swap_qubits(qsim_handle h, int K, const int *a, const int *b) {
     CHECK_HANDLE(h);
     qsim_status st = check_pairs(h, K, a, b);
     if (st != QSIM_OK) return st;
-    int l[8], hb[8];
+    int l[8] = {0}, hb[8] = {0};  // K <= 8 (check_pairs)
     for (int i = 0; i < K; i++) {
         l[i] = h->phys[a[i]];
         hb[i] = h->phys[b[i]];

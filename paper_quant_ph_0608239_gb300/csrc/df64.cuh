@@ -174,7 +174,9 @@ DF_HD df df_mul(df a, df b) {
 template <int N>
 DF_HD df df_dot(const df (&a)[N], const df (&b)[N]) {
     float s = 0.0f, err = 0.0f;
+#if defined(__CUDACC__)
 #pragma unroll
+#endif
     for (int k = 0; k < N; k++) {
         const float p = a[k].h * b[k].h;
         float e = df_fma(a[k].h, b[k].h, -p);

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
 
 }  // namespace
 
-size_t batch_smem_bytes() { return (size_t)8 << 12; }
+static size_t batch_smem_bytes() { return (size_t)8 << kMaxTB; }
 
 cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, const TileOp *ops,
                          const TilePhase *phases, const BatchItem *items, uint64_t nitems, uint32_t *counters,

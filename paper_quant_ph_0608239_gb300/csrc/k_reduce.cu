@@ -403,7 +403,6 @@ double *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
 
 }  // namespace
 
-size_t noalloc_scratch_bytes() { return kNoAllocDoubles * sizeof(double); }
 
 cudaError_t launch_bit_probs_noalloc(const void *amp, int dt, int n, double *dout, cudaStream_t s) {
     int dev = 0;

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(amp_t<R> *__restrict__ a,
 
 }  // namespace
 
-size_t tile_smem_bytes(int dt, int T) { return (size_t)(dt == 0 ? 8 : 16) << T; }
+static size_t tile_smem_bytes(int dt, int T) { return (size_t)(dt == 0 ? 8 : 16) << T; }
 
 cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp *ops, int nops, const void *dmat,
                              uint32_t *err, int sm_count, cudaStream_t s) {

@@ -79,6 +79,7 @@ enum RegFamily : int {
     RC_EXCHC = 5,   // bit flip with controls
     RC_PHASE = 6,   // diag(1, u11) on a register bit, any controls
     RC_DIAG = 7,    // diag(u00, u11) on a register bit, any controls
+                    // (8: unused)
     RC_LANE = 9,    // pair op on a lane bit (tl), no local controls; k = pair kind
     RC_LANEC = 10,  // pair op on a lane bit with controls; k = pair kind
     RC_THR = 11,    // phase (k = 0) or diagonal (k = 1) on a lane/warp bit (tl)
@@ -151,10 +152,10 @@ cudaError_t launch_dense(void *amp, int dt, int n, int k, const int *qpos, const
 // err: device word set on a bounded-wait timeout.
 cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp *ops, int nops,
                              const void *dmat, uint32_t *err, int sm_count, cudaStream_t s);
-size_t tile_smem_bytes(int dt, int T);
 
-// Register-blocked tile pass (k_tile2.cu), complex64: T = 8 + register
-// bits = 12 or 13, L >= 5 (the lane bits are the physical bits 0..4).
+// Register-blocked tile pass (k_tile2.cu), complex64: T = 5 lane bits +
+// kRegWarpBits warp bits + register bits = 12 or 13, L >= 5 (the lane bits
+// are the physical bits 0..4).
 bool tile2_supported(int dt, int T);
 
 // complex128 tile pass in double-float arithmetic (k_tile_df.cu); convert =
@@ -193,7 +194,6 @@ struct BatchItem {
 };
 // counters: one 64-bit item counter (zeroed before the launch); done: one
 // zeroed counter per pass of the batch.  budget: SM cycles a wait may take.
-size_t batch_smem_bytes();
 cudaError_t launch_batch(const BatchCircuit *circs, const BatchPass *passes, const TileOp *ops,
                          const TilePhase *phases, const BatchItem *items, uint64_t nitems, uint32_t *counters,
                          uint32_t *done, uint32_t *err, long long budget, int sm_count, cudaStream_t s);
@@ -216,7 +216,6 @@ cudaError_t launch_gather_chunk(const void *amp, int dt, int n, const int *physp
 
 // Per-bit marginals on the library's static scratch array instead of a
 // caller buffer (no device allocation); see k_reduce.cu.
-size_t noalloc_scratch_bytes();
 cudaError_t launch_bit_probs_noalloc(const void *amp, int dt, int n, double *dout, cudaStream_t s);
 
 // Sampling (Sec. V.B): block sums of |a|^2 in logical order, then per-sample
