@@ -336,6 +336,8 @@ def run_ours(args, w, ws, rank, local):
     gbs = by / nl / per_launch_s / 1e9
     tflops = fl / nl / per_launch_s / 1e12
     alu_peak = DF64_PEAK_TFLOPS if w["dtype"] == "c128" else FP32_PEAK_TFLOPS
+    if fam == "dense_cuda_core" and w["dtype"] == "c128":
+        alu_peak = FP64_PEAK_TFLOPS  # dense blocks compute in FP64
     frac_hbm, frac_alu = gbs / hbm_peak, tflops / alu_peak
     traffic = ncu_traffic(fam, args.workload)
     hbm_roof = {"bound": "hbm", "kernel": fam, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -343,7 +345,8 @@ def run_ours(args, w, ws, rank, local):
                 "alg_bytes_per_launch": by / nl, "launches": nl, "avg_launch_ms": ms / nl}
     alu_roof = {"bound": "alu", "kernel": fam, "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": frac_alu, "traffic": traffic,
-                "peak_source": ("double-float on the FP32 pipes: 152 SM x 128 lanes x 2.07 GHz / 6.2 FP32 "
+                "peak_source": ("nominal FP64: 1.25 TFLOP/s" if alu_peak == FP64_PEAK_TFLOPS else
+                                "double-float on the FP32 pipes: 152 SM x 128 lanes x 2.07 GHz / 6.2 FP32 "
                                 "instructions per emulated FP64 flop" if w["dtype"] == "c128"
                                 else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
                 "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
@@ -370,7 +373,9 @@ def run_ours(args, w, ws, rank, local):
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
                    "path": ("one sweep per gate" if args.pergate else
-                            "planner (fused %d-qubit blocks on the tensor cores)" % pst["fuse_k"] if pst["fuse_k"]
+                            "planner (fused %d-qubit blocks on the %s)" % (
+                                pst["fuse_k"], "tensor cores" if w["dtype"] == "c64" and pst["fuse_k"] in (4, 5)
+                                else "CUDA cores") if pst["fuse_k"]
                             else "planner (tile passes)"), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
                    "autotune": [dict(c, chosen=(i == pst["chosen"])) for i, c in enumerate(pst["autotune"])],
                    "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
@@ -494,6 +499,19 @@ def companions(q, w, gates, x0, args):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     res["pergate_fp64_c128_sample"] = {"gates_per_s": len(sub) / el, "sample": "first %d gates" % len(sub)}
+    # the same gates fused into dense 5-qubit blocks applied in FP64 on the
+    # CUDA cores (GB300's FP64 rate is ~1/58 of FP32: slow by design), first layer
+    sub1 = gates[: n + n // 2] if w["kind"] == "random" else gates[:32]
+    plan = st.plan(sub1, fuse_k=5)
+    plan.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.run()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    res["fused_fp64_k5_c128_sample"] = {"gates_per_s": len(sub1) / el, "blocks": plan.stats()["passes"],
+                                        "sample": "first %d gates" % len(sub1)}
+    plan.free()
     st.free()
     torch.cuda.empty_cache()
     return res

@@ -104,7 +104,10 @@ enum {
 typedef struct {
     int32_t mode;       /* QSIM_MODE_* */
     int32_t tile_bits;  /* T, qubits held per shared-memory tile; 0 = default */
-    int32_t fuse_k;     /* width of dense fused blocks; 0 = planner default, -1 = never */
+    int32_t fuse_k;     /* > 0: apply the circuit as dense blocks of at most fuse_k qubits
+                           (1..6), each the FP64 product of its gates: complex64 with
+                           k = 4 or 5 on the tensor cores (3xTF32), other widths and
+                           complex128 (in FP64) on the CUDA cores.  0 or -1: tile passes */
     int32_t max_swap;   /* most bit pairs exchanged per interchange pass; 0 = default */
     int32_t wait_budget_us; /* batches: longest device-side wait between passes
                                before QSIM_ETIMEOUT; 0 = about 2 s */

@@ -475,6 +475,12 @@ struct qsim_plan_s {
     std::vector<FusedBlock> blocks;  // FUSED mode with fuse_k: dense blocks on the tensor cores
     std::vector<float> bmats;        // their B operands, 2 (2^(k+1))^2 floats each
     float *d_bmats = nullptr;
+    // dense blocks the tensor-core kernel does not take (complex128, k = 6, ...)
+    // run on the CUDA cores (k_dense): their matrices in the state's precision
+    bool cuda_core = false;
+    std::vector<unsigned char> cmats;
+    size_t cmat_stride = 0;
+    void *d_cmats = nullptr;
     qsim_plan_stats stats{};
     // QSIM_MODE_AUTO: one candidate plan per tile size / fusion width; the
     // first runs time each candidate, later runs use the fastest
@@ -514,9 +520,33 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         return QSIM_OK;
     }
+    if (o.fuse_k > 0 && !fused_tc_supported((int)h->dt, o.fuse_k, h->n)) {
+        // dense blocks on the CUDA cores (complex128, k = 1..6, small registers)
+        if (o.fuse_k > 6 || o.fuse_k > h->n) return fail(QSIM_EUNSUPPORTED, "fused blocks need k <= min(6, n)");
+        plan_fused(pg, h->n, o.fuse_k, P.blocks);
+        const size_t ent = (size_t)1 << (2 * o.fuse_k);
+        P.cuda_core = true;
+        P.cmat_stride = ent * amp_bytes(h->dt);
+        P.cmats.resize(P.cmat_stride * P.blocks.size());
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            const std::vector<double> &U = P.blocks[b].U;
+            unsigned char *dst = P.cmats.data() + P.cmat_stride * b;
+            if (h->dt == QSIM_C64) {
+                for (size_t i = 0; i < 2 * ent; i++) {
+                    const float f = (float)U[i];
+                    std::memcpy(dst + 4 * i, &f, 4);
+                }
+            } else {
+                std::memcpy(dst, U.data(), 16 * ent);
+            }
+            P.stats.alg_flops += P.blocks[b].flops;
+        }
+        P.stats.passes = (int)P.blocks.size();
+        P.stats.tile_bits = 0;
+        P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
+        return QSIM_OK;
+    }
     if (o.fuse_k > 0) {
-        if (!fused_tc_supported((int)h->dt, o.fuse_k, h->n))
-            return fail(QSIM_EUNSUPPORTED, "fused blocks on the tensor cores need complex64, k = 4 or 5, n >= k + 7");
         plan_fused(pg, h->n, o.fuse_k, P.blocks);
         const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
         P.bmats.resize(per * P.blocks.size());
@@ -546,9 +576,19 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     return QSIM_OK;
 }
 
-static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *d_bmats) {
+static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *d_bmats, const void *d_cmats) {
     if (P.blocks.empty()) return QSIM_OK;
     const int k = P.blocks[0].k;
+    if (P.cuda_core) {
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            const void *dU = static_cast<const unsigned char *>(d_cmats) + P.cmat_stride * b;
+            CK(launch(h, F_DENSE, 2.0 * (double)state_bytes(h), 1,
+                      [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, P.blocks[b].pos, dU, h->stream); },
+                      P.blocks[b].flops),
+               "fused block (CUDA cores)");
+        }
+        return QSIM_OK;
+    }
     const size_t per = 2 * (size_t)(2 << k) * (size_t)(2 << k);
     for (size_t b = 0; b < P.blocks.size(); b++) {
         TileGeom g;
@@ -563,7 +603,9 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
 }
 
 static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops, const TilePhase *d_phases) {
-    if (!P.blocks.empty()) return run_blocks(h, P, P.d_bmats ? P.d_bmats : static_cast<const float *>(h->d_dense));
+    if (!P.blocks.empty())
+        return run_blocks(h, P, P.d_bmats ? P.d_bmats : static_cast<const float *>(h->d_dense),
+                          P.d_cmats ? P.d_cmats : h->d_dense);
     if (P.mode == QSIM_MODE_PERGATE) {
         for (const PGate &g : P.sweeps) {
             qsim_status st = sweep_gate(h, g);
@@ -580,10 +622,11 @@ qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, c
     qsim_status st = build_plan(h, gates, ng, opts, P);
     if (st != QSIM_OK) return st;
     if (!P.blocks.empty()) {
-        const size_t bytes = P.bmats.size() * sizeof(float);
+        const size_t bytes = P.cuda_core ? P.cmats.size() : P.bmats.size() * sizeof(float);
+        const void *src = P.cuda_core ? static_cast<const void *>(P.cmats.data()) : static_cast<const void *>(P.bmats.data());
         st = ensure_dense(h, bytes);
         if (st != QSIM_OK) return st;
-        CK(cudaMemcpyAsync(h->d_dense, P.bmats.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload blocks");
+        CK(cudaMemcpyAsync(h->d_dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "upload blocks");
         CK(cudaStreamSynchronize(h->stream), "sync");  // the host copy dies with P
         h->h2d += bytes;
         return run_built(h, P, nullptr, nullptr);
@@ -600,6 +643,7 @@ static void plan_release(qsim_plan_s *P) {
     for (qsim_plan_s *c : P->cands) plan_release(c);
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     if (P->d_bmats) cudaFree(P->d_bmats);
+    if (P->d_cmats) cudaFree(P->d_cmats);
     if (P->d_ops) cudaFree(P->d_ops);
     if (P->d_phases) cudaFree(P->d_phases);
     delete P;
@@ -622,6 +666,12 @@ static qsim_status create_one(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         if (e != cudaSuccess) st = cuda_fail(e, "upload plan");
         else h->h2d += P->plan.ops.size() * sizeof(TileOp) + P->plan.phases.size() * sizeof(TilePhase);
+    }
+    if (st == QSIM_OK && !P->cmats.empty()) {
+        cudaError_t e = cudaMalloc(&P->d_cmats, P->cmats.size());
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_cmats, P->cmats.data(), P->cmats.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload fused blocks");
+        else h->h2d += P->cmats.size();
     }
     if (st == QSIM_OK && !P->bmats.empty()) {
         cudaError_t e = cudaMalloc(&P->d_bmats, P->bmats.size() * sizeof(float));

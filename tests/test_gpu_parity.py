@@ -424,6 +424,33 @@ def test_fused_blocks_circuit_c64(q, k, n):
     st.free()
 
 
+@pytest.mark.parametrize("dt,k", [("c128", 3), ("c128", 5), ("c128", 6), ("c64", 6)])
+def test_fused_blocks_cuda_cores(q, dt, k):
+    # fusion widths and precisions the tensor-core kernel does not take run
+    # as dense blocks on the CUDA cores (FP64 for complex128)
+    n = 13
+    gates = inputs.random_circuit(n, 5, seed=300 + k)
+    rng = np.random.default_rng(k)
+    gates += [g for g in controlled_gates(rng, n, 10) if len(g.controls) + len(g.targets) <= k]
+    x0 = inputs.random_basis(n, seed=k)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, dt)
+    st.set_basis(x0)
+    st.profile(True)
+    plan = st.plan(gates, fuse_k=k)
+    assert plan.stats()["fuse_k"] == k
+    plan.run()
+    prof = st.profile_read()
+    assert "dense_cuda_core" in prof and "tile_pass" not in prof, prof
+    assert err(st.get_state(), ref) < TOL[dt]
+    # the one-shot path (gate list in host memory) gives the same state
+    st.set_basis(x0)
+    st.run(gates, fuse_k=k)
+    assert err(st.get_state(), ref) < TOL[dt]
+    plan.free()
+    st.free()
+
+
 def test_fused_blocks_adder_exact(q):
     values, m = [45, 17], 7
     n = 2 * m
