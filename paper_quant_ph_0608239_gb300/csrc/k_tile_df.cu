@@ -27,6 +27,10 @@ constexpr int kThreadsDF = 256;
 constexpr int kMaxHDF = 10;
 constexpr int kMaxCopyShiftDF = 14;
 constexpr long long kWaitBudgetDF = 4000000000ll;
+#ifndef QSIM_DF_PAIRS
+#define QSIM_DF_PAIRS 2
+#endif
+constexpr int kPairIt = QSIM_DF_PAIRS;  // pairs a thread updates per loop iteration
 
 __device__ __forceinline__ uint32_t ins0d(uint32_t i, int pos) {
     return ((i >> pos) << (pos + 1)) | (i & ((1u << pos) - 1u));
@@ -109,42 +113,50 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
             }
             return;
         }
-        // two independent pairs per iteration: the two-sum chains of one pair
-        // fill the latency of the other's
+        // kPairIt independent pairs per iteration: the two-sum chains of one
+        // pair fill the latency of the others'
         const uint32_t half = npair, step = blockDim.x;
-        for (uint32_t p = threadIdx.x; p < half; p += 2 * step) {
-            const uint32_t q = p + step;
-            const bool has2 = q < half;
-            const uint32_t i0 = pair0(p), j0 = has2 ? pair0(q) : i0;
-            const uint32_t i1 = i0 | bt, j1 = j0 | bt;
-            const bool ok0 = true, ok1 = has2;
-            const dcx a = ldx(t, i0), b = ldx(t, i1);
-            const dcx c = ldx(t, j0), d = ldx(t, j1);
-            dcx x0, x1, y0, y1;
+        for (uint32_t p = threadIdx.x; p < half; p += kPairIt * step) {
+            uint32_t ia[kPairIt], ib[kPairIt];
+            bool ok[kPairIt];
+            dcx va[kPairIt], vb[kPairIt];
+#pragma unroll
+            for (int k = 0; k < kPairIt; k++) {
+                const uint32_t pp = p + (uint32_t)k * step;
+                ok[k] = pp < half;
+                ia[k] = pair0(ok[k] ? pp : p);
+                ib[k] = ia[k] | bt;
+                va[k] = ldx(t, ia[k]);
+                vb[k] = ldx(t, ib[k]);
+            }
             if (pk == 0) {
-                x0 = dcx_mul2(u0, a, u1, b);
-                y0 = dcx_mul2(u0, c, u1, d);
-                x1 = dcx_mul2(u2, a, u3, b);
-                y1 = dcx_mul2(u2, c, u3, d);
+#pragma unroll
+                for (int k = 0; k < kPairIt; k++) {
+                    const dcx x0 = dcx_mul2(u0, va[k], u1, vb[k]), x1 = dcx_mul2(u2, va[k], u3, vb[k]);
+                    va[k] = x0;
+                    vb[k] = x1;
+                }
             } else if (pk == 1) {
-                x0 = dcx_rmul2(u0.re, a, u1.re, b);
-                y0 = dcx_rmul2(u0.re, c, u1.re, d);
-                x1 = dcx_rmul2(u2.re, a, u3.re, b);
-                y1 = dcx_rmul2(u2.re, c, u3.re, d);
+#pragma unroll
+                for (int k = 0; k < kPairIt; k++) {
+                    const dcx x0 = dcx_rmul2(u0.re, va[k], u1.re, vb[k]), x1 = dcx_rmul2(u2.re, va[k], u3.re, vb[k]);
+                    va[k] = x0;
+                    vb[k] = x1;
+                }
             } else {
-                x0 = dcx_mul(u1, b);
-                y0 = dcx_mul(u1, d);
-                x1 = dcx_mul(u2, a);
-                y1 = dcx_mul(u2, c);
+#pragma unroll
+                for (int k = 0; k < kPairIt; k++) {
+                    const dcx x0 = dcx_mul(u1, vb[k]), x1 = dcx_mul(u2, va[k]);
+                    va[k] = x0;
+                    vb[k] = x1;
+                }
             }
-            if (ok0) {
-                stx(t, i0, x0);
-                stx(t, i1, x1);
-            }
-            if (ok1) {
-                stx(t, j0, y0);
-                stx(t, j1, y1);
-            }
+#pragma unroll
+            for (int k = 0; k < kPairIt; k++)
+                if (ok[k]) {
+                    stx(t, ia[k], va[k]);
+                    stx(t, ib[k], vb[k]);
+                }
         }
     } else if (kind == TOP_PHASE) {
         const uint32_t bt = 1u << op.tl, fixed = bt | lc;
