@@ -107,7 +107,10 @@ typedef struct {
     int32_t fuse_k;     /* > 0: apply the circuit as dense blocks of at most fuse_k qubits
                            (1..6), each the FP64 product of its gates: complex64 with
                            k = 4 or 5 on the tensor cores (3xTF32), other widths and
-                           complex128 (in FP64) on the CUDA cores.  0 or -1: tile passes */
+                           complex128 (in FP64) on the CUDA cores.  A block may take a
+                           gate past earlier gates on other qubits (they commute).
+                           QSIM_EINVAL if a gate acts on more than fuse_k qubits
+                           (controls included).  0 or -1: tile passes */
     int32_t max_swap;   /* most bit pairs exchanged per interchange pass; 0 = default */
     int32_t wait_budget_us; /* batches: longest device-side wait between passes
                                before QSIM_ETIMEOUT; 0 = about 2 s */
@@ -242,6 +245,21 @@ QSIM_API qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, siz
 QSIM_API qsim_status qsim_plan_run(qsim_handle h, qsim_plan p);
 QSIM_API qsim_status qsim_plan_get_stats(qsim_plan p, qsim_plan_stats *out);
 QSIM_API qsim_status qsim_plan_free(qsim_plan p);
+
+/* qsim_fuse_blocks: the dense blocks a plan with fuse_k = k applies, computed
+ * on the host (no state, no device work), for inspecting a fusion before
+ * running it.  Gates are read in order on qubits 0..n-1 (identity map).  The
+ * blocks are the circuit's gates grouped into products on at most k qubits
+ * (Sec. II.B gates; a block may take a gate past earlier gates on other
+ * qubits, with which it commutes); applied in order they equal the circuit.
+ * Sets *nblocks to their number and, for blocks b < max_blocks, writes
+ * pos[b * k + j] = the qubit of bit j of block b's index and, if U is not
+ * NULL, U[b * 2 * 4^k ...] = its 2^k x 2^k unitary (FP64, row-major (re, im)
+ * pairs).  pos and U may be NULL (count only); both are caller-owned.
+ * QSIM_EINVAL: a bad gate, k outside [1, min(6, n)], or a gate on more than
+ * k qubits (controls included). */
+QSIM_API qsim_status qsim_fuse_blocks(int n, const qsim_gate *gates, size_t ng, int k, int32_t *pos, double *U,
+                                      size_t max_blocks, size_t *nblocks);
 
 /* ---- instrumentation --------------------------------------------------------
  * qsim_profile_enable(h, 1): from now on every kernel launch made for h is

@@ -237,6 +237,24 @@ class Plan:
             pass
 
 
+def fuse_blocks(n, gates, k):
+    """The dense blocks a plan with ``fuse_k=k`` applies, planned on the host
+    (no device): a list of (qubits, U), U the 2^k x 2^k complex128 product of
+    the block's gates (bit j of U's index = qubits[j]).  Applied in order the
+    blocks equal the circuit."""
+    arr = gate_array(gates)
+    nb = ctypes.c_size_t()
+    _capi.call("qsim_fuse_blocks", int(n), arr, len(gates), int(k), None, None, 0, ctypes.byref(nb))
+    m = nb.value
+    pos = np.zeros((max(m, 1), k), dtype=np.int32)
+    D = 1 << k
+    U = np.zeros((max(m, 1), D, D, 2), dtype=np.float64)
+    _capi.call("qsim_fuse_blocks", int(n), arr, len(gates), int(k), pos.ctypes.data_as(ctypes.c_void_p),
+               U.ctypes.data_as(ctypes.c_void_p), m, ctypes.byref(nb))
+    Uc = U[..., 0] + 1j * U[..., 1]
+    return [(tuple(int(q) for q in pos[b]), Uc[b]) for b in range(m)]
+
+
 def _circuit_array(states, x0s, gate_lists):
     nc = len(states)
     arr = (QsimCircuit * nc)()

@@ -113,6 +113,8 @@ _SIGS = {
     "qsim_plan_run": ([c_handle, ctypes.c_void_p], None),
     "qsim_plan_get_stats": ([ctypes.c_void_p, ctypes.POINTER(QsimPlanStats)], None),
     "qsim_plan_free": ([ctypes.c_void_p], None),
+    "qsim_fuse_blocks": ([ctypes.c_int, ctypes.POINTER(QsimGate), ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], None),
     "qsim_profile_enable": ([c_handle, ctypes.c_int], None),
     "qsim_profile_read": ([c_handle, ctypes.POINTER(QsimKernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                           None),

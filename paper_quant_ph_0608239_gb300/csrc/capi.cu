@@ -523,7 +523,8 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     if (o.fuse_k > 0 && !fused_tc_supported((int)h->dt, o.fuse_k, h->n)) {
         // dense blocks on the CUDA cores (complex128, k = 1..6, small registers)
         if (o.fuse_k > 6 || o.fuse_k > h->n) return fail(QSIM_EUNSUPPORTED, "fused blocks need k <= min(6, n)");
-        plan_fused(pg, h->n, o.fuse_k, P.blocks);
+        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+            return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         const size_t ent = (size_t)1 << (2 * o.fuse_k);
         P.cuda_core = true;
         P.cmat_stride = ent * amp_bytes(h->dt);
@@ -547,7 +548,8 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         return QSIM_OK;
     }
     if (o.fuse_k > 0) {
-        plan_fused(pg, h->n, o.fuse_k, P.blocks);
+        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+            return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
         P.bmats.resize(per * P.blocks.size());
         for (size_t b = 0; b < P.blocks.size(); b++) {
@@ -745,7 +747,9 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
         o.fuse_k = x.second;
         qsim_plan_s *c = nullptr;
         qsim_status st = create_one(h, gates, ng, &o, c);
-        if (st == QSIM_EUNSUPPORTED) continue;  // e.g. no tile geometry for a fused width
+        // skipped: no tile geometry for a fused width, or a gate wider than it
+        // (the tile candidates, planned first, have validated every gate)
+        if (st == QSIM_EUNSUPPORTED || (st == QSIM_EINVAL && x.second > 0)) continue;
         if (st != QSIM_OK) {
             plan_release(A);
             return st;
@@ -812,6 +816,29 @@ qsim_status qsim_plan_free(qsim_plan p) {
     if (!p) return QSIM_OK;
     cudaDeviceSynchronize();  // runs in flight may still read the plan's tables
     plan_release(p);
+    return QSIM_OK;
+}
+
+qsim_status qsim_fuse_blocks(int n, const qsim_gate *gates, size_t ng, int k, int32_t *pos, double *U,
+                             size_t max_blocks, size_t *nblocks) {
+    if (!nblocks || (ng && !gates)) return fail(QSIM_EINVAL, "null argument");
+    if (n < 1 || n > kMaxQubits) return fail(QSIM_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    if (k < 1 || k > 6 || k > n) return fail(QSIM_EINVAL, "k = %d outside [1, min(6, n)]", k);
+    int ident[64];
+    for (int q = 0; q < 64; q++) ident[q] = q;
+    std::vector<PGate> pg(ng);
+    std::string msg;
+    for (size_t i = 0; i < ng; i++)
+        if (!prepare_gate(gates[i], n, ident, pg[i], msg)) return fail(QSIM_EINVAL, "gate %zu: %s", i, msg.c_str());
+    std::vector<FusedBlock> blocks;
+    if (!plan_fused(pg, n, k, blocks)) return fail(QSIM_EINVAL, "a gate acts on more qubits than k");
+    *nblocks = blocks.size();
+    const size_t ent = (size_t)1 << (2 * k);
+    for (size_t b = 0; b < blocks.size() && b < max_blocks; b++) {
+        if (pos)
+            for (int j = 0; j < k; j++) pos[b * k + j] = blocks[b].pos[j];
+        if (U) std::memcpy(U + 2 * ent * b, blocks[b].U.data(), 16 * ent);
+    }
     return QSIM_OK;
 }
 

@@ -542,22 +542,53 @@ void emit_block(const std::vector<const PGate *> &gs, uint64_t mask, int n, int 
 
 }  // namespace
 
-void plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out) {
+bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out) {
     out.clear();
-    std::vector<const PGate *> cur;
-    uint64_t mask = 0;
-    for (const PGate &g : gates) {
-        const uint64_t m = block_bits(g);
-        if (__builtin_popcountll(mask | m) <= k) {
-            mask |= m;
-            cur.push_back(&g);
-        } else {
-            emit_block(cur, mask, n, k, out);
-            cur.assign(1, &g);
-            mask = m;
-        }
+    const int ng = (int)gates.size();
+    std::vector<uint64_t> bits((size_t)ng);
+    std::vector<std::vector<int>> queue(64);  // per qubit: the gates touching it, in circuit order
+    for (int i = 0; i < ng; i++) {
+        bits[i] = block_bits(gates[i]);
+        if (popc(bits[i]) > k) return false;
+        for (uint64_t m = bits[i]; m; m &= m - 1) queue[__builtin_ctzll(m)].push_back(i);
     }
-    if (!cur.empty()) emit_block(cur, mask, n, k, out);
+    std::vector<size_t> head(64, 0);  // first gate of each queue not yet placed
+    std::vector<char> placed((size_t)ng, 0);
+    auto ready = [&](int i) {  // every earlier gate on i's qubits is placed
+        for (uint64_t m = bits[i]; m; m &= m - 1)
+            if (queue[__builtin_ctzll(m)][head[__builtin_ctzll(m)]] != i) return false;
+        return true;
+    };
+    std::vector<const PGate *> cur;
+    int first = 0;
+    for (;;) {
+        while (first < ng && placed[first]) first++;
+        if (first == ng) break;
+        uint64_t mask = 0;
+        cur.clear();
+        int pick = first;  // a block starts at the earliest gate not yet placed
+        while (pick >= 0) {
+            mask |= bits[pick];
+            cur.push_back(&gates[pick]);
+            placed[pick] = 1;
+            for (uint64_t m = bits[pick]; m; m &= m - 1) head[__builtin_ctzll(m)]++;
+            // next: the ready gate adding the fewest qubits (the earliest on ties)
+            pick = -1;
+            int best = 65;
+            for (int q = 0; q < 64; q++) {
+                if (head[q] >= queue[q].size()) continue;
+                const int i = queue[q][head[q]];
+                if (popc(bits[i] | mask) > k) continue;
+                const int add = popc(bits[i] & ~mask);
+                if (add > best || (add == best && i > pick)) continue;
+                if (!ready(i)) continue;
+                best = add;
+                pick = i;
+            }
+        }
+        emit_block(cur, mask, n, k, out);
+    }
+    return true;
 }
 
 bool fused_geometry(int n, int k, const int *pos, TileGeom &g, FusedMap &fm) {

@@ -67,15 +67,19 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
 void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vector<TileOp> &ops_out,
                   std::vector<TilePhase> &phases_out);
 
-// Dense fusion: consecutive gates grouped into blocks acting on at most k
-// qubits; each block's 2^k x 2^k unitary is the FP64 product of its gates.
+// Dense fusion: the gates grouped into blocks acting on at most k qubits;
+// each block's 2^k x 2^k unitary is the FP64 product of its gates.  A block
+// starts at the earliest gate not yet placed and keeps taking a gate whose
+// earlier gates on each of its qubits are all placed (so it moves only past
+// gates on other qubits, which commute with it), the one adding the fewest
+// qubits first.  False if a gate acts on more than k qubits.
 struct FusedBlock {
     int k;
     int pos[8];               // physical bits, bit j of U's index = pos[j]
     std::vector<double> U;    // 2^k x 2^k complex, row-major (re, im)
     double flops;             // algorithmic flops: 8 * 2^k per amplitude
 };
-void plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out);
+bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out);
 
 // Tile geometry of a fused block on the tensor cores: T = k + 7 bits holding
 // the block's qubits; false if n is too small.

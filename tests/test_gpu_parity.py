@@ -234,6 +234,32 @@ def test_autotuned_plan(q, dt):
     st.free()
 
 
+def test_autotune_drops_fusion_narrower_than_a_gate(q):
+    # a NOT with four controls acts on 5 qubits: the k = 4 candidate cannot
+    # hold it and is left out, k = 5 stays; a plain fused plan that is too
+    # narrow is rejected before any work
+    n = 16
+    gates = inputs.random_circuit(n, 4, seed=17)
+    gates.insert(40, Gate("NOT", (3,), (0, 7, 11, 15), ()))
+    x0 = inputs.random_basis(n, seed=17)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, "c64")
+    plan = st.plan(gates, mode=q.MODE_AUTO)
+    ks = [c["fuse_k"] for c in plan.stats()["autotune"]]
+    assert 5 in ks and 4 not in ks, ks
+    for _ in range(len(ks) + 1):
+        st.set_basis(x0)
+        plan.run()
+        assert err(st.get_state(), ref) < 2 * TOL["c64"]
+    plan.free()
+    st.set_basis(x0)
+    with pytest.raises(q.QsimError) as e:
+        st.run(gates, fuse_k=4)
+    assert e.value.status == q.QSIM_EINVAL
+    assert err(st.get_state(), oracle.basis(n, x0)) == 0.0  # nothing applied
+    st.free()
+
+
 def test_qft_config_c128_and_closed_form(q):
     n = 10
     x, gates = inputs.qft_circuit(n, seed=1)
