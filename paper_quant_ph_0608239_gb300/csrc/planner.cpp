@@ -2,6 +2,7 @@
 #include "planner.hpp"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -552,13 +553,43 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
         if (popc(bits[i]) > k) return false;
         for (uint64_t m = bits[i]; m; m &= m - 1) queue[__builtin_ctzll(m)].push_back(i);
     }
-    std::vector<size_t> head(64, 0);  // first gate of each queue not yet placed
-    std::vector<char> placed((size_t)ng, 0);
-    auto ready = [&](int i) {  // every earlier gate on i's qubits is placed
+    using Heads = std::array<uint32_t, 64>;  // per qubit: first gate of its queue not yet placed
+    auto front = [&](const Heads &hd, int q) { return hd[q] < queue[q].size() ? queue[q][hd[q]] : -1; };
+    auto ready = [&](const Heads &hd, int i) {  // every earlier gate on i's qubits is placed
         for (uint64_t m = bits[i]; m; m &= m - 1)
-            if (queue[__builtin_ctzll(m)][head[__builtin_ctzll(m)]] != i) return false;
+            if (front(hd, __builtin_ctzll(m)) != i) return false;
         return true;
     };
+    auto take = [&](Heads &hd, int i) {
+        for (uint64_t m = bits[i]; m; m &= m - 1) hd[__builtin_ctzll(m)]++;
+    };
+    // the ready gate that fits a block on mask and adds the fewest qubits
+    // (the earliest on ties), or -1; each gate is seen at its lowest qubit
+    auto next_min = [&](const Heads &hd, uint64_t mask, int &add) {
+        int pick = -1;
+        add = 65;
+        for (int q = 0; q < 64; q++) {
+            const int i = front(hd, q);
+            if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | mask) > k) continue;
+            const int a = popc(bits[i] & ~mask);
+            if (a > add || (a == add && i > pick) || !ready(hd, i)) continue;
+            add = a;
+            pick = i;
+        }
+        return pick;
+    };
+    // gates the fewest-qubits-first rule would still add to a block (at most cap)
+    constexpr int kLookCap = 1024;
+    auto greedy_count = [&](Heads hd, uint64_t mask) {
+        int c = 0, add;
+        for (int i; c < kLookCap && (i = next_min(hd, mask, add)) >= 0; c++) {
+            mask |= bits[i];
+            take(hd, i);
+        }
+        return c;
+    };
+    Heads head{};
+    std::vector<char> placed((size_t)ng, 0);
     std::vector<const PGate *> cur;
     int first = 0;
     for (;;) {
@@ -571,19 +602,25 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
             mask |= bits[pick];
             cur.push_back(&gates[pick]);
             placed[pick] = 1;
-            for (uint64_t m = bits[pick]; m; m &= m - 1) head[__builtin_ctzll(m)]++;
-            // next: the ready gate adding the fewest qubits (the earliest on ties)
-            pick = -1;
-            int best = 65;
+            take(head, pick);
+            int add;
+            pick = next_min(head, mask, add);  // gates inside the block's qubits come first
+            if (pick < 0 || add == 0) continue;
+            // a gate adding qubits: the one after which the block takes the
+            // most gates (fewer added qubits, then the earliest, on ties)
+            int best_cnt = -1, best_add = 65;
             for (int q = 0; q < 64; q++) {
-                if (head[q] >= queue[q].size()) continue;
-                const int i = queue[q][head[q]];
-                if (popc(bits[i] | mask) > k) continue;
-                const int add = popc(bits[i] & ~mask);
-                if (add > best || (add == best && i > pick)) continue;
-                if (!ready(i)) continue;
-                best = add;
-                pick = i;
+                const int i = front(head, q);
+                if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | mask) > k || !ready(head, i)) continue;
+                Heads h2 = head;
+                take(h2, i);
+                const int cnt = greedy_count(h2, mask | bits[i]);
+                const int a = popc(bits[i] & ~mask);
+                if (cnt > best_cnt || (cnt == best_cnt && (a < best_add || (a == best_add && i < pick)))) {
+                    best_cnt = cnt;
+                    best_add = a;
+                    pick = i;
+                }
             }
         }
         emit_block(cur, mask, n, k, out);

@@ -71,8 +71,10 @@ void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vecto
 // each block's 2^k x 2^k unitary is the FP64 product of its gates.  A block
 // starts at the earliest gate not yet placed and keeps taking a gate whose
 // earlier gates on each of its qubits are all placed (so it moves only past
-// gates on other qubits, which commute with it), the one adding the fewest
-// qubits first.  False if a gate acts on more than k qubits.
+// gates on other qubits, which commute with it): gates inside the block's
+// qubits first, else the gate after which the fewest-qubits-first rule would
+// add the most gates (one step of lookahead).  False if a gate acts on more
+// than k qubits.
 struct FusedBlock {
     int k;
     int pos[8];               // physical bits, bit j of U's index = pos[j]
