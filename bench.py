@@ -339,7 +339,10 @@ def run_ours(args, w, ws, rank, local):
     if fam == "dense_cuda_core" and w["dtype"] == "c128":
         alu_peak = FP64_PEAK_TFLOPS  # dense blocks compute in FP64
     frac_hbm, frac_alu = gbs / hbm_peak, tflops / alu_peak
-    traffic = ncu_traffic(fam, args.workload)
+    tkey = args.workload
+    if pst["fuse_k"] and "_fused" not in tkey:  # the autotuner picked dense blocks
+        tkey += "_fused%d" % pst["fuse_k"]
+    traffic = ncu_traffic(fam, tkey)
     hbm_roof = {"bound": "hbm", "kernel": fam, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": frac_hbm, "traffic": traffic, "peak_source": peak_src + " copy (MEASURED_PEAKS.json)",
                 "alg_bytes_per_launch": by / nl, "launches": nl, "avg_launch_ms": ms / nl}

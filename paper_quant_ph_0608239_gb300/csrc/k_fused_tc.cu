@@ -30,7 +30,6 @@ namespace qsim {
 
 namespace {
 
-constexpr int kThreadsTC = 256;
 constexpr int kMaxHTC = 10;
 constexpr long long kWaitBudgetTC = 4000000000ll;
 
@@ -41,51 +40,81 @@ __host__ __device__ __forceinline__ uint32_t canon_off(uint32_t row, uint32_t kk
     return (row & 7u) * 16u + (kk & 3u) * 4u + (kk >> 2) * 128u + (row >> 3) * (kr * 32u);
 }
 
+// Slots: one CTA per SM holds NS independent pipelines of 128 threads (four
+// warps = the 128 tensor-memory lanes), each with its own tile and operand
+// buffers, barriers and accumulator columns, all sharing one copy of B_hi /
+// B_lo.  A slot's steps (fetch, split, MMA, epilogue, store) run in order,
+// the slots overlap one another.
+template <int K> struct TcSlots;
+template <> struct TcSlots<4> { static constexpr int NS = 4; };  // 4 x 32 KiB + 8 KiB
+template <> struct TcSlots<5> { static constexpr int NS = 3; };  // 3 x 64 KiB + 32 KiB
+constexpr int kSlotThreads = 128;
+
+__device__ __forceinline__ void slot_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+// OR of v over the slot's 128 threads (a barrier as well)
+__device__ __forceinline__ bool slot_any(bool v, uint32_t id) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(r) : "r"((uint32_t)v), "r"(id) : "memory");
+    return r != 0;
+}
+
 template <int K>
-__global__ void __launch_bounds__(kThreadsTC, 2)
+__global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     k_fused_tc(float2 *__restrict__ a, TileGeom g, FusedMap fm, const float *__restrict__ bmat, uint32_t *err,
                uint64_t ntiles) {
+    constexpr int NS = TcSlots<K>::NS;
     constexpr int KR = 2 << K;              // real columns = 2 * 2^K
     constexpr int N = KR;                   // output columns
     constexpr int T = K + 7;                // 128 groups per tile
     constexpr uint32_t TS = 1u << T;
     constexpr uint32_t OPB = 8u << T;       // operand bytes (A_hi, A_lo, tile)
     constexpr uint32_t BB = (uint32_t)N * KR * 4u;
-    constexpr int PER = TS / kThreadsTC;    // amplitudes per thread
+    constexpr int PER = TS / kSlotThreads;  // amplitudes per thread
+    constexpr uint32_t TCOLS = NS * N <= 32 ? 32 : NS * N <= 64 ? 64 : NS * N <= 128 ? 128 : 256;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *s_tile = smem_raw;       // loaded tile, then A_lo
-    unsigned char *s_ahi = smem_raw + OPB;  // A_hi, then the output tile
-    unsigned char *s_bhi = smem_raw + 2 * OPB;
-    unsigned char *s_blo = s_bhi + BB;
-    __shared__ __align__(8) uint64_t bar_ld, bar_mma, bar_b;
+    unsigned char *s_bhi = smem_raw;
+    unsigned char *s_blo = smem_raw + BB;
+    __shared__ __align__(8) uint64_t bar_ld[NS], bar_mma[NS], bar_b;
     __shared__ uint32_t tmem_slot;
-    __shared__ uint64_t runoff[1 << kMaxHTC];
+    __shared__ int s_hb[kMaxHTC];     // the high tile bits, indexed at run time
+    __shared__ uint32_t s_wsp[T];     // local bit b of a tile index -> its byte weight in the operand layout
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
     const uint32_t run_bytes = 8u << L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = threadIdx.x / kSlotThreads, st = threadIdx.x % kSlotThreads, ws = st >> 5;
+    const uint32_t bar_id = 1u + (uint32_t)slot;  // named barrier of the slot (0 is __syncthreads)
+    unsigned char *s_tile = smem_raw + 2 * BB + (size_t)slot * 2 * OPB;  // loaded tile, then A_lo
+    unsigned char *s_ahi = s_tile + OPB;                                // A_hi, then the output tile
 
-    __shared__ int s_hb[kMaxHTC];  // the high tile bits, indexed at run time
-    if (threadIdx.x < kMaxHTC) s_hb[threadIdx.x] = threadIdx.x < (unsigned)H ? g.hb[threadIdx.x] : 0;
-    for (uint32_t j = threadIdx.x; j < nruns; j += blockDim.x) {
-        uint64_t o = 0;
-        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
-        runoff[j] = o;
+    if (threadIdx.x == 0) {  // (compile-time indices into the parameters: no local-memory copy)
+#pragma unroll
+        for (int k = 0; k < kMaxHTC; k++) s_hb[k] = k < H ? g.hb[k] : 0;
+#pragma unroll
+        for (int r = 0; r < T - K; r++)  // row-index bit r: canon_off weight of m bit r
+            s_wsp[fm.row[r]] = r < 3 ? 16u << r : (uint32_t)(KR * 32) << (r - 3);
+#pragma unroll
+        for (int j = 0; j < K; j++)  // input column bit j: weight of kk bit j + 1 (kk = 2c)
+            s_wsp[fm.col[j]] = j == 0 ? 8u : 128u << (j - 1);
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bar_ld, 1);
-        mbar_init(&bar_mma, 1);
+        for (int i = 0; i < NS; i++) {
+            mbar_init(&bar_ld[i], 1);
+            mbar_init(&bar_mma[i], 1);
+        }
         mbar_init(&bar_b, 1);
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(&tmem_slot, N < 32 ? 32 : N);
+        tmem_alloc(&tmem_slot, TCOLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
+    const uint32_t tmem = tmem_slot + (uint32_t)(slot * N);  // the slot's accumulator columns
 
     // B_hi, B_lo: 2 x BB bytes from global, once per CTA
     if (threadIdx.x == 0) {
@@ -93,41 +122,58 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
         bulk_g2s(s_bhi, bmat, BB, &bar_b);
         bulk_g2s(s_blo, bmat + BB / 4, BB, &bar_b);
     }
-    // every abort decision goes through a block-wide vote, so all threads
-    // leave the loop at the same barrier
+    // every abort decision goes through a vote, so the threads of a slot
+    // leave its loop at the same barrier
     bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) != 0;
 
-    const uint32_t idesc = umma_idesc_tf32(128, N);
-    const uint32_t ibase = [&] {  // epilogue: tile bits of this thread's group (TMEM lane)
-        const uint32_t m = (uint32_t)(32 * (warp & 3) + lane);
-        uint32_t x = 0;
-        for (int b = 0; b < T - K; b++) x |= ((m >> b) & 1u) << fm.row[b];
-        return x;
-    }();
-    uint32_t ld_parity = 0, mma_parity = 0;
-    float2 *tin = reinterpret_cast<float2 *>(s_tile);
+    // Operand offsets are sums of per-bit weights: tile index i = st + 128 s
+    // splits into the thread's bits 0..6 and the step's bits 7..T-1.
+    uint32_t off_lo = 0, w_hi[K];
+#pragma unroll
+    for (int b = 0; b < 7; b++) off_lo += ((uint32_t)st >> b & 1u) * s_wsp[b];
+#pragma unroll
+    for (int b = 0; b < K; b++) w_hi[b] = s_wsp[7 + b];
+    // epilogue: this thread's group m = TMEM lane (32 ws + lane) and the
+    // tile bits of the gate's columns
+    uint32_t ibase = 0, w_col[K];
+    {
+        const uint32_t m = (uint32_t)(32 * ws + lane);
+#pragma unroll
+        for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+#pragma unroll
+        for (int b = 0; b < K; b++) w_col[b] = 1u << fm.col[b];
+    }
+    auto run_off = [&](uint32_t j) {  // offset of run j: its bits deposited at the high tile bits
+        uint64_t o = 0;
+        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << s_hb[k];
+        return o;
+    };
     auto tile_base = [&](uint64_t tile) {
         uint64_t base = tile << L;
         for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
         return base;
     };
-    auto issue_load = [&](uint64_t tile) {  // warp 0
+    float2 *tin = reinterpret_cast<float2 *>(s_tile);
+    auto issue_load = [&](uint64_t tile) {  // warp 0 of the slot
         const uint64_t base = tile_base(tile);
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar_ld, TS * 8u);
+        if (lane == 0) mbar_arrive_expect_tx(&bar_ld[slot], TS * 8u);
         __syncwarp();
-        for (uint32_t j = threadIdx.x; j < nruns; j += 32)
-            bulk_g2s(tin + ((size_t)j << L), a + (base | runoff[j]), run_bytes, &bar_ld);
+        for (uint32_t j = lane; j < nruns; j += 32)
+            bulk_g2s(tin + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[slot]);
     };
-    // Pipeline: the next tile is fetched into the load buffer as soon as the
-    // MMAs have read A_lo out of it, so the fetch runs under this tile's
-    // epilogue and store; the store's reads of the output buffer are awaited
-    // only when the next split is about to overwrite it.
-    if (warp == 0 && !aborted && blockIdx.x < ntiles) issue_load(blockIdx.x);
-    for (uint64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+    uint32_t ld_parity = 0, mma_parity = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * NS;
+    uint64_t tile = (uint64_t)blockIdx.x * NS + slot;
+    // Pipeline of a slot: the next tile is fetched into the load buffer as
+    // soon as the MMAs have read A_lo out of it, so the fetch runs under this
+    // tile's epilogue and store; the store's reads of the output buffer are
+    // awaited only when the next split is about to overwrite it.
+    if (ws == 0 && !aborted && tile < ntiles) issue_load(tile);
+    for (; tile < ntiles && !aborted; tile += stride) {
         const uint64_t base = tile_base(tile);
-        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC)) != 0;
+        aborted = slot_any(!mbar_wait_bounded(&bar_ld[slot], ld_parity, kWaitBudgetTC), bar_id);
         if (aborted) {
-            mbar_wait_bounded(&bar_ld, ld_parity, kWaitBudgetTC);  // let the copies in flight land
+            mbar_wait_bounded(&bar_ld[slot], ld_parity, kWaitBudgetTC);  // let the copies in flight land
             break;
         }
         ld_parity ^= 1u;
@@ -135,30 +181,28 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
         // split into TF32 head / FP32 tail, scatter into the canonical layouts
         float2 x[PER];
 #pragma unroll
-        for (int s = 0; s < PER; s++) x[s] = tin[threadIdx.x + s * kThreadsTC];
-        if (threadIdx.x < 32) bulk_wait_read_all();  // the previous store has read the output buffer
-        __syncthreads();  // the tile buffer becomes A_lo, the output buffer A_hi
+        for (int s = 0; s < PER; s++) x[s] = tin[st + s * kSlotThreads];
+        if (ws == 0) bulk_wait_read_all();  // the previous store has read the output buffer
+        slot_sync(bar_id);                  // the tile buffer becomes A_lo, the output buffer A_hi
 #pragma unroll
         for (int s = 0; s < PER; s++) {
-            const uint32_t i = threadIdx.x + s * kThreadsTC;
-            uint32_t m = 0, c = 0;
+            uint32_t off = off_lo;
 #pragma unroll
-            for (int b = 0; b < T - K; b++) m |= ((i >> fm.row[b]) & 1u) << b;
-#pragma unroll
-            for (int b = 0; b < K; b++) c |= ((i >> fm.col[b]) & 1u) << b;
+            for (int b = 0; b < K; b++)
+                if ((s >> b) & 1) off += w_hi[b];
             const float hr = to_tf32(x[s].x), hi_ = to_tf32(x[s].y);
-            const uint32_t off = canon_off(m, 2 * c, KR);  // (re, im) are adjacent in one 16-byte chunk
-            *reinterpret_cast<float2 *>(s_ahi + off) = make_float2(hr, hi_);
+            *reinterpret_cast<float2 *>(s_ahi + off) = make_float2(hr, hi_);  // (re, im) share a 16-byte chunk
             *reinterpret_cast<float2 *>(s_tile + off) = make_float2(x[s].x - hr, x[s].y - hi_);
         }
         fence_proxy_async_smem();  // generic-proxy writes -> tensor-core (async proxy) reads
         tc_fence_before();
-        __syncthreads();
+        slot_sync(bar_id);
         tc_fence_after();
 
-        if (threadIdx.x == 0) {
+        if (st == 0) {
             const uint32_t ahi = smem_u32(s_ahi), alo = smem_u32(s_tile);
             const uint32_t bhi = smem_u32(s_bhi), blo = smem_u32(s_blo);
+            const uint32_t idesc = umma_idesc_tf32(128, N);
 #pragma unroll
             for (int ks = 0; ks < KR / 8; ks++) {
                 const uint32_t o = (uint32_t)ks * 256u;  // 8 TF32 along K = two core matrices
@@ -167,73 +211,66 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
                 umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(blo + o, 128, KR * 32), idesc, 1u);
                 umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc, 1u);
             }
-            umma_commit(&bar_mma);
+            umma_commit(&bar_mma[slot]);
         }
-        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_mma, mma_parity, kWaitBudgetTC)) != 0;
+        aborted = slot_any(!mbar_wait_bounded(&bar_mma[slot], mma_parity, kWaitBudgetTC), bar_id);
         mma_parity ^= 1u;
         tc_fence_after();
         if (aborted) break;
         // A_lo is consumed: fetch the next tile into the load buffer
-        if (warp == 0 && tile + gridDim.x < ntiles) issue_load(tile + gridDim.x);
+        if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);
 
-        // epilogue: warp w reads lanes 32 (w % 4) .. +31 (groups), column chunk w / 4
+        // epilogue: warp ws reads TMEM lanes 32 ws .. +31 (its groups), 32
+        // columns (16 outputs) at a time
         float2 *tout = reinterpret_cast<float2 *>(s_ahi);
-        const int chunk = warp >> 2;
-        if (chunk < N / 32) {
+#pragma unroll
+        for (int chunk = 0; chunk < N / 32; chunk++) {
             uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * chunk), r);
+            tmem_ld32(tmem + ((uint32_t)(32 * ws) << 16) + (uint32_t)(32 * chunk), r);
             tmem_ld_wait();
+            const uint32_t cb = (K == 5 && chunk) ? w_col[K - 1] : 0u;  // output bit 4 = the chunk
 #pragma unroll
             for (int q = 0; q < 16; q++) {
-                const uint32_t cidx = (uint32_t)(16 * chunk + q);  // output amplitude of the group
-                uint32_t i = ibase;
+                uint32_t i = ibase | cb;
 #pragma unroll
-                for (int b = 0; b < K; b++) i |= ((cidx >> b) & 1u) << fm.col[b];
+                for (int b = 0; b < 4; b++)
+                    if ((q >> b) & 1) i |= w_col[b];
                 tout[i] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
             }
         }
         tc_fence_before();
         fence_proxy_async_smem();
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            for (uint32_t j = threadIdx.x; j < nruns; j += 32)
-                bulk_s2g(a + (base | runoff[j]), tout + ((size_t)j << L), run_bytes);
+        slot_sync(bar_id);
+        if (ws == 0) {
+            for (uint32_t j = lane; j < nruns; j += 32)
+                bulk_s2g(a + (base | run_off(j)), tout + ((size_t)j << L), run_bytes);
             bulk_commit();
         }
     }
-    if (aborted && threadIdx.x == 0) atomicExch(err, kErrTimeout);
-    if (threadIdx.x < 32) bulk_wait_all();
+    if (aborted && st == 0) atomicExch(err, kErrTimeout);
+    if (ws == 0) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, N < 32 ? 32 : N);
+    if (warp == 0) tmem_dealloc(tmem_slot, TCOLS);
 }
 
 template <int K>
 cudaError_t launch_k(void *amp, const TileGeom &g, const FusedMap &fm, const float *bmat, uint32_t *err,
                      int sm_count, cudaStream_t s) {
+    constexpr int NS = TcSlots<K>::NS;
     constexpr int KR = 2 << K;
     constexpr int T = K + 7;
-    // tile + operand buffers, B_hi / B_lo
-    const size_t smem = 2 * ((size_t)8 << T) + 2 * (size_t)KR * KR * 4;
+    // B_hi / B_lo, then per slot a tile and an operand buffer
+    const size_t smem = 2 * (size_t)KR * KR * 4 + (size_t)NS * 2 * ((size_t)8 << T);
     const uint64_t ntiles = 1ull << (g.n - T);
     cudaError_t e = cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // resident blocks per SM from the block's shared memory (plus 1 KiB the
-    // system reserves per block, of 228 KiB) and registers (64 Ki per SM),
-    // at most 4 (tensor memory: 4 x 128 columns)
-    cudaFuncAttributes fa{};
-    e = cudaFuncGetAttributes(&fa, k_fused_tc<K>);
-    if (e != cudaSuccess) return e;
-    const size_t per_block = smem + fa.sharedSizeBytes + 1024;
-    const int regs = ((fa.numRegs + 7) / 8) * 8 * kThreadsTC;
-    int per_sm = (int)((228u * 1024u) / per_block);
-    if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
-    if (per_sm > 4) per_sm = 4;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    uint64_t grid = (uint64_t)sm_count * per_sm;
-    if (grid > ntiles) grid = ntiles;
-    k_fused_tc<K><<<(unsigned)grid, kThreadsTC, smem, s>>>(static_cast<float2 *>(amp), g, fm, bmat, err, ntiles);
+    // one CTA per SM (its slots share B); fewer when there are fewer tiles
+    uint64_t grid = (ntiles + NS - 1) / NS;
+    if (grid > (uint64_t)sm_count) grid = (uint64_t)sm_count;
+    k_fused_tc<K><<<(unsigned)grid, kSlotThreads * NS, smem, s>>>(static_cast<float2 *>(amp), g, fm, bmat, err,
+                                                                  ntiles);
     return cudaGetLastError();
 }
 
