@@ -8,10 +8,12 @@
 //     D (rows = groups, 2K columns) = A (groups x 2K) * B^T,  K = 2^k,
 //
 // where a row of A is the group's amplitudes in their memory order
-// (re, im, re, im, ...).  Each CTA fetches a tile of 2^(k+7) amplitudes
-// (128 groups) with bulk asynchronous copies, splits every value into a TF32
-// head and an FP32 tail (x = hi + lo), writes A_hi and A_lo in the tensor
-// cores' canonical K-major layout, and one thread issues
+// (re, im, re, im, ...).  A slot of 128 threads (see below) fetches a tile of
+// 2^(k+7) amplitudes (128 groups) with bulk asynchronous copies; each thread
+// takes one group and splits every value into a TF32 head and an FP32 tail
+// (x = hi + lo), A_hi into the tensor cores' canonical K-major layout in
+// shared memory and A_lo into tensor memory (the thread's lane).  One thread
+// issues
 //
 //     D = A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T      (3xTF32, FP32 accumulate)
 //
@@ -65,41 +67,35 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     k_fused_tc(float2 *__restrict__ a, TileGeom g, FusedMap fm, const float *__restrict__ bmat, uint32_t *err,
                uint64_t ntiles) {
     constexpr int NS = TcSlots<K>::NS;
-    constexpr int KR = 2 << K;              // real columns = 2 * 2^K
+    constexpr int CK = 1 << K;              // amplitudes of a group
+    constexpr int KR = 2 * CK;              // real columns = 2 * 2^K
     constexpr int N = KR;                   // output columns
     constexpr int T = K + 7;                // 128 groups per tile
     constexpr uint32_t TS = 1u << T;
-    constexpr uint32_t OPB = 8u << T;       // operand bytes (A_hi, A_lo, tile)
+    constexpr uint32_t OPB = 8u << T;       // tile / operand bytes
     constexpr uint32_t BB = (uint32_t)N * KR * 4u;
-    constexpr int PER = TS / kSlotThreads;  // amplitudes per thread
-    constexpr uint32_t TCOLS = NS * N <= 32 ? 32 : NS * N <= 64 ? 64 : NS * N <= 128 ? 128 : 256;
+    // tensor memory per slot: the accumulator (N columns), then A_lo (KR columns)
+    constexpr uint32_t SCOLS = N + KR;
+    constexpr uint32_t TCOLS = NS * SCOLS <= 128 ? 128 : NS * SCOLS <= 256 ? 256 : 512;
+    static_assert(NS * SCOLS <= 512, "tensor memory");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *s_bhi = smem_raw;
     unsigned char *s_blo = smem_raw + BB;
     __shared__ __align__(8) uint64_t bar_ld[NS], bar_mma[NS], bar_b;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_hb[kMaxHTC];     // the high tile bits, indexed at run time
-    __shared__ uint32_t s_wsp[T];     // local bit b of a tile index -> its byte weight in the operand layout
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
     const uint32_t run_bytes = 8u << L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = threadIdx.x / kSlotThreads, st = threadIdx.x % kSlotThreads, ws = st >> 5;
     const uint32_t bar_id = 1u + (uint32_t)slot;  // named barrier of the slot (0 is __syncthreads)
-    unsigned char *s_tile = smem_raw + 2 * BB + (size_t)slot * 2 * OPB;  // loaded tile, then A_lo
+    unsigned char *s_tile = smem_raw + 2 * BB + (size_t)slot * 2 * OPB;  // the fetched tile
     unsigned char *s_ahi = s_tile + OPB;                                // A_hi, then the output tile
 
     if (threadIdx.x == 0) {  // (compile-time indices into the parameters: no local-memory copy)
 #pragma unroll
         for (int k = 0; k < kMaxHTC; k++) s_hb[k] = k < H ? g.hb[k] : 0;
-#pragma unroll
-        for (int r = 0; r < T - K; r++)  // row-index bit r: canon_off weight of m bit r
-            s_wsp[fm.row[r]] = r < 3 ? 16u << r : (uint32_t)(KR * 32) << (r - 3);
-#pragma unroll
-        for (int j = 0; j < K; j++)  // input column bit j: weight of kk bit j + 1 (kk = 2c)
-            s_wsp[fm.col[j]] = j == 0 ? 8u : 128u << (j - 1);
-    }
-    if (threadIdx.x == 0) {
         for (int i = 0; i < NS; i++) {
             mbar_init(&bar_ld[i], 1);
             mbar_init(&bar_mma[i], 1);
@@ -114,7 +110,8 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot + (uint32_t)(slot * N);  // the slot's accumulator columns
+    const uint32_t tmem_d = tmem_slot + (uint32_t)slot * SCOLS;  // the slot's accumulator
+    const uint32_t tmem_alo = tmem_d + N;                         // and its A_lo
 
     // B_hi, B_lo: 2 x BB bytes from global, once per CTA
     if (threadIdx.x == 0) {
@@ -126,23 +123,18 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     // leave its loop at the same barrier
     bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudgetTC)) != 0;
 
-    // Operand offsets are sums of per-bit weights: tile index i = st + 128 s
-    // splits into the thread's bits 0..6 and the step's bits 7..T-1.
-    uint32_t off_lo = 0, w_hi[K];
-#pragma unroll
-    for (int b = 0; b < 7; b++) off_lo += ((uint32_t)st >> b & 1u) * s_wsp[b];
-#pragma unroll
-    for (int b = 0; b < K; b++) w_hi[b] = s_wsp[7 + b];
-    // epilogue: this thread's group m = TMEM lane (32 ws + lane) and the
-    // tile bits of the gate's columns
+    // This thread owns group (row) m = its tensor-memory lane: the tile bits
+    // of m, and of the block's input / output columns.
+    const uint32_t m = (uint32_t)(32 * ws + lane);
     uint32_t ibase = 0, w_col[K];
-    {
-        const uint32_t m = (uint32_t)(32 * ws + lane);
 #pragma unroll
-        for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+    for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
 #pragma unroll
-        for (int b = 0; b < K; b++) w_col[b] = 1u << fm.col[b];
-    }
+    for (int b = 0; b < K; b++) w_col[b] = 1u << fm.col[b];
+    // byte offset of row m in the canonical K-major operand (see canon_off)
+    const uint32_t arow = (m & 7u) * 16u + (m >> 3) * (uint32_t)(KR * 32);
+    const uint32_t lane_off = (uint32_t)(32 * ws) << 16;  // tensor-memory lane field of this warp
+
     auto run_off = [&](uint32_t j) {  // offset of run j: its bits deposited at the high tile bits
         uint64_t o = 0;
         for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << s_hb[k];
@@ -164,9 +156,9 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     uint32_t ld_parity = 0, mma_parity = 0;
     const uint64_t stride = (uint64_t)gridDim.x * NS;
     uint64_t tile = (uint64_t)blockIdx.x * NS + slot;
-    // Pipeline of a slot: the next tile is fetched into the load buffer as
-    // soon as the MMAs have read A_lo out of it, so the fetch runs under this
-    // tile's epilogue and store; the store's reads of the output buffer are
+    // Pipeline of a slot: once every thread holds its group in registers the
+    // next tile is fetched into the load buffer, under this tile's split,
+    // MMAs, epilogue and store; the store's reads of the output buffer are
     // awaited only when the next split is about to overwrite it.
     if (ws == 0 && !aborted && tile < ntiles) issue_load(tile);
     for (; tile < ntiles && !aborted; tile += stride) {
@@ -178,38 +170,55 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
         }
         ld_parity ^= 1u;
 
-        // split into TF32 head / FP32 tail, scatter into the canonical layouts
-        float2 x[PER];
+        float2 x[CK];  // the group's amplitudes, input column c
 #pragma unroll
-        for (int s = 0; s < PER; s++) x[s] = tin[st + s * kSlotThreads];
-        if (ws == 0) bulk_wait_read_all();  // the previous store has read the output buffer
-        slot_sync(bar_id);                  // the tile buffer becomes A_lo, the output buffer A_hi
-#pragma unroll
-        for (int s = 0; s < PER; s++) {
-            uint32_t off = off_lo;
+        for (int c = 0; c < CK; c++) {
+            uint32_t i = ibase;
 #pragma unroll
             for (int b = 0; b < K; b++)
-                if ((s >> b) & 1) off += w_hi[b];
-            const float hr = to_tf32(x[s].x), hi_ = to_tf32(x[s].y);
-            *reinterpret_cast<float2 *>(s_ahi + off) = make_float2(hr, hi_);  // (re, im) share a 16-byte chunk
-            *reinterpret_cast<float2 *>(s_tile + off) = make_float2(x[s].x - hr, x[s].y - hi_);
+                if ((c >> b) & 1) i |= w_col[b];
+            x[c] = tin[i];
         }
+        if (ws == 0) bulk_wait_read_all();  // the previous store has read the output buffer
+        slot_sync(bar_id);
+        if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);  // the load buffer is free
+
+        // split x = hi (TF32) + lo: A_hi into the canonical K-major layout in
+        // shared memory (two amplitudes = one 16-byte chunk), A_lo into tensor
+        // memory (lane m, column 2c + re/im)
+#pragma unroll
+        for (int h = 0; h < CK / 16; h++) {
+            uint32_t lo[32];
+#pragma unroll
+            for (int cc = 0; cc < 16; cc += 2) {
+                const int c = 16 * h + cc;
+                const float4 hv = make_float4(to_tf32(x[c].x), to_tf32(x[c].y), to_tf32(x[c + 1].x),
+                                              to_tf32(x[c + 1].y));
+                *reinterpret_cast<float4 *>(s_ahi + arow + (uint32_t)(c >> 1) * 128u) = hv;
+                lo[2 * cc] = __float_as_uint(x[c].x - hv.x);
+                lo[2 * cc + 1] = __float_as_uint(x[c].y - hv.y);
+                lo[2 * cc + 2] = __float_as_uint(x[c + 1].x - hv.z);
+                lo[2 * cc + 3] = __float_as_uint(x[c + 1].y - hv.w);
+            }
+            tmem_st32(tmem_alo + lane_off + (uint32_t)(32 * h), lo);
+        }
+        tmem_st_wait();
         fence_proxy_async_smem();  // generic-proxy writes -> tensor-core (async proxy) reads
         tc_fence_before();
         slot_sync(bar_id);
         tc_fence_after();
 
         if (st == 0) {
-            const uint32_t ahi = smem_u32(s_ahi), alo = smem_u32(s_tile);
+            const uint32_t ahi = smem_u32(s_ahi);
             const uint32_t bhi = smem_u32(s_bhi), blo = smem_u32(s_blo);
             const uint32_t idesc = umma_idesc_tf32(128, N);
 #pragma unroll
             for (int ks = 0; ks < KR / 8; ks++) {
                 const uint32_t o = (uint32_t)ks * 256u;  // 8 TF32 along K = two core matrices
-                umma_tf32(tmem, umma_desc(alo + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc,
-                          ks > 0 ? 1u : 0u);
-                umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(blo + o, 128, KR * 32), idesc, 1u);
-                umma_tf32(tmem, umma_desc(ahi + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc, 1u);
+                umma_tf32_ts(tmem_d, tmem_alo + (uint32_t)(8 * ks), umma_desc(bhi + o, 128, KR * 32), idesc,
+                             ks > 0 ? 1u : 0u);
+                umma_tf32(tmem_d, umma_desc(ahi + o, 128, KR * 32), umma_desc(blo + o, 128, KR * 32), idesc, 1u);
+                umma_tf32(tmem_d, umma_desc(ahi + o, 128, KR * 32), umma_desc(bhi + o, 128, KR * 32), idesc, 1u);
             }
             umma_commit(&bar_mma[slot]);
         }
@@ -217,16 +226,14 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
         mma_parity ^= 1u;
         tc_fence_after();
         if (aborted) break;
-        // A_lo is consumed: fetch the next tile into the load buffer
-        if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);
 
-        // epilogue: warp ws reads TMEM lanes 32 ws .. +31 (its groups), 32
-        // columns (16 outputs) at a time
+        // epilogue: warp ws reads its 32 lanes (groups), 32 columns (16
+        // outputs) at a time, into the output buffer at the groups' positions
         float2 *tout = reinterpret_cast<float2 *>(s_ahi);
 #pragma unroll
         for (int chunk = 0; chunk < N / 32; chunk++) {
             uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * ws) << 16) + (uint32_t)(32 * chunk), r);
+            tmem_ld32(tmem_d + lane_off + (uint32_t)(32 * chunk), r);
             tmem_ld_wait();
             const uint32_t cb = (K == 5 && chunk) ? w_col[K - 1] : 0u;  // output bit 4 = the chunk
 #pragma unroll
