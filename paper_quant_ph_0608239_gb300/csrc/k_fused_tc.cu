@@ -51,6 +51,11 @@ template <int K> struct TcSlots;
 template <> struct TcSlots<4> { static constexpr int NS = 4; };  // 4 x 32 KiB + 8 KiB
 template <> struct TcSlots<5> { static constexpr int NS = 3; };  // 3 x 64 KiB + 32 KiB
 constexpr int kSlotThreads = 128;
+// Lane rotation against shared-memory bank conflicts (see the kernel).  It
+// pays for 4-qubit blocks (30-qubit random circuit: 612 -> 584 ms); for
+// 5-qubit blocks its register swaps cost more than the conflicts they remove
+// (432 -> 496 ms), so they run without it.
+template <int K> constexpr bool kRotate = (K == 4);
 
 __device__ __forceinline__ void slot_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 // OR of v over the slot's 128 threads (a barrier as well)
@@ -131,6 +136,32 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     for (int b = 0; b < T - K; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
 #pragma unroll
     for (int b = 0; b < K; b++) w_col[b] = 1u << fm.col[b];
+    // Lane rotation against bank conflicts: the 16 lanes of a half-warp read
+    // (and later write) 16 different 8-byte words of a bank row only if the
+    // tile bits 0..3 of their addresses differ.  A lane bit l < 4 whose row
+    // bit lies at tile bit >= 4 is paired with a gate column j at tile bit < 4
+    // (there are as many of each): the lane visits column c ^ rot at step c,
+    // rot = sum of (lane bit l) << j, and conditional swaps of register pairs
+    // undo the order.  rmask: the rotated column bits (the same for all lanes).
+    uint32_t rot = 0, rmask = 0;
+    if (kRotate<K>) {
+        uint32_t freecol = 0;  // gate columns at tile bits < 4 (the lowest j, col[] ascends)
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            if (fm.col[j] < 4) freecol |= 1u << j;
+#pragma unroll
+        for (int l = 0; l < 4; l++)
+            if (fm.row[l] >= 4 && freecol) {
+                const int j = __ffs(freecol) - 1;
+                freecol &= freecol - 1u;
+                rot |= (((uint32_t)lane >> l) & 1u) << j;
+                rmask |= 1u << j;
+            }
+    }
+    uint32_t rbase = ibase;  // the group's tile index with the rotated column bits set
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+        if ((rot >> b) & 1u) rbase |= w_col[b];
     // byte offset of row m in the canonical K-major operand (see canon_off)
     const uint32_t arow = (m & 7u) * 16u + (m >> 3) * (uint32_t)(KR * 32);
     const uint32_t lane_off = (uint32_t)(32 * ws) << 16;  // tensor-memory lane field of this warp
@@ -170,37 +201,62 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
         }
         ld_parity ^= 1u;
 
-        float2 x[CK];  // the group's amplitudes, input column c
+        // The group in parts of HS amplitudes: read (step c reads column
+        // c ^ rot), undo the rotation, split x = hi (TF32) + lo, A_hi into the
+        // canonical K-major layout in shared memory (two amplitudes = one
+        // 16-byte chunk), A_lo into tensor memory (lane m, column 2c + re/im).
+        // Once the last part is read the fetch buffer is free and the next
+        // tile's fetch starts.
+        constexpr int HS = kRotate<K> ? 16 : CK;  // the rotation's swaps want few live registers
 #pragma unroll
-        for (int c = 0; c < CK; c++) {
-            uint32_t i = ibase;
+        for (int p = 0; p < CK / HS; p++) {
+            float2 x[HS];  // input columns HS p .. HS p + HS - 1
 #pragma unroll
-            for (int b = 0; b < K; b++)
-                if ((c >> b) & 1) i |= w_col[b];
-            x[c] = tin[i];
-        }
-        if (ws == 0) bulk_wait_read_all();  // the previous store has read the output buffer
-        slot_sync(bar_id);
-        if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);  // the load buffer is free
-
-        // split x = hi (TF32) + lo: A_hi into the canonical K-major layout in
-        // shared memory (two amplitudes = one 16-byte chunk), A_lo into tensor
-        // memory (lane m, column 2c + re/im)
+            for (int c = 0; c < HS; c++) {
+                uint32_t i = rbase;
 #pragma unroll
-        for (int h = 0; h < CK / 16; h++) {
-            uint32_t lo[32];
-#pragma unroll
-            for (int cc = 0; cc < 16; cc += 2) {
-                const int c = 16 * h + cc;
-                const float4 hv = make_float4(to_tf32(x[c].x), to_tf32(x[c].y), to_tf32(x[c + 1].x),
-                                              to_tf32(x[c + 1].y));
-                *reinterpret_cast<float4 *>(s_ahi + arow + (uint32_t)(c >> 1) * 128u) = hv;
-                lo[2 * cc] = __float_as_uint(x[c].x - hv.x);
-                lo[2 * cc + 1] = __float_as_uint(x[c].y - hv.y);
-                lo[2 * cc + 2] = __float_as_uint(x[c + 1].x - hv.z);
-                lo[2 * cc + 3] = __float_as_uint(x[c + 1].y - hv.w);
+                for (int b = 0; b < K; b++)
+                    if (((HS * p + c) >> b) & 1) i ^= w_col[b];
+                x[c] = tin[i];
             }
-            tmem_st32(tmem_alo + lane_off + (uint32_t)(32 * h), lo);
+            if (kRotate<K>) {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if ((rmask >> j) & 1u) {
+                        const bool sw = (rot >> j) & 1u;
+#pragma unroll
+                        for (int c = 0; c < HS; c++)
+                            if (!((c >> j) & 1)) {
+                                const float2 u = x[c], v = x[c | (1 << j)];
+                                x[c] = sw ? v : u;
+                                x[c | (1 << j)] = sw ? u : v;
+                            }
+                    }
+            }
+            if (p == 0) {
+                if (ws == 0) bulk_wait_read_all();  // the previous store has read the output buffer
+                if (p < CK / HS - 1) slot_sync(bar_id);
+            }
+            if (p == CK / HS - 1) {
+                slot_sync(bar_id);
+                if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);  // the fetch buffer is free
+            }
+#pragma unroll
+            for (int h = 0; h < HS / 16; h++) {
+                uint32_t lo[32];
+#pragma unroll
+                for (int cc = 0; cc < 16; cc += 2) {
+                    const int e = 16 * h + cc, c = HS * p + e;
+                    const float4 hv = make_float4(to_tf32(x[e].x), to_tf32(x[e].y), to_tf32(x[e + 1].x),
+                                                  to_tf32(x[e + 1].y));
+                    *reinterpret_cast<float4 *>(s_ahi + arow + (uint32_t)(c >> 1) * 128u) = hv;
+                    lo[2 * cc] = __float_as_uint(x[e].x - hv.x);
+                    lo[2 * cc + 1] = __float_as_uint(x[e].y - hv.y);
+                    lo[2 * cc + 2] = __float_as_uint(x[e + 1].x - hv.z);
+                    lo[2 * cc + 3] = __float_as_uint(x[e + 1].y - hv.w);
+                }
+                tmem_st32(tmem_alo + lane_off + (uint32_t)(32 * (HS / 16 * p + h)), lo);
+            }
         }
         tmem_st_wait();
         fence_proxy_async_smem();  // generic-proxy writes -> tensor-core (async proxy) reads
@@ -235,13 +291,28 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
             uint32_t r[32];
             tmem_ld32(tmem_d + lane_off + (uint32_t)(32 * chunk), r);
             tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 4; j++)  // output q of the chunk -> register pair q ^ rot
+                if (kRotate<K> && ((rmask >> j) & 1u)) {
+                    const bool sw = (rot >> j) & 1u;
+#pragma unroll
+                    for (int q = 0; q < 16; q++)
+                        if (!((q >> j) & 1)) {
+                            const int p = q | (1 << j);
+                            const uint32_t u0 = r[2 * q], u1 = r[2 * q + 1], v0 = r[2 * p], v1 = r[2 * p + 1];
+                            r[2 * q] = sw ? v0 : u0;
+                            r[2 * q + 1] = sw ? v1 : u1;
+                            r[2 * p] = sw ? u0 : v0;
+                            r[2 * p + 1] = sw ? u1 : v1;
+                        }
+                }
             const uint32_t cb = (K == 5 && chunk) ? w_col[K - 1] : 0u;  // output bit 4 = the chunk
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                uint32_t i = ibase | cb;
+            for (int q = 0; q < 16; q++) {  // step q writes output q ^ rot
+                uint32_t i = rbase | cb;
 #pragma unroll
                 for (int b = 0; b < 4; b++)
-                    if ((q >> b) & 1) i |= w_col[b];
+                    if ((q >> b) & 1) i ^= w_col[b];
                 tout[i] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
             }
         }
