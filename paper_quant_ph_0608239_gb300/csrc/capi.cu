@@ -419,7 +419,20 @@ static qsim_status upload_program(qsim_state *h, const Plan &plan) {
 
 static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *d_ops, const TilePhase *d_phases) {
     const double pass_bytes = 2.0 * (double)state_bytes(h);
-    for (const PassPlan &pp : plan.passes) {
+    // complex128: the state stays in double-float form in HBM from the first
+    // arithmetic pass to the last one of this run (only those two convert);
+    // every pass of a complex128 plan runs in k_tile_df.  A run that fails
+    // part-way leaves the state unspecified, as any failed run does.
+    int last_arith = -1;
+    bool df_carry = h->dt == QSIM_C128;
+    for (size_t i = 0; i < plan.passes.size(); i++) {
+        const PassPlan &pp = plan.passes[i];
+        if (pp.phase_count > 0) df_carry = false;
+        if (pp.phase_count == 0 && pp.op_count > 0 && pp.arith) last_arith = (int)i;
+    }
+    bool in_df = false;  // the state is in double-float form now
+    for (size_t pi = 0; pi < plan.passes.size(); pi++) {
+        const PassPlan &pp = plan.passes[pi];
         if (pp.phase_count > 0) {
             CK(launch(h, F_TILE, pass_bytes, 1,
                       [&] {
@@ -433,13 +446,17 @@ static qsim_status launch_passes(qsim_state *h, const Plan &plan, const TileOp *
         }
         if (pp.op_count == 0) continue;
         if (h->dt == QSIM_C128) {
+            const bool cvt_in = pp.arith && !in_df;
+            const bool cvt_out = pp.arith && (!df_carry || (int)pi == last_arith);
             CK(launch(h, F_TILE, pass_bytes, 1,
                       [&] {
-                          return launch_tile_pass_df(h->amp, pp.geom, d_ops + pp.op_begin, pp.op_count, pp.arith,
-                                                     h->d_err, h->sm_count, h->stream);
+                          return launch_tile_pass_df(h->amp, pp.geom, d_ops + pp.op_begin, pp.op_count - pp.nglob,
+                                                     pp.nglob, pp.absorber, cvt_in, cvt_out, h->d_err, h->sm_count,
+                                                     h->stream);
                       },
                       pp.flops),
                "double-float tile pass");
+            if (pp.arith) in_df = !cvt_out;
             continue;
         }
         CK(launch(h, F_TILE, pass_bytes, 1,
@@ -567,7 +584,12 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     }
     int T, L, RB;
     tile_defaults(h, &o, T, L, RB);
-    plan_tiles(pg, h->n, T, L, P.plan, RB);
+    // register passes stay within the staged-program capacity of k_tile2
+    plan_tiles(pg, h->n, T, L, P.plan, RB, RB ? kRegMaxOps : 0, RB ? kRegMaxPhases : 0);
+    if (h->dt == QSIM_C128) {
+        defer_butterflies(P.plan);
+        hoist_global_diagonals(P.plan);
+    }
     for (const PassPlan &pp : P.plan.passes)
         if (pp.op_count || pp.phase_count) P.stats.passes++;
     P.stats.ops = (int)P.plan.ops.size();
@@ -1273,7 +1295,7 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
         Plan plan;
         // 12-bit tiles of complex64 circuits run the register program
         const int RB = (T == 12 && tile2_supported(0, T)) ? kBatchRB : 0;
-        plan_tiles(pg, h->n, T, L, plan, RB);
+        plan_tiles(pg, h->n, T, L, plan, RB, kRegMaxOps, kRegMaxPhases);  // k_batch stages every pass
         circs[i].amp = h->amp;
         circs[i].x0 = cs[i].x0;
         circs[i].pass_begin = (int32_t)passes.size();
@@ -1286,6 +1308,8 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
             plan.passes.push_back(pp);
         }
         for (const PassPlan &pp : plan.passes) {
+            if (pp.op_count > kRegMaxOps || pp.phase_count > kRegMaxPhases)  // the planner's cap guarantees this
+                return fail(QSIM_EUNSUPPORTED, "circuit %zu: a pass exceeds the staged program capacity", i);
             alg_bytes += 2.0 * (double)state_bytes(h);  // each pass reads and writes the state once
             alg_flops += pp.flops;
             BatchPass bp{};

@@ -30,8 +30,8 @@ constexpr int kThreadsB = 256;
 constexpr int kMaxHB = 10;
 constexpr int kMaxTB = 12;                            // tiles of at most 2^12 amplitudes
 constexpr int kLoadIt = (1 << kMaxTB) / kThreadsB;    // amplitudes a thread loads per tile
-constexpr int kStageOpsB = 64;                        // ops of one pass staged in shared memory (12 KiB)
-constexpr int kStagePhB = 32;                         // phases of one pass staged (1.4 KiB)
+constexpr int kStageOpsB = kRegMaxOps;                // ops of one pass staged in shared memory (12 KiB)
+constexpr int kStagePhB = kRegMaxPhases;              // phases of one pass staged (1.4 KiB)
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
         const int L = g.L, H = g.H, T = L + H;
         const uint32_t TS = 1u << T, lowmask = (1u << L) - 1u;
         const uint32_t pass_id = (uint32_t)(c.pass_begin + item.pass);
-        const bool ops_staged = ps.op_count <= kStageOpsB, ph_staged = ps.phase_count <= kStagePhB;
+        // (the host checked that every pass fits the staged copies)
         if (pass_id != staged_pass) {
             // (the previous item ended with a barrier: nobody reads the old copies)
             for (uint32_t j = threadIdx.x; j < (1u << H); j += blockDim.x) {
@@ -100,13 +100,13 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
                 for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << g.hb[k];
                 runoff[j] = o;
             }
-            if (ops_staged) {
+            {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(ops + ps.op_begin);
                 uint32_t *dst = reinterpret_cast<uint32_t *>(s_ops);
                 for (uint32_t w = threadIdx.x; w < (uint32_t)ps.op_count * (sizeof(TileOp) / 4); w += blockDim.x)
                     dst[w] = src[w];
             }
-            if (ph_staged) {
+            {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(phases + ps.phase_begin);
                 uint32_t *dst = reinterpret_cast<uint32_t *>(s_ph);
                 for (uint32_t w = threadIdx.x; w < (uint32_t)ps.phase_count * (sizeof(TilePhase) / 4); w += blockDim.x)
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
             }
             staged_pass = pass_id;
         }
-        // ops indexed by their position in the batch's op array
-        const TileOp *ops_p = ops_staged ? s_ops - ps.op_begin : ops;
+        // ops indexed by their position in the batch's op array (shared-memory copies only)
+        const TileOp *ops_p = s_ops - ps.op_begin;
         uint64_t base = (uint64_t)item.tile << L;
         for (int k = 0; k < H; k++) base = insert_zero(base, g.hb[k]);
         __syncthreads();
@@ -144,8 +144,7 @@ __global__ void __launch_bounds__(kThreadsB, 3) k_batch(const BatchCircuit *__re
         if (ps.phase_count > 0) {
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             for (int p = 0; p < ps.phase_count; p++)
-                t2::run_phase<false, kBatchRB>(t, ph_staged ? s_ph[p] : phases[ps.phase_begin + p], ops_p, base, lane,
-                                               warp, 1, 1);
+                t2::run_phase<false, kBatchRB>(t, s_ph[p], ops_p, base, lane, warp, 1, 1);
         } else {
             for (int o = ps.op_begin; o < ps.op_begin + ps.op_count; o++) {
                 tile_apply_op<float>(t, T, ops_p[o], base, nullptr);

@@ -35,8 +35,6 @@ constexpr int kMaxH2 = 10;
 constexpr int kMaxCopyShift2 = 14;
 constexpr long long kWaitBudget2 = 4000000000ll;
 
-constexpr int kMaxStagedOps = 96;     // ops of a pass copied to shared memory (18 KiB)
-constexpr int kMaxStagedPhases = 48;  // phases of a pass copied to shared memory (2.25 KiB)
 #ifndef QSIM_T2_MINB
 #define QSIM_T2_MINB (QSIM_T2_NWB == 4 ? 2 : 3)
 #endif
@@ -62,26 +60,23 @@ __global__ void __launch_bounds__(kThreads2, kMinBlocks2)
     const uint32_t ncopies = nruns << sub_shift;
     const uint32_t copy_bytes = 1u << (sub_L + amp_shift);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // the pass's ops, read by every thread for every tile: staged in shared
-    // memory after the tile when they fit (phases index them from op_base)
+    // the pass's ops and phases, read by every thread for every tile: copied
+    // to shared memory after the tile (the planner keeps a pass within
+    // kRegMaxOps / kRegMaxPhases), so the op reads of the gate program are
+    // shared-memory loads; phases index the ops from op_base
     TileOp *ops_s = reinterpret_cast<TileOp *>(smem_raw + (sizeof(S) << T));
-    const bool staged = op_count <= kMaxStagedOps;
-    if (staged) {
+    {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(ops_g + op_base);
         uint32_t *dst = reinterpret_cast<uint32_t *>(ops_s);
         for (uint32_t w = threadIdx.x; w < (uint32_t)op_count * (sizeof(TileOp) / 4); w += blockDim.x) dst[w] = src[w];
     }
-    const TileOp *ops = staged ? ops_s - op_base : ops_g;
-    // likewise the phases, after the staged ops
-    TilePhase *phases_s =
-        reinterpret_cast<TilePhase *>(smem_raw + (sizeof(S) << T) + (staged ? (size_t)op_count * sizeof(TileOp) : 0));
-    const bool pstaged = nphases <= kMaxStagedPhases;
-    if (pstaged) {
+    const TileOp *ops = ops_s - op_base;
+    TilePhase *phases = reinterpret_cast<TilePhase *>(smem_raw + (sizeof(S) << T) + (size_t)op_count * sizeof(TileOp));
+    {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(phases_g);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(phases_s);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(phases);
         for (uint32_t w = threadIdx.x; w < (uint32_t)nphases * (sizeof(TilePhase) / 4); w += blockDim.x) dst[w] = src[w];
     }
-    const TilePhase *phases = pstaged ? phases_s : phases_g;
     __shared__ int s_hb[kMaxH2];  // the high tile bits, indexed at run time
     if (threadIdx.x < kMaxH2) s_hb[threadIdx.x] = threadIdx.x < (unsigned)H ? g.hb[threadIdx.x] : 0;
 
@@ -147,8 +142,8 @@ cudaError_t launch2(void *amp, const TileGeom &g, const TilePhase *phases, int n
                     int op_base, int op_count, uint32_t *err, int sm_count, cudaStream_t s) {
     using S = typename t2::AmpT<C128>::S;
     const int T = g.L + g.H;
-    const size_t smem = (sizeof(S) << T) + (op_count <= kMaxStagedOps ? (size_t)op_count * sizeof(TileOp) : 0) +
-                        (nphases <= kMaxStagedPhases ? (size_t)nphases * sizeof(TilePhase) : 0);
+    if (op_count > kRegMaxOps || nphases > kRegMaxPhases) return cudaErrorInvalidValue;
+    const size_t smem = (sizeof(S) << T) + (size_t)op_count * sizeof(TileOp) + (size_t)nphases * sizeof(TilePhase);
     const uint64_t ntiles = 1ull << (g.n - T);
     int per_sm = (int)((220u * 1024u) / (smem + 9u * 1024u));
     if (per_sm < 1) per_sm = 1;

@@ -6,9 +6,17 @@
 // memory in double-float arithmetic (df64.cuh) instead of FP64: GB300 runs
 // FP64 at about 1/58 of its FP32 rate.  After the tile lands it is converted
 // in place from IEEE double to double-float (two floats per real, integer
-// operations only); before it is stored it is converted back.  A pass whose
-// ops only move data (bit flips, SWAP gates, interchanges) skips both
-// conversions and stays bit-exact.
+// operations only); before it is stored it is converted back.  Within one
+// run of a plan the state stays in double-float form in HBM between two
+// arithmetic passes (same 16 bytes per amplitude: re.h, re.l, im.h, im.l), so
+// only the first arithmetic pass converts on load and only the last converts
+// on store.  A pass whose ops only move data (bit flips, SWAP gates,
+// interchanges) moves 16-byte amplitudes in either form and stays bit-exact.
+//
+// Uncontrolled Hadamard-type gates s*[[1,1],[1,-1]] arrive from the planner
+// as unscaled butterflies (a0 + a1, a0 - a1): the product of their factors s
+// is folded into one other op of the same pass that touches every amplitude
+// once (the planner's choice), which is exact as every op is linear.
 //
 // Each op is one sweep over the tile's pairs in shared memory, with the
 // target bit a runtime value, so one compact code path serves every target
@@ -36,12 +44,15 @@ __device__ __forceinline__ uint32_t ins0d(uint32_t i, int pos) {
     return ((i >> pos) << (pos + 1)) | (i & ((1u << pos) - 1u));
 }
 
-__device__ __forceinline__ dcx ldx(const float4 *t, uint32_t i) {
-    const float4 f = t[i];
+// The tile is addressed by its shared-window address t (16 bytes per amplitude).
+__device__ __forceinline__ float4 ld4(uint32_t t, uint32_t i) { return lds128(t + (i << 4)); }
+__device__ __forceinline__ void st4(uint32_t t, uint32_t i, float4 v) { sts128(t + (i << 4), v); }
+__device__ __forceinline__ dcx ldx(uint32_t t, uint32_t i) {
+    const float4 f = ld4(t, i);
     return dcx{df{f.x, f.y}, df{f.z, f.w}};
 }
-__device__ __forceinline__ void stx(float4 *t, uint32_t i, const dcx &v) {
-    t[i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+__device__ __forceinline__ void stx(uint32_t t, uint32_t i, const dcx &v) {
+    st4(t, i, make_float4(v.re.h, v.re.l, v.im.h, v.im.l));
 }
 // An op as staged in shared memory: every thread reads every op of the pass
 // for every tile, so the pass's ops are copied once (or once per chunk) per
@@ -55,20 +66,21 @@ struct __align__(16) DfOp {
 static_assert(sizeof(DfOp) == 80, "DfOp layout");
 constexpr int kStageDF = 40;  // ops per staged chunk (3.1 KiB)
 
-__device__ __forceinline__ void stage_df(DfOp *dst, const TileOp *src, int cn) {
-    for (int k = threadIdx.x; k < cn; k += blockDim.x) {
-        const TileOp &op = src[k];
-        DfOp d;
+__device__ __forceinline__ DfOp to_dfop(const TileOp &op) {
+    DfOp d;
 #pragma unroll
-        for (int j = 0; j < 4; j++) d.c[j] = make_float4(op.uh[2 * j], op.ul[2 * j], op.uh[2 * j + 1], op.ul[2 * j + 1]);
-        d.gcmask = op.gcmask;
-        d.lcmask = op.lcmask;
-        d.kind = (uint8_t)op.kind;
-        d.tl = (uint8_t)op.tl;
-        d.pk = (uint8_t)op.pk;
-        d.tl2 = (uint8_t)op.tl2;
-        dst[k] = d;
-    }
+    for (int j = 0; j < 4; j++) d.c[j] = make_float4(op.uh[2 * j], op.ul[2 * j], op.uh[2 * j + 1], op.ul[2 * j + 1]);
+    d.gcmask = op.gcmask;
+    d.lcmask = op.lcmask;
+    d.kind = (uint8_t)op.kind;
+    d.tl = (uint8_t)op.tl;
+    d.pk = (uint8_t)op.pk;
+    d.tl2 = (uint8_t)op.tl2;
+    return d;
+}
+
+__device__ __forceinline__ void stage_df(DfOp *dst, const TileOp *src, int cn) {
+    for (int k = threadIdx.x; k < cn; k += blockDim.x) dst[k] = to_dfop(src[k]);
 }
 
 __device__ __forceinline__ dcx coefx(const DfOp &op, int k) {
@@ -90,7 +102,7 @@ __device__ __forceinline__ uint32_t expand_fixed(uint32_t p, uint32_t fixed) {
 // permutation's bit list).  An op enumerates only the amplitudes its local
 // controls select (the control bits fixed at 1), so a gate with c controls
 // costs 2^-c of a sweep.
-__device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, uint64_t base) {
+__device__ void apply_df(uint32_t t, int T, const DfOp &op, const TileOp &gop, uint64_t base) {
     if ((base & op.gcmask) != op.gcmask) return;
     const uint32_t lc = op.lcmask;
     const uint32_t TS = 1u << T;
@@ -107,9 +119,9 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
             for (uint32_t p = threadIdx.x; p < npair; p += blockDim.x) {
                 const uint32_t i0 = pair0(p);
                 const uint32_t i1 = i0 | bt;
-                const float4 x = t[i0];
-                t[i0] = t[i1];
-                t[i1] = x;
+                const float4 x = ld4(t, i0), y = ld4(t, i1);
+                st4(t, i0, y);
+                st4(t, i1, x);
             }
             return;
         }
@@ -133,6 +145,14 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
 #pragma unroll
                 for (int k = 0; k < kPairIt; k++) {
                     const dcx x0 = dcx_mul2(u0, va[k], u1, vb[k]), x1 = dcx_mul2(u2, va[k], u3, vb[k]);
+                    va[k] = x0;
+                    vb[k] = x1;
+                }
+            } else if (pk == 4) {  // unscaled butterfly: (a0 + a1, a0 - a1)
+#pragma unroll
+                for (int k = 0; k < kPairIt; k++) {
+                    const dcx x0{df_add(va[k].re, vb[k].re), df_add(va[k].im, vb[k].im)};
+                    const dcx x1{df_add(va[k].re, df_neg(vb[k].re)), df_add(va[k].im, df_neg(vb[k].im))};
                     va[k] = x0;
                     vb[k] = x1;
                 }
@@ -180,9 +200,9 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
         for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
             if (!(i & b0) || (i & b1) || (i & lc) != lc) continue;
             const uint32_t j = (i & ~b0) | b1;
-            const float4 x = t[i];
-            t[i] = t[j];
-            t[j] = x;
+            const float4 x = ld4(t, i), y = ld4(t, j);
+            st4(t, i, y);
+            st4(t, j, x);
         }
     } else if (kind == TOP_PERM) {
         const int nperm = gop.nperm;
@@ -194,22 +214,55 @@ __device__ void apply_df(float4 *t, int T, const DfOp &op, const TileOp &gop, ui
                 j |= (bl << gop.ph[k]) | (bh << gop.pl[k]);
             }
             if (j > i) {
-                const float4 x = t[i];
-                t[i] = t[j];
-                t[j] = x;
+                const float4 x = ld4(t, i), y = ld4(t, j);
+                st4(t, i, y);
+                st4(t, j, x);
             }
         }
     }
 }
 
+// The factor of the hoisted diagonal ops for the tile at `base` (each op
+// scales the tile by u00 or u11 by its bit, if its global controls are set),
+// and the absorber with its coefficients multiplied by it.  One thread.
+__device__ __noinline__ void tile_factor(const TileOp *ops, int nops, int nglob, int absorber, uint64_t base,
+                                        DfOp &abs_out, float4 &g_out, int &one_out) {
+    dcx g{df{1.0f, 0.0f}, df{0.0f, 0.0f}};
+    bool one = true;
+    for (int k = 0; k < nglob; k++) {
+        const TileOp &go = ops[nops + k];
+        if ((base & go.gcmask) != go.gcmask) continue;
+        const int c = ((base >> go.tl) & 1ull) ? 3 : 0;
+        const dcx f{df{go.uh[2 * c], go.ul[2 * c]}, df{go.uh[2 * c + 1], go.ul[2 * c + 1]}};
+        if (f.re.h == 1.0f && f.re.l == 0.0f && f.im.h == 0.0f && f.im.l == 0.0f) continue;
+        g = one ? f : dcx_mul(g, f);
+        one = false;
+    }
+    g_out = make_float4(g.re.h, g.re.l, g.im.h, g.im.l);
+    one_out = one ? 1 : 0;
+    if (absorber >= 0) {
+        DfOp d = to_dfop(ops[absorber]);
+        if (!one)
+            for (int j = 0; j < 4; j++) {
+                const dcx r = dcx_mul(g, coefx(d, j));
+                d.c[j] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
+            }
+        abs_out = d;
+    }
+}
+
 __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a, TileGeom g,
-                                                        const TileOp *__restrict__ ops, int nops, int convert,
-                                                        uint32_t *err, uint64_t ntiles) {
+                                                        const TileOp *__restrict__ ops, int nops, int nglob,
+                                                        int absorber, int cvt_in, int cvt_out, uint32_t *err,
+                                                        uint64_t ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double2 *t = reinterpret_cast<double2 *>(smem_raw);
-    float4 *tf = reinterpret_cast<float4 *>(smem_raw);
+    const uint32_t tf = smem_u32(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ DfOp s_ops[kStageDF];
+    __shared__ DfOp s_abs;          // the absorber with this tile's factor folded in
+    __shared__ float4 s_g;          // this tile's factor of the hoisted diagonals
+    __shared__ int s_gone;          // ... which is exactly 1
     __shared__ int abort_flag;
     const int L = g.L, H = g.H, T = L + H;
     uint64_t *runoff = reinterpret_cast<uint64_t *>(smem_raw + ((size_t)16 << T));  // 2^H entries
@@ -249,6 +302,7 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
                          copy_bytes, &bar);
             }
         }
+        if (nglob > 0 && threadIdx.x == 0) tile_factor(ops, nops, nglob, absorber, base, s_abs, s_g, s_gone);
         if (!mbar_wait_bounded(&bar, parity, kWaitBudgetDF)) {
             atomicExch(err, kErrTimeout);
             abort_flag = 1;
@@ -260,7 +314,7 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
         }
         parity ^= 1u;
 
-        if (convert) {
+        if (cvt_in) {
             for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
                 const double2 d = t[i];
                 stx(tf, i, dcx{df_from_double(d.x), df_from_double(d.y)});
@@ -274,11 +328,16 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
                 __syncthreads();
             }
             for (int o = 0; o < cn; o++) {
-                apply_df(tf, T, s_ops[o], ops[c0 + o], base);
+                apply_df(tf, T, c0 + o == absorber ? s_abs : s_ops[o], ops[c0 + o], base);
                 __syncthreads();
             }
         }
-        if (convert) {
+        if (nglob > 0 && absorber < 0 && !s_gone) {  // no absorber: one multiply of the tile
+            const dcx gf{df{s_g.x, s_g.y}, df{s_g.z, s_g.w}};
+            for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) stx(tf, i, dcx_mul(gf, ldx(tf, i)));
+            __syncthreads();
+        }
+        if (cvt_out) {
             for (uint32_t i = threadIdx.x; i < TS; i += blockDim.x) {
                 const dcx v = ldx(tf, i);
                 t[i] = make_double2(df_to_double(v.re), df_to_double(v.im));
@@ -303,10 +362,11 @@ __global__ void __launch_bounds__(kThreadsDF) k_tile_df(double2 *__restrict__ a,
 
 }  // namespace
 
-cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, bool convert,
-                                uint32_t *err, int sm_count, cudaStream_t s) {
+cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, int nglob, int absorber,
+                                bool cvt_in, bool cvt_out, uint32_t *err, int sm_count, cudaStream_t s) {
     const int T = g.L + g.H;
     if (g.H < 0 || g.H > kMaxHDF || T > g.n || T > 13 || g.L < 1) return cudaErrorInvalidValue;
+    if (nops < 0 || nglob < 0 || absorber >= nops) return cudaErrorInvalidValue;
     const size_t smem = ((size_t)16 << T) + ((size_t)8 << g.H);  // tile + run offsets
     const uint64_t ntiles = 1ull << (g.n - T);
     cudaError_t e = cudaFuncSetAttribute(k_tile_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -317,8 +377,8 @@ cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops,
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     uint64_t grid = (uint64_t)sm_count * per_sm;
     if (grid > ntiles) grid = ntiles;
-    k_tile_df<<<(unsigned)grid, kThreadsDF, smem, s>>>(static_cast<double2 *>(amp), g, ops, nops, convert ? 1 : 0,
-                                                      err, ntiles);
+    k_tile_df<<<(unsigned)grid, kThreadsDF, smem, s>>>(static_cast<double2 *>(amp), g, ops, nops, nglob, absorber,
+                                                      cvt_in ? 1 : 0, cvt_out ? 1 : 0, err, ntiles);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,13 @@ enum RegFamily : int {
 #endif
 constexpr int kRegWarpBits = QSIM_T2_NWB;
 
+// Capacity of the shared-memory copies of one register pass's program (ops
+// and phases) in k_tile2.cu and k_batch.cu.  The planner keeps every register
+// pass (and every pass of a batch) within it, so the kernels read ops and
+// phases from shared memory only.
+constexpr int kRegMaxOps = 64;
+constexpr int kRegMaxPhases = 32;
+
 // One phase of a register-blocked tile program: which local bits are held in
 // registers, the ops it applies, and an optional permutation of local bit
 // pairs applied when the phase stores back (quantum SWAP gates, interchanges).
@@ -158,10 +165,18 @@ cudaError_t launch_tile_pass(void *amp, int dt, const TileGeom &g, const TileOp 
 // are the physical bits 0..4).
 bool tile2_supported(int dt, int T);
 
-// complex128 tile pass in double-float arithmetic (k_tile_df.cu); convert =
-// false for passes that only move data (kept bit-exact).
-cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, bool convert,
-                                uint32_t *err, int sm_count, cudaStream_t s);
+// complex128 tile pass in double-float arithmetic (k_tile_df.cu).  cvt_in:
+// the tile arrives as IEEE doubles and is converted after the load; cvt_out:
+// it is converted back to IEEE doubles before the store.  Without them the
+// pass reads / writes the double-float form (re.h, re.l, im.h, im.l), which a
+// run keeps in HBM between its arithmetic passes.  Passes that only move data
+// take neither (bit-exact in either form).  Ops with pk == 4 are unscaled
+// butterflies (a0 + a1, a0 - a1), see defer_butterflies().  ops[0, nops) is
+// the program; ops[nops, nops + nglob) are diagonal ops on bits outside the
+// tile, multiplied into one factor per tile and folded into the coefficients
+// of program op `absorber` (or, if absorber < 0, applied as one multiply).
+cudaError_t launch_tile_pass_df(void *amp, const TileGeom &g, const TileOp *ops, int nops, int nglob, int absorber,
+                                bool cvt_in, bool cvt_out, uint32_t *err, int sm_count, cudaStream_t s);
 // ops: the plan's op array; the pass's phases use ops[op_base, op_base + op_count).
 cudaError_t launch_tile_pass2(void *amp, int dt, const TileGeom &g, const TilePhase *phases, int nphases,
                               const TileOp *ops, int op_base, int op_count, uint32_t *err, int sm_count,

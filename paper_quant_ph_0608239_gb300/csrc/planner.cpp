@@ -2,6 +2,7 @@
 #include "planner.hpp"
 
 #include <algorithm>
+#include <iterator>
 #include <array>
 #include <cmath>
 #include <complex>
@@ -381,7 +382,8 @@ void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vecto
     }
 }
 
-void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB) {
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB, int max_ops,
+                int max_phases) {
     plan.passes.clear();
     plan.ops.clear();
     plan.dense.clear();
@@ -449,17 +451,49 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
         int j = 0;
         for (int b = 0; b < 64; b++)
             if ((hmask >> b) & 1ull) pp.geom.hb[j++] = b;
-        pp.flops = 0.0;
-        for (int gi : sched) pp.flops += gate_flops(gates[gi], n);
         std::vector<TileOp> pass_ops;
         for (int gi : sched) {
             TileOp op;
             make_tile_op(gates[gi], pp.geom, op);  // fits by construction
             pass_ops.push_back(op);
         }
+        const bool reg = RB > 0 && L + hcount == RB + 5 + kRegWarpBits && L >= 5;
+        // keep the pass within the program capacity: the largest prefix of
+        // its gates that fits; the others return to the remaining list
+        size_t take = sched.size();
+        std::vector<TileOp> rops;
+        std::vector<TilePhase> rph;
+        for (;;) {
+            size_t nops = take, nph = 0;
+            if (reg) {
+                rops.clear();
+                rph.clear();
+                build_phases(std::vector<TileOp>(pass_ops.begin(), pass_ops.begin() + take), L + hcount, RB, rops,
+                             rph);
+                nops = rops.size();
+                nph = rph.size();
+            }
+            const size_t over_o = (max_ops > 0 && nops > (size_t)max_ops) ? nops - (size_t)max_ops : 0;
+            const size_t over_p = (max_phases > 0 && nph > (size_t)max_phases) ? nph - (size_t)max_phases : 0;
+            if ((!over_o && !over_p) || take <= 1) break;
+            const size_t cut = over_o > over_p ? over_o : over_p;
+            take = cut < take ? take - cut : 1;
+        }
+        if (take < sched.size()) {
+            // the dropped gates commute with the skipped ones before them, so
+            // merging both back in program order keeps the circuit
+            std::vector<int> merged;
+            merged.reserve(rest.size() + sched.size() - take);
+            std::merge(sched.begin() + take, sched.end(), rest.begin(), rest.end(), std::back_inserter(merged));
+            rest.swap(merged);
+            sched.resize(take);
+            pass_ops.resize(take);
+        }
+        pp.flops = 0.0;
+        for (int gi : sched) pp.flops += gate_flops(gates[gi], n);
         pp.op_begin = (int)plan.ops.size();
         pp.phase_begin = (int)plan.phases.size();
-        if (RB > 0 && L + hcount == RB + 5 + kRegWarpBits && L >= 5) {
+        if (reg) {
             build_phases(pass_ops, L + hcount, RB, plan.ops, plan.phases);
         } else {
             plan.ops.insert(plan.ops.end(), pass_ops.begin(), pass_ops.end());
@@ -471,6 +505,87 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
             if (gates[gi].kind != QSIM_GATE_SWAP && gates[gi].gc != GC_EXCHANGE) pp.arith = true;
         plan.passes.push_back(pp);
         remaining.swap(rest);
+    }
+}
+
+namespace {
+
+// s if U = s * [[1, 1], [1, -1]] exactly (real s != 0), else 0.
+double hadamard_factor(const double (&u)[8]) {
+    const double s = u[0];
+    if (s == 0.0 || u[1] != 0.0 || u[3] != 0.0 || u[5] != 0.0 || u[7] != 0.0) return 0.0;
+    if (u[2] != s || u[4] != s || u[6] != -s) return 0.0;
+    return s;
+}
+
+void scale_op(TileOp &op, double f) {
+    for (int k = 0; k < 8; k++) {
+        op.u[k] *= f;
+        op.uh[k] = (float)op.u[k];
+        op.ul[k] = (float)(op.u[k] - (double)op.uh[k]);
+    }
+}
+
+}  // namespace
+
+void defer_butterflies(Plan &plan) {
+    for (PassPlan &pp : plan.passes) {
+        if (pp.phase_count > 0 || pp.op_count == 0) continue;
+        TileOp *ops = plan.ops.data() + pp.op_begin;
+        std::vector<int> bf;
+        int absorber = -1;
+        double S = 1.0;
+        for (int i = 0; i < pp.op_count; i++) {
+            TileOp &op = ops[i];
+            if (op.lcmask != 0 || op.gcmask != 0) continue;  // controlled: touches a subset
+            const double s = op.kind == TOP_GENERAL ? hadamard_factor(op.u) : 0.0;
+            if (s != 0.0 && (int)bf.size() < kMaxDeferred) {
+                bf.push_back(i);
+                S *= s;
+            } else if (absorber < 0 && (op.kind == TOP_GENERAL || op.kind == TOP_ANTIDIAG || op.kind == TOP_DIAG ||
+                                        op.kind == TOP_DIAG_G)) {
+                absorber = i;
+            }
+        }
+        if (bf.empty()) continue;
+        if (absorber < 0) {  // one Hadamard-type op takes the whole factor
+            absorber = bf.back();
+            bf.pop_back();
+            if (bf.empty()) continue;  // a single one: nothing to defer
+            scale_op(ops[absorber], S / ops[absorber].u[0]);
+        } else {
+            scale_op(ops[absorber], S);
+        }
+        for (int i : bf) {
+            ops[i].pk = 4;
+            scale_op(ops[i], 1.0 / ops[i].u[0]);  // the entries read +-1 (unused by the kernel)
+        }
+    }
+}
+
+void hoist_global_diagonals(Plan &plan) {
+    for (PassPlan &pp : plan.passes) {
+        if (pp.phase_count > 0 || pp.op_count == 0) continue;
+        TileOp *ops = plan.ops.data() + pp.op_begin;
+        std::vector<TileOp> prog, glob;
+        for (int i = 0; i < pp.op_count; i++) {
+            if (ops[i].kind == TOP_DIAG_G && ops[i].lcmask == 0) glob.push_back(ops[i]);
+            else prog.push_back(ops[i]);
+        }
+        if (glob.empty()) continue;
+        pp.nglob = (int)glob.size();
+        pp.absorber = -1;
+        for (size_t i = 0; i < prog.size(); i++) {
+            const TileOp &op = prog[i];
+            if (op.lcmask != 0 || op.gcmask != 0) continue;
+            if ((op.kind == TOP_GENERAL && op.pk == 0) || op.kind == TOP_ANTIDIAG || op.kind == TOP_DIAG) {
+                pp.absorber = (int)i;
+                break;
+            }
+        }
+        int k = 0;
+        for (const TileOp &op : prog) ops[k++] = op;
+        for (const TileOp &op : glob) ops[k++] = op;
     }
 }
 

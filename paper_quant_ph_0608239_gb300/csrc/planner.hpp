@@ -38,6 +38,12 @@ struct PassPlan {
     int phase_begin, phase_count; // range in the plan's phase array (0 phases: shared-memory kernel)
     double flops;                 // algorithmic flops of the pass
     bool arith;                   // some op does arithmetic (not only data movement)
+    // complex128 shared-memory passes (hoist_global_diagonals): the last
+    // nglob ops of the range are diagonal ops on bits outside the tile, one
+    // factor per tile; absorber >= 0 names the op of the program whose
+    // coefficients take that factor each tile (else a separate multiply)
+    int nglob = 0;
+    int absorber = -1;
 };
 
 // Algorithmic real flops of one gate over an n-qubit state: 14 per amplitude
@@ -61,7 +67,30 @@ struct Plan {
 // RB > 0: cut each pass with T = RB + 5 + kRegWarpBits bits into register phases for the
 // register-blocked kernel (k_tile2.cu); passes that do not fit that shape
 // keep a flat op list for the shared-memory kernel (k_tile.cu).
-void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB = 0);
+// max_ops / max_phases > 0: a pass takes only as many of its gates (in order)
+// as keep its op list, and the phase list of a register pass, within them;
+// the rest go to later passes.
+void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan, int RB = 0, int max_ops = 0,
+                int max_phases = 0);
+
+// complex128 shared-memory passes (k_tile_df.cu): in every pass without
+// register phases, uncontrolled Hadamard-type ops s*[[1,1],[1,-1]] (at most
+// kMaxDeferred of them) become unscaled butterflies (pk = 4) and the product
+// of their factors s is folded into one op of the same pass that touches
+// every amplitude exactly once: an uncontrolled 2x2 pair op or diagonal, else
+// one of the Hadamard-type ops, which then keeps its real 2x2 form.
+constexpr int kMaxDeferred = 24;  // bounds the growth of the unscaled amplitudes to 2^12
+void defer_butterflies(Plan &plan);
+
+// complex128 shared-memory passes: every op that is diagonal on a bit outside
+// the tile and has no control inside it (TOP_DIAG_G, lcmask == 0) scales a
+// whole tile by one factor, and commutes with every op of the pass (no op of
+// a pass acts non-diagonally outside its tile).  They move to the end of the
+// pass's op range (nglob of them); the kernel multiplies them into one factor
+// per tile and folds it into the coefficients of one uncontrolled op that
+// touches every amplitude once and stays of its kind when scaled by a complex
+// number (dense 2x2, anti-diagonal or diagonal), the pass's absorber.
+void hoist_global_diagonals(Plan &plan);
 
 // Cut one pass's op list into register phases (see k_tile2.cu).
 void build_phases(const std::vector<TileOp> &pass_ops, int T, int RB, std::vector<TileOp> &ops_out,

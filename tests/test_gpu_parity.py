@@ -206,6 +206,46 @@ def test_long_pass_many_ops(q, dt):
     st.free()
 
 
+@pytest.mark.parametrize("absorber", [True, False])
+def test_c128_tile_pass_factor_folding(q, absorber):
+    # complex128 tile passes fold the factors of uncontrolled Hadamard gates
+    # and of phases on bits outside the tile into one op per pass: passes with
+    # such an op (dense SU(2) gates present) and without it (only H, phases and
+    # CNOTs), phases with controls inside and outside the tile
+    n, tile = 16, 8
+    rng = np.random.default_rng(2024 + absorber)
+    gates = []
+    for _layer in range(6):
+        for t in range(n):
+            k = int(rng.integers(3))
+            if k == 1:
+                gates.append(g1("R", t, (), (float(rng.uniform(0, 2 * math.pi)),)))
+            elif k == 2 and absorber:
+                gates.append(g1("SU2", t, (), PARAMS["SU2"]))
+            else:
+                gates.append(g1("H", t))
+        for _ in range(6):
+            a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+            gates.append(g1("R", a, (b,), (float(rng.uniform(0, 2 * math.pi)),)))
+        p = [int(x) for x in rng.permutation(n)]
+        for i in range(0, n, 2):
+            gates.append(g1("NOT", p[i + 1], (p[i],)))
+    psi = rand_state(n, 7 + absorber)
+    ref = oracle.run(n, gates, state=psi.copy())
+    got = run_gpu(q, n, "c128", gates, psi=psi, tile_bits=tile)
+    assert err(got, ref) < TOL["c128"]
+    # the same through a plan run twice (the state returns to IEEE doubles
+    # after every run)
+    st = q.State(n, "c128")
+    plan = st.plan(gates, tile_bits=tile)
+    for _ in range(2):
+        st.set_state(psi)
+        plan.run()
+        assert err(st.get_state(), ref) < TOL["c128"]
+    plan.free()
+    st.free()
+
+
 @pytest.mark.parametrize("dt", DTYPES)
 def test_autotuned_plan(q, dt):
     # QSIM_MODE_AUTO: each of the first runs uses another candidate (tile size,
