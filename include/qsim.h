@@ -51,7 +51,7 @@ typedef enum {
     QSIM_ENOMEM = 2,        /* device or pinned host allocation failed */
     QSIM_ECUDA = 3,         /* a CUDA call failed; see qsim_last_error() */
     QSIM_ETIMEOUT = 4,      /* a bounded device-side wait expired */
-    QSIM_EUNSUPPORTED = 5   /* valid request this build cannot serve */
+    QSIM_EUNSUPPORTED = 5   /* valid request the library cannot serve */
 } qsim_status;
 
 typedef enum {

@@ -152,3 +152,47 @@ def test_paper_circuits_exact(emu):
     got, _ = run_emu(emu, 2 * m, gates, psi, 12)
     assert int(np.argmax(np.abs(got))) == inputs.adder_expected_index(values, m)
     assert abs(np.max(np.abs(got)) - 1.0) < 1e-12
+
+
+# Plausible slips planted in a copy of the planner: each must make the
+# emulated programs disagree with the oracle (so the checks above can see them).
+PLANNER_MUTANTS = {
+    "absorber not scaled": ("            scale_op(ops[absorber], S);\n", "\n"),
+    "pass cut reorders gates": (
+        "std::merge(sched.begin() + take, sched.end(), rest.begin(), rest.end(), std::back_inserter(merged));",
+        "merged.insert(merged.end(), rest.begin(), rest.end()); "
+        "merged.insert(merged.end(), sched.begin() + take, sched.end());"),
+    "controlled phase hoisted": ("if (ops[i].kind == TOP_DIAG_G && ops[i].lcmask == 0) glob.push_back(ops[i]);",
+                                 "if (ops[i].kind == TOP_DIAG_G) glob.push_back(ops[i]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PLANNER_MUTANTS))
+def test_planner_mutants_are_caught(emu, name, tmp_path):
+    old, new = PLANNER_MUTANTS[name]
+    src = open(os.path.join(ROOT, "paper_quant_ph_0608239_gb300", "csrc", "planner.cpp")).read()
+    assert src.count(old) == 1, name
+    d = tmp_path / "pkg" / "csrc"  # the same relative layout as the package
+    d.mkdir(parents=True)
+    (tmp_path / "include").mkdir()
+    shutil.copy(os.path.join(ROOT, "include", "qsim.h"), tmp_path / "include" / "qsim.h")
+    for f in ("planner.hpp", "kernels.hpp"):
+        shutil.copy(os.path.join(ROOT, "paper_quant_ph_0608239_gb300", "csrc", f), d / f)
+    (d / "planner.cpp").write_text(src.replace(old, new))
+    emu_src = open(os.path.join(ROOT, "tests", "host", "plan_emu.cpp")).read().replace(
+        "../../paper_quant_ph_0608239_gb300/csrc/planner.hpp", str(d / "planner.hpp"))
+    (tmp_path / "plan_emu.cpp").write_text(emu_src)
+    exe = str(tmp_path / "mutant")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", CUDA_INC, "-I", os.path.join(ROOT, "include"), "-o", exe,
+                    str(tmp_path / "plan_emu.cpp"), str(d / "planner.cpp")], check=True)
+    n = 14
+    cases = [(layered_circuit(n, 5, 77), dict(T=10)),
+             (mixed_circuit(n, 150, 78) + layered_circuit(n, 3, 79),
+              dict(T=12, RB=4, c128=False, max_ops=5, max_phases=2))]
+    caught = False
+    for gates, kw in cases:
+        psi = rand_state(n, 5)
+        ref = oracle.run(n, gates, state=psi.copy())
+        got, _ = run_emu(exe, n, gates, psi, **kw)
+        caught |= float(np.max(np.abs(got - ref))) > 1e-9
+    assert caught, name
