@@ -401,6 +401,7 @@ def run_ours(args, w, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_companions and w["kind"] == "random":
         out["companions"] = companions(q, w, gates, x0, args)
         out["single_gate_sweeps"] = single_gate_sweeps(q)
+        out["qubit_interchange_sweeps"] = qubit_interchange_sweeps(q)
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, done, thr, note = oracle_sample(w, gates, x0, args.cpu_budget)
         out["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": thr, "kind": "oracle",
@@ -449,6 +450,49 @@ def single_gate_sweeps(q, n=30, targets=(0, 1, 2, 4, 8, 16, 29)):
         out[dt] = res
         st.free()
         torch.cuda.empty_cache()
+    return out
+
+
+def qubit_interchange_sweeps(q, n=30, Ks=(1, 2, 4)):
+    """The paper's qubit interchange (Sec. III.B: local bit l_i <-> nonlocal
+    bit h_i for i < K, Eqs. onequbitchange and twoqubitchange0-5) as one pass
+    over the state (qsim_permute_bits), timed with CUDA events: effective GB/s
+    per K.  Algorithmic bytes: 2 S 2^n per pass, 2 S 2^(n-1) for K = 1 (the
+    half whose two bits differ).  A failure is reported in place of a figure
+    and does not stop the run."""
+    import torch
+    hbm, _ = peaks()
+    out = {}
+    for dt in ("c64", "c128"):
+        S = 8 if dt == "c64" else 16
+        res = {}
+        st = None
+        try:
+            st = q.State(n, dt)
+            for K in Ks:
+                lo, hi = list(range(K)), [n - 1 - i for i in range(K)]
+                try:
+                    st.permute_bits(lo, hi)  # warm-up
+                    stream = torch.cuda.current_stream()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(4):
+                        st.permute_bits(lo, hi)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / 4
+                    moved = 0.5 if K == 1 else 1.0
+                    gbs = 2.0 * S * moved * (1 << n) / (ms / 1e3) / 1e9
+                    res[str(K)] = {"ms": round(ms, 3), "GBs": round(gbs, 1), "frac": round(gbs / hbm, 3)}
+                except Exception as e:  # noqa: BLE001 -- reported, not fatal
+                    res[str(K)] = {"error": str(e)[:200]}
+        except Exception as e:  # noqa: BLE001
+            res = {"error": str(e)[:200]}
+        finally:
+            if st is not None:
+                st.free()
+            torch.cuda.empty_cache()
+        out[dt] = res
     return out
 
 
