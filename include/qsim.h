@@ -206,7 +206,10 @@ QSIM_API qsim_status qsim_get_layout(qsim_handle h, int *phys);
 
 /* qsim_run_circuit: apply ng gates in order, as opts->mode says (NULL =
  * defaults).  The gate list is read during the call only.  On EINVAL (a bad
- * gate) nothing has been applied. */
+ * gate) nothing has been applied.  After any other error (ECUDA, ETIMEOUT)
+ * the state is unspecified: a complex128 run keeps the amplitudes in an
+ * internal double-float form between its first and last tile pass, and a
+ * run stopped in between leaves them so. */
 QSIM_API qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, const qsim_opts *opts);
 
 /* ---- plans: a circuit planned and uploaded once, run many times ------------
@@ -214,7 +217,8 @@ QSIM_API qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, siz
  * current qubit-to-bit map) and uploads the tile programs to device memory,
  * so that qsim_plan_run only enqueues kernels.  A plan may be run on any
  * handle with the same n, dtype and map; EINVAL otherwise.  qsim_plan_run
- * leaves the map unchanged. */
+ * leaves the map unchanged; after an error (ECUDA, ETIMEOUT) the state is
+ * unspecified, as for qsim_run_circuit. */
 typedef struct qsim_plan_s *qsim_plan;
 
 typedef struct {

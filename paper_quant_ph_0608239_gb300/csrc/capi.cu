@@ -588,6 +588,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     plan_tiles(pg, h->n, T, L, P.plan, RB, RB ? kRegMaxOps : 0, RB ? kRegMaxPhases : 0);
     if (h->dt == QSIM_C128) {
         defer_butterflies(P.plan);
+        merge_local_diagonals(P.plan);
         hoist_global_diagonals(P.plan);
     }
     for (const PassPlan &pp : P.plan.passes)

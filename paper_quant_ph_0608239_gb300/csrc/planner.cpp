@@ -528,6 +528,107 @@ void scale_op(TileOp &op, double f) {
 
 }  // namespace
 
+namespace {
+
+// The op acts non-diagonally on local bit b (moves or mixes amplitudes along b).
+bool mixes_bit(const TileOp &op, int b) {
+    switch (op.kind) {
+    case TOP_GENERAL:
+    case TOP_ANTIDIAG:
+    case TOP_EXCHANGE: return op.tl == b;
+    case TOP_SWAPGATE: return op.tl == b || op.tl2 == b;
+    case TOP_PERM:
+    case TOP_DENSE:
+        for (int k = 0; k < op.nperm; k++)
+            if (op.pl[k] == b || (op.kind == TOP_PERM && op.ph[k] == b)) return true;
+        return false;
+    default: return false;  // diagonal ops
+    }
+}
+
+bool uncontrolled(const TileOp &op) { return op.lcmask == 0 && op.gcmask == 0; }
+
+// Row-major complex 2x2 product C = A * B (interleaved re, im).
+void mat2_mul(const double (&A)[8], const double (&B)[8], double (&C)[8]) {
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < 2; k++) {
+                const double ar = A[2 * (2 * r + k)], ai = A[2 * (2 * r + k) + 1];
+                const double br = B[2 * (2 * k + c)], bi = B[2 * (2 * k + c) + 1];
+                re += ar * br - ai * bi;
+                im += ar * bi + ai * br;
+            }
+            C[2 * (2 * r + c)] = re;
+            C[2 * (2 * r + c) + 1] = im;
+        }
+}
+
+void set_matrix(TileOp &op, const double (&M)[8]) {
+    for (int k = 0; k < 8; k++) {
+        op.u[k] = M[k];
+        op.uh[k] = (float)M[k];
+        op.ul[k] = (float)(M[k] - (double)op.uh[k]);
+    }
+}
+
+// Can `d` (an uncontrolled diagonal on local bit b) be merged into `x`, an
+// uncontrolled op on the same bit that keeps its kind and cost: a dense
+// complex 2x2, or another phase / diagonal.
+bool merge_target(const TileOp &x, int b) {
+    if (!uncontrolled(x) || x.tl != b) return false;
+    if (x.kind == TOP_GENERAL) return x.pk == 0;
+    return x.kind == TOP_PHASE || x.kind == TOP_DIAG;
+}
+
+}  // namespace
+
+void merge_local_diagonals(Plan &plan) {
+    for (PassPlan &pp : plan.passes) {
+        if (pp.phase_count > 0 || pp.op_count < 2) continue;
+        std::vector<TileOp> ops(plan.ops.begin() + pp.op_begin, plan.ops.begin() + pp.op_begin + pp.op_count);
+        std::vector<bool> gone(ops.size(), false);
+        for (size_t i = 0; i < ops.size(); i++) {
+            TileOp &d = ops[i];
+            if ((d.kind != TOP_PHASE && d.kind != TOP_DIAG) || !uncontrolled(d)) continue;
+            const int b = d.tl;
+            int into = -1;
+            bool after = false;  // d is applied after ops[into]
+            for (int j = (int)i - 1; j >= 0; j--) {  // back to the last op on bit b
+                if (gone[j]) continue;
+                if (merge_target(ops[j], b)) {
+                    into = j;
+                    after = true;
+                    break;
+                }
+                if (mixes_bit(ops[j], b)) break;
+            }
+            if (into < 0)
+                for (size_t j = i + 1; j < ops.size(); j++) {  // forward to the next op on bit b
+                    if (merge_target(ops[j], b)) {
+                        into = (int)j;
+                        break;
+                    }
+                    if (mixes_bit(ops[j], b)) break;
+                }
+            if (into < 0) continue;
+            TileOp &x = ops[into];
+            double M[8];
+            if (after) mat2_mul(d.u, x.u, M);
+            else mat2_mul(x.u, d.u, M);
+            if (x.kind != TOP_GENERAL)  // diagonal times diagonal
+                x.kind = (x.kind == TOP_PHASE && d.kind == TOP_PHASE) ? TOP_PHASE : TOP_DIAG;
+            set_matrix(x, M);
+            gone[i] = true;
+        }
+        int k = 0;
+        for (size_t i = 0; i < ops.size(); i++)
+            if (!gone[i]) plan.ops[pp.op_begin + k++] = ops[i];
+        // the pass shrinks in place; the tail of its old range is unused
+        pp.op_count = k;
+    }
+}
+
 void defer_butterflies(Plan &plan) {
     for (PassPlan &pp : plan.passes) {
         if (pp.phase_count > 0 || pp.op_count == 0) continue;

@@ -82,6 +82,14 @@ void plan_tiles(const std::vector<PGate> &gates, int n, int T, int L, Plan &plan
 constexpr int kMaxDeferred = 24;  // bounds the growth of the unscaled amplitudes to 2^12
 void defer_butterflies(Plan &plan);
 
+// complex128 shared-memory passes (after defer_butterflies): an uncontrolled
+// phase or diagonal on a local bit b merges into the nearest uncontrolled op
+// on b before it (else after it) that keeps its kind and cost when multiplied
+// by it -- a dense complex 2x2, a phase or a diagonal -- provided no op in
+// between moves or mixes amplitudes along b (diagonal ops and controls on b
+// commute with it).  The merged op's FP64 matrix is the product.
+void merge_local_diagonals(Plan &plan);
+
 // complex128 shared-memory passes: every op that is diagonal on a bit outside
 // the tile and has no control inside it (TOP_DIAG_G, lcmask == 0) scales a
 // whole tile by one factor, and commutes with every op of the pass (no op of

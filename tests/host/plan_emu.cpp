@@ -136,6 +136,7 @@ int main() {
     plan_tiles(pg, n, T, L, plan, RB, max_ops, max_phases);
     if (c128) {
         defer_butterflies(plan);
+        merge_local_diagonals(plan);
         hoist_global_diagonals(plan);
     }
     int32_t stats[6] = {0, 0, 0, 0, 0, 0};

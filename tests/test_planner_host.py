@@ -164,6 +164,10 @@ PLANNER_MUTANTS = {
         "merged.insert(merged.end(), sched.begin() + take, sched.end());"),
     "controlled phase hoisted": ("if (ops[i].kind == TOP_DIAG_G && ops[i].lcmask == 0) glob.push_back(ops[i]);",
                                  "if (ops[i].kind == TOP_DIAG_G) glob.push_back(ops[i]);"),
+    "merged phase on the wrong side": ("if (after) mat2_mul(d.u, x.u, M);", "if (!after) mat2_mul(d.u, x.u, M);"),
+    "phase merged across a mixing op": ("after = true;\n                    break;\n                }\n"
+                                        "                if (mixes_bit(ops[j], b)) break;",
+                                        "after = true;\n                    break;\n                }"),
 }
 
 
