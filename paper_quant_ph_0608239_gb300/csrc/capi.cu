@@ -591,9 +591,11 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         merge_local_diagonals(P.plan);
         hoist_global_diagonals(P.plan);
     }
-    for (const PassPlan &pp : P.plan.passes)
+    P.stats.ops = 0;  // (a pass shrunk by merging leaves unused entries in the op array)
+    for (const PassPlan &pp : P.plan.passes) {
         if (pp.op_count || pp.phase_count) P.stats.passes++;
-    P.stats.ops = (int)P.plan.ops.size();
+        P.stats.ops += pp.op_count;
+    }
     P.stats.phases = (int)P.plan.phases.size();
     P.stats.tile_bits = P.plan.passes.empty() ? 0 : P.plan.passes[0].geom.L + P.plan.passes[0].geom.H;
     P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
