@@ -17,6 +17,10 @@
 // as unscaled butterflies (a0 + a1, a0 - a1): the product of their factors s
 // is folded into one other op of the same pass that touches every amplitude
 // once (the planner's choice), which is exact as every op is linear.
+// Diagonal ops on bits outside the tile without local controls come after the
+// program (nglob of them): one thread multiplies them into one factor per tile
+// while the tile loads, and that factor scales the coefficients of the
+// pass's absorber op (or, without one, the tile in one multiply).
 //
 // Each op is one sweep over the tile's pairs in shared memory, with the
 // target bit a runtime value, so one compact code path serves every target
