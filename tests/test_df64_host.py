@@ -5,7 +5,9 @@ random doubles and compares against long double references:
   * double -> (hi, lo) by bit manipulation: |hi + lo - d| <= 2^-47 |d|
     (plus 2^-125 absolute where the low word underflows the float range);
   * (hi, lo) -> double by integer merging: within 1 ulp of the exact sum;
-  * the complex 2x2 row u a + v b: relative error <= 2^-44.
+  * the complex 2x2 row u a + v b: relative error <= 2^-44;
+  * the unscaled butterfly (a0 + a1, a0 - a1) of Hadamard-type gates:
+    relative error <= 2^-46 of |a0| + |a1| per component.
 """
 import os
 import subprocess
@@ -72,6 +74,21 @@ int main() {
         long double mr = Ur * Ar - Ui * Ai, mi = Ur * Ai + Ui * Ar;
         long double ms = fabsl(Ur * Ar) + fabsl(Ui * Ai) + fabsl(Ur * Ai) + fabsl(Ui * Ar);
         if ((double)((fabsl(ld(m.re) - mr) + fabsl(ld(m.im) - mi)) / ms) > std::ldexp(1.0, -44)) bad++;
+    }
+    // the unscaled butterfly of a Hadamard-type gate: (a0 + a1, a0 - a1) by
+    // double-float additions, relative to |a0| + |a1| per component
+    for (int i = 0; i < 200000; i++) {
+        const double e0 = E(g) / 4, e1 = E(g) / 4;
+        dcx a{df_from_double(U(g) * std::ldexp(1.0, (int)e0)), df_from_double(U(g) * std::ldexp(1.0, (int)e0))};
+        dcx b{df_from_double(U(g) * std::ldexp(1.0, (int)e1)), df_from_double(U(g) * std::ldexp(1.0, (int)e1))};
+        const df s_re = df_add(a.re, b.re), s_im = df_add(a.im, b.im);
+        const df d_re = df_add(a.re, df_neg(b.re)), d_im = df_add(a.im, df_neg(b.im));
+        const long double pairs[4][3] = {{ld(s_re), ld(a.re) + ld(b.re), fabsl(ld(a.re)) + fabsl(ld(b.re))},
+                                         {ld(s_im), ld(a.im) + ld(b.im), fabsl(ld(a.im)) + fabsl(ld(b.im))},
+                                         {ld(d_re), ld(a.re) - ld(b.re), fabsl(ld(a.re)) + fabsl(ld(b.re))},
+                                         {ld(d_im), ld(a.im) - ld(b.im), fabsl(ld(a.im)) + fabsl(ld(b.im))}};
+        for (const auto &p : pairs)
+            if (p[2] > 0 && (double)(fabsl(p[0] - p[1]) / p[2]) > std::ldexp(1.0, -46)) bad++;
     }
     std::printf("%d %.3e %.3e %.3e\n", bad, worst_split, worst_join, worst_dot);
     return 0;
