@@ -67,11 +67,10 @@ WORKLOADS = {
 # FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# complex128 runs in double-float on the FP32 pipes: the FP32 issue rate
-# (152 SMs x 128 lanes x 2.07 GHz) over the 6.2 FP32 instructions the
-# double-float formulas spend per algorithmic FP64 flop (dense 2x2: 86
-# instructions for 14 flops per amplitude; real 2x2, phase, diagonal: 6.3)
-DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 6.2 / 1e12
+# FP32-pipe issue rate in thread-instructions per second: 152 SMs x 128 lanes
+# x 2.07 GHz (the hardware ceiling of the double-float complex128 kernels,
+# which run on the FP32 pipes)
+FP32_ISSUE_TINST = 152 * 128 * 2.07e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # TF32 dense tensor rate = bf16 rate x (1.1 / 2.25), the nominal ratio
@@ -95,6 +94,17 @@ def workload_gates(w):
     raise ValueError(w["kind"])
 
 
+def dtype_label(dt, pst=None):
+    """Arithmetic type of the path: complex64 computes in FP32; complex128
+    keeps IEEE doubles in memory and computes in double-float (two FP32
+    values, ~48 significand bits) in the tile passes and per-gate sweeps."""
+    if dt == "c64":
+        return "f32"
+    if pst and pst.get("fuse_k"):
+        return "f64"  # dense blocks on the CUDA cores compute in FP64
+    return "df64 (IEEE f64 storage, double-float arithmetic)"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -115,9 +125,8 @@ def tf32_peak():
     return FALLBACK_BF16_TFLOPS * TF32_OVER_BF16, "fallback bf16 x 1.1/2.25"
 
 
-def ncu_traffic(kernel, workload):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+def _ncu_table(name, kernel, workload):
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -126,6 +135,17 @@ def ncu_traffic(kernel, workload):
             if len(ln) >= 3 and ln[0] == kernel and ln[1] == workload:
                 return float(ln[2])
     return None
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None."""
+    return _ncu_table("ncu_traffic.txt", kernel, workload)
+
+
+def ncu_fp32_inst(kernel, workload):
+    """Per-launch FP32-pipe thread-instructions of a kernel (ncu instruction
+    counters of the current kernel build), or None."""
+    return _ncu_table("ncu_fp32_inst.txt", kernel, workload)
 
 
 # ---------------------------------------------------------------- clocks
@@ -335,10 +355,7 @@ def run_ours(args, w, ws, rank, local):
     per_launch_s = ms / nl / 1e3
     gbs = by / nl / per_launch_s / 1e9
     tflops = fl / nl / per_launch_s / 1e12
-    alu_peak = DF64_PEAK_TFLOPS if w["dtype"] == "c128" else FP32_PEAK_TFLOPS
-    if fam == "dense_cuda_core" and w["dtype"] == "c128":
-        alu_peak = FP64_PEAK_TFLOPS  # dense blocks compute in FP64
-    frac_hbm, frac_alu = gbs / hbm_peak, tflops / alu_peak
+    frac_hbm = gbs / hbm_peak
     tkey = args.workload
     if pst["fuse_k"] and "_fused" not in tkey:  # the autotuner picked dense blocks
         tkey += "_fused%d" % pst["fuse_k"]
@@ -346,13 +363,25 @@ def run_ours(args, w, ws, rank, local):
     hbm_roof = {"bound": "hbm", "kernel": fam, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": frac_hbm, "traffic": traffic, "peak_source": peak_src + " copy (MEASURED_PEAKS.json)",
                 "alg_bytes_per_launch": by / nl, "launches": nl, "avg_launch_ms": ms / nl}
-    alu_roof = {"bound": "alu", "kernel": fam, "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": traffic,
-                "peak_source": ("nominal FP64: 1.25 TFLOP/s" if alu_peak == FP64_PEAK_TFLOPS else
-                                "double-float on the FP32 pipes: 152 SM x 128 lanes x 2.07 GHz / 6.2 FP32 "
-                                "instructions per emulated FP64 flop" if w["dtype"] == "c128"
-                                else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
-                "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
+    if w["dtype"] == "c128" and fam != "dense_cuda_core":
+        # double-float arithmetic on the FP32 pipes: FP32 thread-instructions
+        # per second (ncu's per-launch count over the live launch time)
+        # against the FP32 issue rate; null without a capture of this kernel
+        inst = ncu_fp32_inst(fam, tkey)
+        ach = inst / (ms / nl / 1e3) / 1e12 if inst else None
+        alu_roof = {"bound": "alu", "kernel": fam, "achieved": ach, "peak": FP32_ISSUE_TINST,
+                    "unit": "T FP32 thread-instructions/s", "frac": ach / FP32_ISSUE_TINST if ach else None,
+                    "traffic": traffic, "peak_source": "FP32 issue: 152 SM x 128 lanes x 2.07 GHz",
+                    "fp32_inst_per_launch": inst, "alg_flops_per_launch": fl / nl,
+                    "alg_tflops": tflops, "launches": nl, "avg_launch_ms": ms / nl}
+    else:
+        alu_peak = FP64_PEAK_TFLOPS if fam == "dense_cuda_core" and w["dtype"] == "c128" else FP32_PEAK_TFLOPS
+        alu_roof = {"bound": "alu", "kernel": fam, "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": tflops / alu_peak, "traffic": traffic,
+                    "peak_source": ("nominal FP64: 1.25 TFLOP/s" if alu_peak == FP64_PEAK_TFLOPS
+                                    else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
+                    "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
+    frac_alu = alu_roof["frac"] or 0.0
     if fam == "fused_tensor_core":
         # 3xTF32: three TF32 products per algorithmic product; the achieved
         # figure counts algorithmic flops once
@@ -372,7 +401,7 @@ def run_ours(args, w, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w["dtype"] == "c128" else "f32",
+        "dtype": dtype_label(w["dtype"], pst),
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
                    "path": ("one sweep per gate" if args.pergate else

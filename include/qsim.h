@@ -56,7 +56,13 @@ typedef enum {
 
 typedef enum {
     QSIM_C64 = 0,           /* complex64: float2 amplitudes, FP32 arithmetic */
-    QSIM_C128 = 1           /* complex128: double2 amplitudes, FP64 arithmetic */
+    QSIM_C128 = 1           /* complex128: double2 amplitudes (IEEE FP64 in memory).
+                               Per-gate sweeps and tile passes compute in
+                               double-float (an unevaluated sum of two FP32
+                               values, about 48 significand bits; magnitudes
+                               below 2^-126 flush to zero), dense blocks on the
+                               CUDA cores in FP64.  Sec. III.A asks for 13-15
+                               significant digits; double-float keeps ~14.4. */
 } qsim_dtype;
 
 typedef struct qsim_state *qsim_handle;
@@ -182,7 +188,8 @@ QSIM_API qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g);
 /* qsim_apply_fused: dense 2^k x 2^k unitary U (row-major, 2 * 4^k doubles
  * (re, im)) on the k distinct logical qubits qubits[0..k-1]: qubits[j] is bit
  * j of U's row/column index; for every group of 2^k amplitudes that differ
- * only in those qubits, a'_r = sum_c U_rc a_c.  1 <= k <= 7.  A product of
+ * only in those qubits, a'_r = sum_c U_rc a_c.  1 <= k <= min(6, n), else
+ * EINVAL.  A product of
  * the paper's gates on k qubits, built on the host in FP64, applied in one
  * pass of the state. */
 QSIM_API qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U);
@@ -361,9 +368,10 @@ QSIM_API qsim_status qsim_qubit_probs(qsim_handle h, double *out);
  *
  * No device memory is allocated or freed: the block partial sums go to one
  * static device array of 608 x 34 doubles (161.5 KiB) that every GPU loading
- * the library holds until the process exits.  The first call on a device looks
- * the array's address up (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device share
+ * the library holds until the process exits.  Every call looks the array's
+ * address up (cudaGetSymbolAddress) on the current device; the first call on
+ * a device may load the library's device code there, so make it before any
+ * stream capture.  All calls on a device share
  * the array, so calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and corrupt each other's results; serialise
  * them.  The array keeps the last call's partial sums, which no later call

@@ -162,6 +162,14 @@ def adder_expected_index(values, m):
     return idx
 
 
+def adder_pairs(m=15, count=8, seed=3):
+    """Seeded register values for the two-register adder: ``count`` pairs
+    (a, b) drawn as ``default_rng(seed).integers(0, 2^m, (count, 2))``; the
+    first pair is the one the single-pair workload draws."""
+    rng = np.random.default_rng(seed)
+    return [(int(a), int(b)) for a, b in rng.integers(0, 1 << m, (count, 2))]
+
+
 def _random_layers(rng, n, depth):
     gates = []
     for _ in range(depth):

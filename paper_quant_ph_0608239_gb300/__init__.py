@@ -6,7 +6,7 @@ the stream (``State(..., use_torch=True)``, the default) -- it never computes.
 
     st = State(10, "c128")
     st.set_basis(x)
-    st.run(gates)                 # list of inputs.Gate, planner path
+    st.run(gates)                 # list of Gate records, planner path
     p = st.qubit_probs()          # <Q_q>, Eq. Shor7
 """
 from __future__ import annotations
@@ -16,6 +16,7 @@ import ctypes
 import numpy as np
 
 from . import _capi
+from .gate import Gate  # noqa: F401
 from ._capi import (QsimError, QsimGate, QsimOpts, QsimCircuit, QsimPlanStats, QsimKernelTime,  # noqa: F401
                     QsimCounters, gate_array, gate_record,
                     MODE_PERGATE, MODE_FUSED, MODE_AUTO, QSIM_C64, QSIM_C128, QSIM_ETIMEOUT, QSIM_EINVAL)
@@ -150,7 +151,7 @@ class State:
         _capi.call("qsim_permute_bits", self.handle, K, (ctypes.c_int * K)(*l), (ctypes.c_int * K)(*h))
 
     def run(self, gates, mode=MODE_FUSED, tile_bits=0, fuse_k=0, gate_arr=None):
-        """Apply a gate list (inputs.Gate objects, or a pre-marshalled array)."""
+        """Apply a gate list (Gate records, or a pre-marshalled array)."""
         arr = gate_arr if gate_arr is not None else gate_array(gates)
         ng = len(gates) if gates is not None else len(arr)
         o = opts(mode, tile_bits, fuse_k)

@@ -10,7 +10,6 @@
 //
 // The partial sums of each block go to a caller-provided scratch buffer in
 // global memory and a second kernel adds them up.
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels.hpp"
@@ -397,31 +396,18 @@ constexpr size_t kNoAllocDoubles = (size_t)kNoAllocBlocks * kMaxQubits;  // 161.
 // Block partials of the last call: [block][bit], kNoAllocBlocks x n used.
 static __device__ __align__(256) double g_noalloc_partial[kNoAllocDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
-
 }  // namespace
 
 
 cudaError_t launch_bit_probs_noalloc(const void *amp, int dt, int n, double *dout, cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // The array's name is not a device address in host code: look the address
+    // up on every call, with the caller's device current.  The lookup is a
+    // host-side query, and doing it each time keeps the address right after a
+    // context was torn down and the module loaded again (cudaDeviceReset).
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    double *scratch = nullptr;
-    {
-        // Set-up, once per device, with that device current: host code cannot
-        // use the array's name as an address, so look the address up.
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_partial);
-            if (e != cudaSuccess) return e;
-            g_noalloc_ptr[dev] = static_cast<double *>(p);
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    double *scratch = static_cast<double *>(p);
     if (n < kChunkBits + 1) {  // small registers reduce in one block, no scratch
         if (dt == 0)
             k_bits_small<float><<<1, 256, 0, s>>>(static_cast<const float2 *>(amp), n, dout);

@@ -34,7 +34,7 @@ from __future__ import annotations
 import math
 from collections import namedtuple
 
-from inputs.circuits import Gate
+from .gate import Gate
 
 Step = namedtuple("Step", ["kind", "args"])  # kind: "gates", "swap", "measure"
 

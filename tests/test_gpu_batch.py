@@ -74,6 +74,7 @@ def test_batch_graph_replay_is_repeatable(q):
     b = q.Batch(states, x0s, [g for _, g in circs])
     stats = b.stats()
     assert stats["circuits"] == 12 and stats["items"] >= stats["passes"] >= 12
+    assert stats["graph"], "the persistent launch was not captured in a CUDA graph"
     first = None
     for rep in range(3):
         b.run()
@@ -117,6 +118,7 @@ def test_batch_config_512_sampled(q):
     states = [q.State(n, "c64") for n, _ in circs]
     x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
     b = q.Batch(states, x0s, [g for _, g in circs])
+    assert b.stats()["graph"], "the persistent launch was not captured in a CUDA graph"
     b.run()
     b.sync()
     for st, (n, g) in zip(states, circs):

@@ -1,5 +1,6 @@
 """The App. A command format: parsing on the CPU, execution on the GPU."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -8,6 +9,8 @@ import inputs
 import oracle
 from inputs import Gate
 from paper_quant_ph_0608239_gb300 import program
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 PROG_H = """
 # Hadamard on every qubit of a 12-qubit register, with interchanges
@@ -124,3 +127,15 @@ def test_run_programs_on_gpu():
     got = sum(1 << qb for qb, v in res[0].items() if v > 0.5)
     assert got == want
     st.free()
+
+
+def test_package_does_not_need_the_input_generators():
+    # the product (binding and program front-end) must import and parse without
+    # the repository's test-input package on the path
+    import subprocess
+    import sys
+    code = ("import sys; sys.modules['inputs'] = None\n"
+            "import paper_quant_ph_0608239_gb300.program as p\n"
+            "L, x0, steps = p.parse('QUBITS 3\\nH 0\\nCNOT 1 0\\n')\n"
+            "assert L == 3 and steps[0].args[0].kind == 'H'\n")
+    subprocess.check_call([sys.executable, "-c", code], cwd=ROOT)

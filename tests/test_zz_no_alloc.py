@@ -32,7 +32,9 @@ def test_noalloc_marginals_match_allocating_entry_point(dt):
     from paper_quant_ph_0608239_gb300 import _capi
     lib = _capi.load()
     dcode = q.QSIM_C64 if dt == "c64" else q.QSIM_C128
-    for n, seed in ((20, 5), (13, 6)):   # two calls in a row, the second on a smaller register
+    # calls in a row: the second on a smaller register, the third on one small
+    # enough to be reduced by a single block without the scratch array
+    for n, seed in ((20, 5), (13, 6), (5, 7)):
         st = q.State(n, dt)
         st.set_basis(inputs.random_basis(n, seed))
         st.run(inputs.random_circuit(n, 4, seed))
