@@ -83,10 +83,10 @@ struct qsim_state {
 
 // Kernel families reported by qsim_profile_read.
 enum Fam { F_INIT, F_PAIR, F_DIAG, F_DENSE, F_TILE, F_NORM, F_BITS, F_PROBS, F_GATHER, F_SAMPLE, F_FUSED_TC,
-           F_BATCH, F_COUNT };
+           F_BATCH, F_FUSED_TC128, F_COUNT };
 static const char *kFamName[F_COUNT] = {"init_basis", "pair_sweep", "diag_sweep", "dense_cuda_core", "tile_pass",
                                         "norm", "bit_probs", "probs", "gather", "sample", "fused_tensor_core",
-                                        "batch"};
+                                        "batch", "fused_tc_digits"};
 
 static cudaEvent_t take_event(qsim_state *h) {
     if (!h->pool.empty()) {
@@ -495,6 +495,7 @@ struct qsim_plan_s {
     // dense blocks the tensor-core kernel does not take (complex128, k = 6, ...)
     // run on the CUDA cores (k_dense): their matrices in the state's precision
     bool cuda_core = false;
+    bool tc128 = false;  // complex128 blocks on the tensor cores (bmats holds bf16 slices)
     std::vector<unsigned char> cmats;
     size_t cmat_stride = 0;
     void *d_cmats = nullptr;
@@ -537,7 +538,33 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         return QSIM_OK;
     }
-    if (o.fuse_k > 0 && !fused_tc_supported((int)h->dt, o.fuse_k, h->n)) {
+    if (o.fuse_k > 0 && h->dt == QSIM_C128 && fused_tc128_supported(o.fuse_k, h->n)) {
+        // complex128 blocks on the tensor cores (bf16 digit slices); a block
+        // the scheme cannot take exactly sends the whole plan to the CUDA cores
+        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+            return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
+        const size_t per = fused_tc128_b_bytes() / sizeof(float);
+        P.bmats.resize(per * P.blocks.size());
+        bool ok = true;
+        for (size_t b = 0; b < P.blocks.size() && ok; b++) {
+            TileGeom g;
+            FusedMap fm;
+            ok = fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm) &&
+                 fused_tc128_prepare_b(P.blocks[b].U.data(), reinterpret_cast<uint16_t *>(P.bmats.data() + per * b));
+            P.stats.alg_flops += P.blocks[b].flops;
+        }
+        if (ok) {
+            P.tc128 = true;
+            P.stats.passes = (int)P.blocks.size();
+            P.stats.tile_bits = o.fuse_k + 7;
+            P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
+            return QSIM_OK;
+        }
+        P.blocks.clear();
+        P.bmats.clear();
+        P.stats.alg_flops = 0.0;
+    }
+    if (o.fuse_k > 0 && (h->dt == QSIM_C128 || !fused_tc_supported((int)h->dt, o.fuse_k, h->n))) {
         // dense blocks on the CUDA cores (complex128, k = 1..6, small registers)
         if (o.fuse_k > 6 || o.fuse_k > h->n) return fail(QSIM_EUNSUPPORTED, "fused blocks need k <= min(6, n)");
         if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
@@ -613,6 +640,20 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
                       [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, P.blocks[b].pos, dU, h->stream); },
                       P.blocks[b].flops),
                "fused block (CUDA cores)");
+        }
+        return QSIM_OK;
+    }
+    if (P.tc128) {
+        const size_t per = fused_tc128_b_bytes() / sizeof(float);
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            TileGeom g;
+            FusedMap fm;
+            fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
+            const uint16_t *bm = reinterpret_cast<const uint16_t *>(d_bmats + per * b);
+            CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
+                      [&] { return launch_fused_tc128(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream); },
+                      P.blocks[b].flops),
+               "fused block (tensor cores, complex128)");
         }
         return QSIM_OK;
     }
@@ -754,6 +795,7 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
     };
     if (h->dt == QSIM_C128) {
         for (int T : {11, 12, 13}) add(T, 0);
+        if (fused_tc128_supported(5, h->n)) add(0, 5);
     } else {
         for (int T : {12, 13}) add(T, 0);
         for (int k : {4, 5})
@@ -930,7 +972,26 @@ qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const doub
     const double flops = 8.0 * (double)(1u << k) * std::ldexp(1.0, h->n);
     TileGeom g;
     FusedMap fm;
-    if (fused_tc_supported((int)h->dt, k, h->n) && fused_geometry(h->n, k, pos, g, fm)) {
+    if (h->dt == QSIM_C128 && fused_tc128_supported(k, h->n) && fused_geometry(h->n, k, pos, g, fm)) {
+        std::vector<uint16_t> b(fused_tc128_b_bytes() / sizeof(uint16_t));
+        if (fused_tc128_prepare_b(U, b.data())) {
+            const size_t bytes = fused_tc128_b_bytes();
+            qsim_status st = ensure_dense(h, bytes);
+            if (st != QSIM_OK) return st;
+            CK(cudaMemcpyAsync(h->d_dense, b.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+            CK(cudaStreamSynchronize(h->stream), "sync");  // b is freed on return
+            h->h2d += bytes;
+            CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
+                      [&] {
+                          return launch_fused_tc128(h->amp, g, fm, static_cast<const uint16_t *>(h->d_dense),
+                                                    h->d_err, h->sm_count, h->stream);
+                      },
+                      flops),
+               "fused gate (tensor cores, complex128)");
+            return QSIM_OK;
+        }
+    }
+    if (h->dt == QSIM_C64 && fused_tc_supported((int)h->dt, k, h->n) && fused_geometry(h->n, k, pos, g, fm)) {
         // tensor cores: B operand (3xTF32 head and tail) from U
         std::vector<float> b(2 * (size_t)(2 << k) * (size_t)(2 << k));
         fused_tc_prepare_b(k, U, b.data());

@@ -1,0 +1,382 @@
+// k_fused_tc_c128.cu -- complex128 dense 5-qubit gates on the tensor cores.
+//
+// A fused gate is the FP64 product U of the gates it replaces (2^5 x 2^5,
+// built on the host).  For every group of 32 amplitudes that differ only in
+// the five qubits, a' = U a.  With complex numbers as real 2x2 blocks this is
+//
+//     D (rows = groups, 64 columns) = A (groups x 64) * B^T,
+//
+// a row of A being the group's 64 reals (re, im, re, im, ...).  The doubles
+// are cut into six bf16 digit slices against the group's largest exponent,
+// and U's entries into six slices of their own (digits.cuh: the split, the
+// exact level sums and the combination, with their error bounds).  The 21
+// slice products A_i B_j^T with i + j <= 5 run as tcgen05.mma kind::f16
+// (bf16 inputs, FP32 accumulation in tensor memory), accumulated per level
+// (levels 0, 1, 2, 3 exactly, levels 4 and 5 together).
+//
+// One CTA per SM, 512 threads: the four warps of a tensor-memory lane
+// quarter share its 32 groups, each taking one quarter of a group's 32
+// amplitudes -- which is one K step (16 reals) of the product.  Per tile of
+// 128 groups (4096 amplitudes, 64 KiB):
+//   1. the tile arrives by bulk asynchronous copies (TMA engine) into one of
+//      two shared-memory buffers, fetched two tiles ahead;
+//   2. split: each thread reads its 8 amplitudes, the four threads of a group
+//      agree on its largest exponent, and the thread writes its digits into
+//      the A slices in tensor memory (its lane, 8 columns per slice);
+//   3. one thread issues the 84 MMAs (21 products x 4 K steps of 16);
+//   4. epilogue: each thread reads the five accumulators of its 16 output
+//      reals, combines them into doubles and writes them into the same
+//      buffer at the groups' positions (its input there was consumed in 2);
+//   5. bulk stores write the tile back; once they have read the buffer, the
+//      fetch of the tile two ahead reuses it.
+// Tensor memory: accumulators at columns 0..319 (level L at 64 L), the A
+// slices at 320 + 48 s + 8 i (K step s, slice i): all 512 columns.
+#include <cstring>
+#include <cmath>
+
+#include "common.cuh"
+#include "digits.cuh"
+#include "kernels.hpp"
+#include "ptx.cuh"
+#include "tcgen05.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreads128 = 512;
+constexpr int kK = 5;                          // qubits of a block
+constexpr int kAmps = 1 << kK;                 // 32 amplitudes of a group
+constexpr int kReals = 2 * kAmps;              // 64: K and N of the product
+constexpr int kTileBits = kK + 7;              // 128 groups per tile
+constexpr uint32_t kTileBytes = 16u << kTileBits;           // 64 KiB
+constexpr uint32_t kSliceBytes = kReals * kReals * 2;       // 8 KiB per B slice
+constexpr uint32_t kBBytes = kDigits * kSliceBytes;         // 48 KiB
+constexpr uint32_t kAccCols = kDigitLevels * kReals;        // 320
+constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxH128 = 10;
+constexpr long long kWaitBudget128 = 4000000000ll;
+
+// byte offset of element (n, kk) in a bf16 K-major, no-swizzle operand of 64
+// K columns: core matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes
+// apart, row-adjacent ones 1024 bytes apart
+__host__ __device__ constexpr uint32_t bcanon_off(uint32_t n, uint32_t kk) {
+    return (n & 7u) * 16u + (kk & 7u) * 2u + (kk >> 3) * 128u + (n >> 3) * 1024u;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, bf16 inputs, issued by one thread
+__device__ __forceinline__ void umma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds_u4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts_u4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// barrier of the four warps sharing a tensor-memory lane quarter
+__device__ __forceinline__ void quarter_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+__global__ void __launch_bounds__(kThreads128, 1)
+    k_fused_tc_c128(double2 *__restrict__ a, TileGeom g, FusedMap fm, const uint16_t *__restrict__ bmat,
+                    uint32_t *err, uint64_t ntiles) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *s_b = smem_raw;                    // six B slices
+    unsigned char *s_buf0 = smem_raw + kBBytes;       // two tile buffers
+    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma, bar_b;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ uint32_t s_max[4][128];  // per K quarter, per group: largest exponent field
+    __shared__ int s_hb[kMaxH128];
+    const int L = g.L, H = g.H;
+    const uint32_t nruns = 1u << H;
+    const uint32_t run_bytes = 16u << L;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lq = warp & 3, qq = warp >> 2;  // lane quarter, K quarter
+    const uint32_t m = (uint32_t)(32 * lq + lane);
+
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < kMaxH128; k++) s_hb[k] = k < H ? g.hb[k] : 0;
+        mbar_init(&bar_ld[0], 1);
+        mbar_init(&bar_ld[1], 1);
+        mbar_init(&bar_mma, 1);
+        mbar_init(&bar_b, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_s, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
+
+    auto run_off = [&](uint32_t j) {
+        uint64_t o = 0;
+        for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << s_hb[k];
+        return o;
+    };
+    auto tile_base = [&](uint64_t tile) {
+        uint64_t base = tile << L;
+        for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
+        return base;
+    };
+    auto buf = [&](int b) { return s_buf0 + (size_t)b * kTileBytes; };
+    auto issue_load = [&](uint64_t tile, int b) {  // warp 0
+        const uint64_t base = tile_base(tile);
+        if (lane == 0) mbar_arrive_expect_tx(&bar_ld[b], kTileBytes);
+        __syncwarp();
+        double2 *dst = reinterpret_cast<double2 *>(buf(b));
+        for (uint32_t j = lane; j < nruns; j += 32)
+            bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[b]);
+    };
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar_b, kBBytes);
+        bulk_g2s(s_b, bmat, kBBytes, &bar_b);
+    }
+    const uint64_t stride = gridDim.x;
+    uint64_t tile = blockIdx.x;
+    // fetches issued (warp 0) and awaited (every thread) per buffer, so that
+    // an aborting CTA can let the copies in flight land before it leaves
+    uint32_t n_issued[2] = {0u, 0u}, n_done[2] = {0u, 0u};
+    if (warp == 0) {
+        if (tile < ntiles) issue_load(tile, 0), n_issued[0]++;
+        if (tile + stride < ntiles) issue_load(tile + stride, 1), n_issued[1]++;
+    }
+    bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128)) != 0;
+
+    // tile index of group m and of the block's columns
+    uint32_t ibase = 0;
+#pragma unroll
+    for (int b = 0; b < kTileBits - kK; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+    uint32_t wc[kK];
+#pragma unroll
+    for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
+    // this thread's amplitudes are columns 8 qq + j, j < 8
+    const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
+    uint32_t coff[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        coff[j] = qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
+
+    uint32_t i = 0;
+    for (; tile < ntiles && !aborted; tile += stride, i++) {
+        const int b = (int)(i & 1u);
+        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld[b], n_done[b] & 1u, kWaitBudget128)) != 0;
+        if (aborted) break;
+        n_done[b]++;
+        const uint32_t sbuf = smem_u32(buf(b));
+
+        // ---- split: 8 amplitudes -> 16 fixed-point reals -> 6 digit slices
+        uint32_t hw[16], lw[16];
+        uint32_t mx = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint4 v = lds_u4(sbuf + 16u * coff[j]);
+            lw[2 * j] = v.x;
+            hw[2 * j] = v.y;
+            lw[2 * j + 1] = v.z;
+            hw[2 * j + 1] = v.w;
+            mx = max(mx, max(v.y & 0x7ff00000u, v.w & 0x7ff00000u));
+        }
+        s_max[qq][m] = mx;
+        quarter_sync(1u + (uint32_t)lq);
+        const uint32_t Mg = max(max(s_max[0][m], s_max[1][m]), max(s_max[2][m], s_max[3][m])) >> 20;
+        uint64_t xc[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) xc[r] = dg_fixed(hw[r], lw[r], Mg);
+        const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;
+        {
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<0>(xc[2 * j]), dg_digit<0>(xc[2 * j + 1]));
+            tmem_st8(acol + 0, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<1>(xc[2 * j]), dg_digit<1>(xc[2 * j + 1]));
+            tmem_st8(acol + 8, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<2>(xc[2 * j]), dg_digit<2>(xc[2 * j + 1]));
+            tmem_st8(acol + 16, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<3>(xc[2 * j]), dg_digit<3>(xc[2 * j + 1]));
+            tmem_st8(acol + 24, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<4>(xc[2 * j]), dg_digit<4>(xc[2 * j + 1]));
+            tmem_st8(acol + 32, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<5>(xc[2 * j]), dg_digit<5>(xc[2 * j + 1]));
+            tmem_st8(acol + 40, w);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+
+        // ---- the 21 slice products, 4 K steps each
+        if (tid == 0) {
+            const uint32_t idesc = idesc_bf16(128, kReals);
+            const uint32_t bb = smem_u32(s_b);
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++)
+#pragma unroll
+                for (int si = 0; si < kDigits; si++)
+#pragma unroll
+                    for (int sj = 0; si + sj < kDigits; sj++) {
+                        const int lv = dg_level_acc(si, sj);
+                        // the first product of a level at K step 0 starts its accumulator
+                        const bool first = ks == 0 && (lv < kDigitLevels - 1 ? si == 0 : si == 0 && sj == lv);
+                        umma_bf16_ts(tmem + (uint32_t)(kReals * lv), tmem + kAccCols + 48u * ks + 8u * si,
+                                     umma_desc(bb + (uint32_t)sj * kSliceBytes + (uint32_t)ks * 256u, 128, 1024),
+                                     idesc, first ? 0u : 1u);
+                    }
+            umma_commit(&bar_mma);
+        }
+        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128)) != 0;
+        tc_fence_after();
+        if (aborted) {
+            if (tid == 0) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs still in flight
+            break;
+        }
+
+        // ---- epilogue: output reals 16 qq .. 16 qq + 15 of group m
+        {
+            uint32_t acc[kDigitLevels][16];
+#pragma unroll
+            for (int lv = 0; lv < kDigitLevels; lv++)
+                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * lv + 16 * qq), acc[lv]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const double re = dg_combine(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
+                                             __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]),
+                                             __uint_as_float(acc[4][2 * j]), Mg);
+                const double im = dg_combine(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
+                                             __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
+                                             __uint_as_float(acc[4][2 * j + 1]), Mg);
+                const uint64_t rb = (uint64_t)__double_as_longlong(re), ib = (uint64_t)__double_as_longlong(im);
+                sts_u4(sbuf + 16u * coff[j], make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (uint32_t)ib,
+                                                        (uint32_t)(ib >> 32)));
+            }
+        }
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        // ---- store, then fetch the tile two ahead into the same buffer
+        if (warp == 0) {
+            const uint64_t base = tile_base(tile);
+            const double2 *src = reinterpret_cast<const double2 *>(buf(b));
+            for (uint32_t j = lane; j < nruns; j += 32) bulk_s2g(a + (base | run_off(j)), src + ((size_t)j << L), run_bytes);
+            bulk_commit();
+            if (tile + 2 * stride < ntiles) {
+                bulk_wait_read_all();
+                __syncwarp();
+                issue_load(tile + 2 * stride, b);
+                n_issued[b]++;
+            }
+        }
+    }
+    if (aborted && tid == 0) atomicExch(err, kErrTimeout);
+    if (aborted && warp == 0) {  // let fetches in flight land before the CTA leaves
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+            for (; n_done[b] < n_issued[b]; n_done[b]++) mbar_wait_bounded(&bar_ld[b], n_done[b] & 1u, kWaitBudget128);
+    }
+    if (warp == 0) bulk_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+// Host: the six B slices of a fused 5-qubit gate in the canonical layout.
+// U: 32 x 32 complex, row-major (re, im) FP64.  out: kBBytes / 2 bf16 bit
+// patterns.  Returns false when an entry is outside (-2, 2) or a row's level
+// sums could leave the exact FP32 range (never for a unitary U): the caller
+// then takes another path.
+bool fused_tc128_prepare_b(const double *U, uint16_t *out) {
+    std::memset(out, 0, kBBytes);
+    double rowsum[kReals][kDigits];
+    for (int n = 0; n < kReals; n++)
+        for (int j = 0; j < kDigits; j++) rowsum[n][j] = 0.0;
+    for (int r = 0; r < kAmps; r++)
+        for (int c = 0; c < kAmps; c++) {
+            const double ur = U[2 * (r * kAmps + c)], ui = U[2 * (r * kAmps + c) + 1];
+            const double v[4] = {ur, -ui, ui, ur};
+            const int nn[4] = {2 * r, 2 * r, 2 * r + 1, 2 * r + 1};
+            const int kk[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+            for (int e = 0; e < 4; e++) {
+                if (!(std::fabs(v[e]) < 2.0)) return false;
+                float d[kDigits];
+                dg_split_entry(v[e], d);
+                for (int j = 0; j < kDigits; j++) {
+                    out[(j * kSliceBytes + bcanon_off((uint32_t)nn[e], (uint32_t)kk[e])) / 2] = (uint16_t)dg_bf16(d[j]);
+                    rowsum[nn[e]][j] += std::fabs(std::ldexp((double)d[j], kDigitBits * j));
+                }
+            }
+        }
+    // level L <= 3 sums at most 256 * sum_{j <= L} ||c_j||_1 (|d_i| <= 256)
+    for (int n = 0; n < kReals; n++) {
+        double s = 0.0;
+        for (int j = 0; j < kDigitLevels - 1; j++) {
+            s += rowsum[n][j];
+            if (256.0 * s >= 16777216.0) return false;
+        }
+    }
+    return true;
+}
+
+size_t fused_tc128_b_bytes() { return kBBytes; }
+
+bool fused_tc128_supported(int k, int n) { return k == kK && n >= kTileBits; }
+
+cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
+                               uint32_t *err, int sm_count, cudaStream_t s) {
+    if (g.L + g.H != kTileBits || g.H > kMaxH128 || g.L < 1) return cudaErrorInvalidValue;
+    const size_t smem = kBBytes + 2 * (size_t)kTileBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tc_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t ntiles = 1ull << (g.n - kTileBits);
+    uint64_t grid = ntiles < (uint64_t)sm_count ? ntiles : (uint64_t)sm_count;
+    k_fused_tc_c128<<<(unsigned)grid, kThreads128, smem, s>>>(static_cast<double2 *>(amp), g, fm, bmat, err, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

@@ -190,6 +190,17 @@ void fused_tc_prepare_b(int k, const double *U, float *out);
 cudaError_t launch_fused_tc(void *amp, int k, const TileGeom &g, const FusedMap &fm, const float *bmat,
                             uint32_t *err, int sm_count, cudaStream_t s);
 
+// Dense 5-qubit gate on the tensor cores for complex128 (k_fused_tc_c128.cu:
+// bf16 digit slices, exact level sums; n >= 12): bmat = device copy of
+// fused_tc128_prepare_b's output (fused_tc128_b_bytes() bytes), which
+// returns false for a matrix the scheme cannot take exactly (an entry
+// outside (-2, 2)).
+bool fused_tc128_supported(int k, int n);
+size_t fused_tc128_b_bytes();
+bool fused_tc128_prepare_b(const double *U, uint16_t *out);
+cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
+                               uint32_t *err, int sm_count, cudaStream_t s);
+
 // ------------------------------------------------------------ batches
 struct BatchCircuit {
     void *amp;            // complex64 state of the circuit

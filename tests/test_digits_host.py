@@ -1,0 +1,191 @@
+"""Digit-slice arithmetic of the complex128 tensor-core blocks, checked on the CPU.
+
+csrc/digits.cuh compiles for the host as well.  A C++ driver cuts groups of
+64 doubles and rows of a 64 x 64 real matrix (the real form of a random 32 x 32
+complex unitary) into the six bf16 digit slices, forms the 21 slice products
+level by level the way the tensor cores do (exact products, FP32 accumulation
+after every 16-element K step), combines the five accumulators and compares
+with the exact dot product of the original doubles in long double:
+
+  * the slices rebuild the fixed-point value exactly and every slice value is
+    a bf16 number (its low 16 bits are zero);
+  * the FP32 accumulators of levels 0..3 equal the exact level sums (the
+    sums of |products| stay below 2^24), for random and adversarial inputs;
+  * the combined result is within 2^-43 of max|x| * ||u_row||_1 of the exact
+    dot product (the dropped levels and the fixed-point truncation), and the
+    typical error is near 2^-48 of the output's magnitude scale.
+"""
+import os
+import subprocess
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+DRIVER = r'''
+#include <algorithm>
+#include <cstdio>
+#include <cmath>
+#include <complex>
+#include <random>
+#include <vector>
+#include "digits.cuh"
+using namespace qsim;
+typedef long double LD;
+
+static std::mt19937_64 g(777);
+static std::normal_distribution<double> N01(0.0, 1.0);
+static std::uniform_real_distribution<double> U01(0.0, 1.0);
+
+// 32 x 32 complex unitary (Gram-Schmidt of a Gaussian matrix), real form
+// B[n][kk]: out_re[r] = sum_c Ure a_re - Uim a_im, out_im[r] = sum_c Uim a_re + Ure a_im
+static void rand_unitary_real(std::vector<double> &B, int kind) {
+    const int K = 32;
+    std::vector<std::complex<double>> Q(K * K);
+    if (kind == 1) {  // a permutation with phases +-1, +-i
+        std::vector<int> p(K);
+        for (int i = 0; i < K; i++) p[i] = i;
+        std::shuffle(p.begin(), p.end(), g);
+        const std::complex<double> ph[4] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+        for (int r = 0; r < K; r++) Q[r * K + p[r]] = ph[g() & 3];
+    } else if (kind == 2) {  // Hadamard^5 (every entry +-2^-2.5)
+        for (int r = 0; r < K; r++)
+            for (int c = 0; c < K; c++) Q[r * K + c] = (__builtin_popcount(r & c) & 1 ? -1.0 : 1.0) / std::sqrt(32.0);
+    } else {
+        for (auto &z : Q) z = {N01(g), N01(g)};
+        for (int r = 0; r < K; r++) {
+            for (int q = 0; q < r; q++) {
+                std::complex<double> d = 0;
+                for (int c = 0; c < K; c++) d += std::conj(Q[q * K + c]) * Q[r * K + c];
+                for (int c = 0; c < K; c++) Q[r * K + c] -= d * Q[q * K + c];
+            }
+            double nn = 0;
+            for (int c = 0; c < K; c++) nn += std::norm(Q[r * K + c]);
+            for (int c = 0; c < K; c++) Q[r * K + c] /= std::sqrt(nn);
+        }
+    }
+    B.assign(64 * 64, 0.0);
+    for (int r = 0; r < K; r++)
+        for (int c = 0; c < K; c++) {
+            const double ur = Q[r * K + c].real(), ui = Q[r * K + c].imag();
+            B[(2 * r) * 64 + 2 * c] = ur;
+            B[(2 * r) * 64 + 2 * c + 1] = -ui;
+            B[(2 * r + 1) * 64 + 2 * c] = ui;
+            B[(2 * r + 1) * 64 + 2 * c + 1] = ur;
+        }
+}
+
+static void group(std::vector<double> &x, int kind) {
+    x.assign(64, 0.0);
+    const int e = -(int)(U01(g) * 40);
+    for (int k = 0; k < 64; k++) {
+        double v = N01(g) * std::ldexp(1.0, e);
+        if (kind == 1) v = std::ldexp(1.0, e) * (2.0 - std::ldexp(1.0, -52)) * ((k * 7 % 3) ? 1 : -1);  // max mantissas
+        if (kind == 2) v = (k == 5 ? 1.0 : std::ldexp(N01(g), -70)) * std::ldexp(1.0, e);  // one large, rest tiny
+        if (kind == 3) v = (k % 4 == 0) ? 0.0 : (k % 4 == 1 ? -0.0 : v);                   // zeros
+        if (kind == 4) v = std::ldexp(1.0, e - (k % 9)) * ((k & 1) ? -1 : 1);               // powers of two
+        if (kind == 5) v = 0.0;                                                             // all zero
+        x[k] = v;
+    }
+}
+
+int main() {
+    int bad_exact = 0, bad_slice = 0, bad_bound = 0, bad_err = 0;
+    double worst = 0.0, sum_typ = 0.0;
+    long cnt = 0;
+    std::vector<double> B, x;
+    for (int trial = 0; trial < 3000; trial++) {
+        rand_unitary_real(B, trial % 7 == 3 ? 1 : trial % 7 == 5 ? 2 : 0);
+        group(x, trial % 11 < 6 ? 0 : trial % 11 - 5);
+        // slices of the group (common exponent) and of the matrix
+        uint32_t Mg = 0;
+        for (double v : x) {
+            uint64_t b = df_bits64(v);
+            uint32_t be = dg_bexp((uint32_t)(b >> 32));
+            if (be > Mg) Mg = be;
+        }
+        float A[kDigits][64], Bd[kDigits][64][64];
+        for (int k = 0; k < 64; k++) {
+            const uint64_t b = df_bits64(x[k]);
+            const uint64_t XC = dg_fixed((uint32_t)(b >> 32), (uint32_t)b, Mg);
+            A[0][k] = dg_digit<0>(XC); A[1][k] = dg_digit<1>(XC); A[2][k] = dg_digit<2>(XC);
+            A[3][k] = dg_digit<3>(XC); A[4][k] = dg_digit<4>(XC); A[5][k] = dg_digit<5>(XC);
+            // the slices rebuild X exactly: sum d_i 2^(45 - 9i) = XC - C
+            LD X = 0;
+            for (int i = 0; i < kDigits; i++) {
+                X += (LD)A[i][k] * std::ldexp((LD)1, 45);  // d_i 2^(-9i) 2^45
+                if ((df_fbits(A[i][k]) & 0xffffu) != 0u) bad_slice++;
+                if (std::fabs(A[i][k]) > std::ldexp(256.0f, -9 * i)) bad_slice++;
+            }
+            if (X != (LD)(int64_t)(XC - kDigitOffset)) bad_slice++;
+        }
+        for (int n = 0; n < 64; n++)
+            for (int k = 0; k < 64; k++) {
+                float d[kDigits];
+                dg_split_entry(B[n * 64 + k], d);
+                for (int j = 0; j < kDigits; j++) {
+                    Bd[j][n][k] = d[j];
+                    if ((df_fbits(d[j]) & 0xffffu) != 0u) bad_slice++;
+                }
+            }
+        for (int n = 0; n < 64; n++) {
+            // the tensor cores: 4 K steps of 16, exact products, FP32 accumulation
+            float acc[kDigitLevels] = {0, 0, 0, 0, 0};
+            LD exact[kDigitLevels] = {0, 0, 0, 0, 0}, mag[kDigitLevels] = {0, 0, 0, 0, 0};
+            for (int ks = 0; ks < 4; ks++)
+                for (int i = 0; i < kDigits; i++)
+                    for (int j = 0; i + j < kDigits; j++) {
+                        const int L = dg_level_acc(i, j);
+                        LD part = 0;
+                        for (int k = 16 * ks; k < 16 * ks + 16; k++) {
+                            const LD p = (LD)A[i][k] * (LD)Bd[j][n][k];
+                            part += p;
+                            mag[L] += std::fabs(p);
+                        }
+                        exact[L] += part;
+                        acc[L] = (float)((LD)acc[L] + part);
+                    }
+            for (int L = 0; L < 4; L++) {
+                if ((LD)acc[L] != exact[L]) bad_exact++;
+                if (mag[L] * std::ldexp((LD)1, 9 * L) >= std::ldexp((LD)1, 24)) bad_bound++;
+            }
+            const double got = dg_combine(acc[0], acc[1], acc[2], acc[3], acc[4], Mg);
+            LD ref = 0, scale = 0, xmax = 0;
+            for (int k = 0; k < 64; k++) {
+                ref += (LD)x[k] * (LD)B[n * 64 + k];
+                scale += std::fabs((LD)B[n * 64 + k]);
+                if (std::fabs((LD)x[k]) > xmax) xmax = std::fabs((LD)x[k]);
+            }
+            if (xmax == 0) {
+                if (got != 0.0) bad_err++;
+                continue;
+            }
+            const double e = (double)(std::fabs((LD)got - ref) / (xmax * scale));
+            if (e > worst) worst = e;
+            sum_typ += e;
+            cnt++;
+            if (e > std::ldexp(1.0, -43)) bad_err++;
+        }
+    }
+    std::printf("%d %d %d %d %.3e %.3e\n", bad_exact, bad_slice, bad_bound, bad_err, worst, sum_typ / cnt);
+    return 0;
+}
+'''
+
+
+def test_digit_slices_exact_levels_and_combination():
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "drv.cpp")
+        exe = os.path.join(tmp, "drv")
+        open(src, "w").write(DRIVER)
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off",
+                               "-I", os.path.join(ROOT, "paper_quant_ph_0608239_gb300", "csrc"),
+                               "-o", exe, src])
+        out = subprocess.check_output([exe], timeout=600).decode().split()
+    bad_exact, bad_slice, bad_bound, bad_err = (int(v) for v in out[:4])
+    worst, mean = float(out[4]), float(out[5])
+    print("worst %.3e (2^%.1f), mean %.3e (2^%.1f)" % (worst, __import__("math").log2(worst or 1e-300),
+                                                        mean, __import__("math").log2(mean or 1e-300)))
+    assert bad_slice == 0, out
+    assert bad_bound == 0 and bad_exact == 0, out
+    assert bad_err == 0 and worst <= 2.0 ** -43, out
+    assert mean <= 2.0 ** -47, out

@@ -103,7 +103,7 @@ def test_c2_prefix_elementwise_every_autotune_candidate(q, c2_prefix, dt):
 
     def check(c, prof):
         if c["fuse_k"]:
-            assert "fused_tensor_core" in prof or "dense_cuda_core" in prof, prof
+            assert "fused_tensor_core" in prof or "fused_tc_digits" in prof, prof
         else:
             assert "tile_pass" in prof, prof
         e, rel, fid = compare(st.get_state(), ref)
@@ -116,8 +116,8 @@ def test_c2_prefix_elementwise_every_autotune_candidate(q, c2_prefix, dt):
             assert abs(st.norm() - 1) < 1e-12
 
     seen = run_candidates(q, st, plan, x0, check)
-    if dt == "c64":  # the tensor-core widths are among the candidates
-        assert {4, 5} <= {c["fuse_k"] for c in seen}, seen
+    # the tensor-core widths are among the candidates
+    assert ({4, 5} if dt == "c64" else {5}) <= {c["fuse_k"] for c in seen}, seen
     plan.free()
     st.free()
 

@@ -490,7 +490,105 @@ def test_fused_blocks_circuit_c64(q, k, n):
     st.free()
 
 
-@pytest.mark.parametrize("dt,k", [("c128", 3), ("c128", 5), ("c128", 6), ("c64", 6)])
+# ------------------------- complex128 fused gates on the tensor cores (digits)
+@pytest.mark.parametrize("n,where", [(12, "low"), (12, "mixed"), (16, "high"), (16, "mixed"), (20, "mixed"),
+                                     (22, "high"), (22, "low")])
+def test_fused_tensor_cores_c128(q, n, where):
+    k = 5
+    rng = np.random.default_rng(170 + n + len(where))
+    if where == "low":
+        qs = list(rng.permutation(k))
+    elif where == "high":
+        qs = [int(x) for x in rng.permutation(np.arange(n - k, n))]
+    else:
+        qs = [int(x) for x in rng.permutation(n)[:k]]
+    Z = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+    U, _ = np.linalg.qr(Z)
+    psi = rand_state(n, 190 + n)
+    ref = oracle.apply_dense(psi.copy(), n, qs, U)
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    st.profile(True)
+    st.apply_fused(qs, U)
+    prof = st.profile_read()
+    assert "fused_tc_digits" in prof, prof  # the tcgen05 digit-slice kernel ran
+    e = err(st.get_state(), ref)
+    # the digit slices keep about 2^-47 of a group's largest magnitude
+    assert e < 1e-14, e
+    st.free()
+
+
+def test_fused_tensor_cores_c128_wide_range_and_zeros(q):
+    # groups with one large amplitude and the rest 2^-60 smaller, all-zero
+    # groups and exact zeros: every output against the oracle to 1e-12
+    # relative to its group's largest magnitude
+    n, k = 13, 5
+    rng = np.random.default_rng(5)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[::7] = rng.standard_normal(psi[::7].size) * 2.0 ** -60
+    psi[::97] = rng.standard_normal(psi[::97].size) + 1j * rng.standard_normal(psi[::97].size)
+    psi[1 << 12:(1 << 12) + 512] = 0.0
+    psi /= np.linalg.norm(psi)
+    qs = [0, 3, 7, 9, 12]
+    Z = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    U, _ = np.linalg.qr(Z)
+    ref = oracle.apply_dense(psi.copy(), n, qs, U)
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    st.profile(True)
+    st.apply_fused(qs, U)
+    assert "fused_tc_digits" in st.profile_read()
+    got = st.get_state()
+    assert err(got, ref) < 1e-14
+    zero = ref == 0
+    assert np.all(got[zero] == 0)
+    st.free()
+
+
+def test_fused_c128_non_unitary_falls_back(q):
+    # an entry outside (-2, 2) is beyond the digit scheme: the gate runs on
+    # the CUDA cores in FP64 instead, with the same result
+    n, k = 12, 5
+    rng = np.random.default_rng(9)
+    U = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    U[3, 4] = 3.5
+    psi = rand_state(n, 4)
+    ref = oracle.apply_dense(psi.copy(), n, list(range(k)), U)
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    st.profile(True)
+    st.apply_fused(list(range(k)), U)
+    prof = st.profile_read()
+    assert "dense_cuda_core" in prof and "fused_tc_digits" not in prof, prof
+    assert err(st.get_state(), ref) < 1e-12 * float(np.max(np.abs(ref)))
+    st.free()
+
+
+@pytest.mark.parametrize("n", [12, 13, 18, 21])
+def test_fused_blocks_circuit_c128_tensor_cores(q, n):
+    gates = inputs.random_circuit(n, 8, seed=400 + n)
+    rng = np.random.default_rng(n + 40)
+    gates += [g for g in controlled_gates(rng, n, 12) if len(g.controls) + len(g.targets) <= 5]
+    x0 = inputs.random_basis(n, seed=n + 3)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, "c128")
+    st.set_basis(x0)
+    st.profile(True)
+    plan = st.plan(gates, fuse_k=5)
+    plan.run()
+    prof = st.profile_read()
+    assert "fused_tc_digits" in prof and "tile_pass" not in prof and "dense_cuda_core" not in prof, prof
+    assert err(st.get_state(), ref) < 1e-12
+    assert abs(st.norm() - 1) < 1e-12
+    # the one-shot path (gate list in host memory) gives the same state
+    st.set_basis(x0)
+    st.run(gates, fuse_k=5)
+    assert err(st.get_state(), ref) < 1e-12
+    plan.free()
+    st.free()
+
+
+@pytest.mark.parametrize("dt,k", [("c128", 3), ("c128", 6), ("c64", 6)])
 def test_fused_blocks_cuda_cores(q, dt, k):
     # fusion widths and precisions the tensor-core kernel does not take run
     # as dense blocks on the CUDA cores (FP64 for complex128)
