@@ -650,8 +650,12 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
             FusedMap fm;
             fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
             const uint16_t *bm = reinterpret_cast<const uint16_t *>(d_bmats + per * b);
+            // double-float form between the first and the last block
+            const bool first = b == 0, last = b + 1 == P.blocks.size();
             CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
-                      [&] { return launch_fused_tc128(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream); },
+                      [&] {
+                          return launch_fused_tc128(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream, first, last);
+                      },
                       P.blocks[b].flops),
                "fused block (tensor cores, complex128)");
         }
@@ -984,7 +988,7 @@ qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const doub
             CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
                       [&] {
                           return launch_fused_tc128(h->amp, g, fm, static_cast<const uint16_t *>(h->d_dense),
-                                                    h->d_err, h->sm_count, h->stream);
+                                                    h->d_err, h->sm_count, h->stream, true, true);
                       },
                       flops),
                "fused gate (tensor cores, complex128)");

@@ -1,43 +1,43 @@
-// digits.cuh -- complex128 dense blocks on the bf16 tensor cores: IEEE
-// doubles cut into bf16 digit slices whose products the tensor cores sum
-// exactly (the Ozaki splitting scheme for error-free matrix products,
-// Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012), and its
-// tensor-core forms, Mukunoki et al., ISC 2020).
+// digits.cuh -- complex128 dense blocks on the bf16 tensor cores: reals cut
+// into bf16 digit slices whose products the tensor cores sum exactly (the
+// Ozaki splitting scheme for error-free matrix products: Ozaki, Ogita, Oishi
+// and Rump, Numer. Algorithms 59 (2012); its tensor-core forms: Mukunoki et
+// al., ISC 2020).
 //
 // A dense block a' = U a (Sec. III.A's gates multiplied into one 2^k x 2^k
 // matrix) is, with complex numbers as real 2x2 blocks, a real product of the
-// group's 2K = 2^(k+1) reals with a 2K x 2K matrix.  Every real x of a group
-// is written in fixed point against the group's largest exponent e
-// (2^e <= max |x| < 2^(e+1)):
+// group's 2K = 2^(k+1) reals with a 2K x 2K matrix.
 //
-//     X = x 2^(52 - e),  |X| < 2^53   (bits below 2^0 are truncated),
-//     X = sum_{i=0..5} d_i 2^(45 - 9i),  d_i integers in [-256, 256],
+// Digits.  Every real of a group is scaled by 2^-e, e the exponent of the
+// group's largest magnitude, so |v'| < 2, and written as six digits on the
+// grids w_i = 2^(-7 - 9i):
 //
-// six signed base-2^9 digits obtained from the bit fields of X + C with
-// C = 256 (2^45 + 2^36 + 2^27 + 2^18 + 2^9 + 1) (field value f, digit
-// f - 256), so the split of X is exact.  The matrix entries (|u| <= 1) get
-// the same six digits c_j against e = 0.  Slice i holds d_i 2^(-9i) as bf16,
-// which is exact: |d_i| <= 256 needs at most 8 significand bits.  Then
+//     v' = sum_{i=0..5} d_i,   d_i = (integer in [-256, 256]) * w_i,
 //
-//     x u = 2^(e - 14) sum_{i,j} d_i c_j 2^(-9(i + j)),
+// up to a remainder below w_5 / 2.  Every digit is a bf16 number (at most 8
+// significand bits).  The matrix entries (|u| <= 1) get six digits c_j on the
+// same grids without scaling.  Then a product of slices i and j is an integer
+// times 2^(-14 - 9(i + j)), and
 //
-// and the tensor cores form the slice products A_i B_j^T (bf16 inputs, exact
-// products, FP32 accumulation) grouped by level L = i + j, L <= 5 (21
-// products).  Over a row of 2K = 64 products a level sums at most
-// (L + 1) 64 2^16 (and level 0 at most 2^18, since |c_0| <= 128 with a unit
-// row norm): below 2^24 for L <= 3, so the accumulators of levels 0..3 hold
-// their sums exactly; levels 4 and 5 share one FP32 accumulator (their
-// rounding is below 2^-50 of the result).  The dropped levels 6..10 and the
-// truncation of X bound the error of an output by about 2^-44 of the group's
-// largest magnitude (typically 2^-48), the class of the double-float tile
-// passes.
+//     (U a)_r = 2^e sum_L sum_{i + j = L} (A_i B_j^T)_r,   L = 0 .. 5
 //
-// The epilogue adds the five accumulators in double-float (two FP32 values,
-// Knuth's two-sum), converts the pair to an IEEE double with integer
-// operations and scales by 2^(e - 14) through the exponent field.  Doubles
-// below 2^-1022 (subnormals) are read as zero.
+// (21 products).  Over a row of 2K = 64 products a level L sums at most
+// (L + 1) 64 2^16 integer units (level 0 at most 2^18, since |c_0| <= 128
+// and a unitary row has unit norm): below 2^24 for L <= 3, so the FP32
+// accumulators of levels 0..3 hold their sums exactly.  Levels 4 and 5 share
+// one accumulator; its rounding stays below 2^-50 of the result.  The dropped
+// levels 6..10 and the last remainder bound an output's error by about 2^-44
+// of the group's largest magnitude (typically 2^-48), the class of the
+// double-float tile passes.
 //
-// The functions compile for the host as well, so the split, the exact level
+// The state is read and written in double-float form (hi + lo, two floats):
+// the split runs on FP32 additions (round to the grid by adding and
+// subtracting 1.5 * 2^23 * w_i, the remainder carried exactly as a pair), the
+// five accumulators are added in double-float (Knuth's two-sum) and scaled
+// back by 2^e.  The first block of a run converts IEEE doubles to this form
+// and the last one converts back, with the integer conversions of df64.cuh.
+//
+// Everything compiles for the host as well, so the split, the exact level
 // sums and the combination are checked on the CPU against long double.
 #pragma once
 
@@ -47,42 +47,80 @@
 
 namespace qsim {
 
-constexpr int kDigits = 6;        // digit slices per real
-constexpr int kDigitBits = 9;     // base 2^9, digits in [-256, 256]
-constexpr int kDigitLevels = 5;   // accumulators: levels 0, 1, 2, 3 and 4-5
-constexpr int kDigitExpShift = 14;  // x u = 2^(e - 14) * (level sums)
-constexpr uint64_t kDigitOffset =   // 256 (2^45 + 2^36 + 2^27 + 2^18 + 2^9 + 1)
+constexpr int kDigits = 6;          // digit slices per real
+constexpr int kDigitBits = 9;       // digits are integers in [-256, 256] on their grid
+constexpr int kDigitLevels = 5;     // accumulators: levels 0, 1, 2, 3 and 4-5
+
+// ---- matrix entries (host): exact integer digits ---------------------------
+// u (|u| < 2) in fixed point X = u 2^52 (truncated toward zero below 2^0),
+// X = sum_j c_j 2^(45 - 9j) with c_j in [-256, 256] read from the bit fields
+// of X + C, C = 256 (2^45 + 2^36 + 2^27 + 2^18 + 2^9 + 1) (field f, digit
+// f - 256); slice j holds c_j 2^(-7 - 9j).
+constexpr uint64_t kDigitOffset =
     (256ull << 45) | (256ull << 36) | (256ull << 27) | (256ull << 18) | (256ull << 9) | 256ull;
 
-// Biased exponent field of a double from its high word (0 for zero and
-// subnormals, which the split reads as zero).
-DF_HD uint32_t dg_bexp(uint32_t hi) { return (hi >> 20) & 0x7ffu; }
-
-// Fixed-point X + C of one real, the group's largest biased exponent Mg >= the
-// real's own (Mg = 0: an all-zero group).  |X| < 2^53; X + C lies in
-// [2^44, 2^54 + 2^45).
-DF_HD uint64_t dg_fixed(uint32_t hi, uint32_t lo, uint32_t Mg) {
-    const uint32_t be = dg_bexp(hi);
+DF_HD void dg_split_entry(double u, float (&d)[kDigits]) {
+    const uint64_t b = df_bits64(u);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t be = (hi >> 20) & 0x7ffu;  // 0: zero or subnormal, read as zero
     const uint64_t M = be ? ((uint64_t)((hi & 0xfffffu) | 0x100000u) << 32) | lo : 0ull;
-    const uint32_t s = Mg - be;  // >= 0
+    const uint32_t s = 1023u - (be < 1023u ? be : 1023u);
     uint64_t X = s < 64u ? M >> s : 0ull;
     if (hi & 0x80000000u) X = 0ull - X;
-    return X + kDigitOffset;
+    const uint64_t XC = X + kDigitOffset;
+    for (int j = 0; j < kDigits; j++) {
+        const int pos = 45 - kDigitBits * j;
+        const uint32_t f = j == 0 ? (uint32_t)(XC >> 45) : (uint32_t)(XC >> pos) & 511u;
+        d[j] = (float)((int)f - 256) * df_ffrom((uint32_t)(127 - 7 - kDigitBits * j) << 23);
+    }
 }
 
-// Digit i of a fixed-point value (X + C), as the bf16-exact float
-// d_i 2^(-9i).
+// ---- the state: FP32 digits of double-float values ------------------------
+// 2^-e and 2^e for a group whose largest hi has the float exponent field E
+// (E = 0: an all-zero group, scales 1 and zero digits).
+DF_HD float dg_scale_down(uint32_t E) { return df_ffrom(E ? (254u - E) << 23 : 127u << 23); }
+DF_HD float dg_scale_up(uint32_t E) { return df_ffrom(E ? E << 23 : 127u << 23); }
+
+// Digit i of the remainder (rh, rl): round rh + rl to the grid w_i, keep the
+// new remainder in rh (exact).
 template <int I>
-DF_HD float dg_digit(uint64_t XC) {
-    constexpr int pos = 45 - kDigitBits * I;
-    const uint32_t f = I == 0 ? (uint32_t)(XC >> 45) : (uint32_t)(XC >> pos) & 511u;
-    // float(2^23 + f) by its bit pattern, then one FMA that subtracts
-    // 2^23 + 256 and scales by 2^(-9i); every intermediate is exact
-    constexpr float sc = 1.0f / (float)(1ull << (kDigitBits * I));
-    return df_fma(df_ffrom(0x4b000000u | f), sc, -8388864.0f * sc);
+DF_HD float dg_step(float &rh, float rl) {
+    constexpr float M = 12582912.0f / (float)(1ull << (7 + kDigitBits * I));  // 1.5 * 2^23 * w_i
+    const float s = rh + rl;
+    const float d = (s + M) - M;
+    if (I < kDigits - 1) rh = rh - d;
+    return d;
 }
 
-// bf16 bit pattern of a float that bf16 holds exactly (the top half).
+// The six slices of (h + l) * scale, scale = dg_scale_down(E).
+DF_HD void dg_split_df(float h, float l, float scale, float (&d)[kDigits]) {
+    float rh = h * scale;
+    const float rl = l * scale;
+    d[0] = dg_step<0>(rh, rl);
+    d[1] = dg_step<1>(rh, rl);
+    d[2] = dg_step<2>(rh, rl);
+    d[3] = dg_step<3>(rh, rl);
+    d[4] = dg_step<4>(rh, rl);
+    d[5] = dg_step<5>(rh, rl);
+}
+
+// Sum of the five level accumulators (levels 0..3 exact, level 4-5 rounded)
+// as a normalised double-float, times scale = dg_scale_up(E).
+DF_HD df dg_combine_df(float a0, float a1, float a2, float a3, float a4, float scale) {
+    // a0 is a multiple of 2^-14 with |a0| <= 16, a1 a multiple of 2^-23 with
+    // |a1| < 0.6: either |a0| >= |a1| or the sum is exact, so the quick
+    // two-sum is error free
+    df s = quick_two_sum(a0, a1);
+    df t = two_sum(s.h, a2);
+    t.l += s.l;
+    s = quick_two_sum(t.h, t.l);
+    t = two_sum(s.h, a3);
+    t.l += s.l + a4;
+    s = quick_two_sum(t.h, t.l);
+    return df{s.h * scale, s.l * scale};
+}
+
+// bf16 bit pattern of a float that bf16 holds exactly (its top half).
 DF_HD uint32_t dg_bf16(float v) { return df_fbits(v) >> 16; }
 
 // Two bf16 values in one 32-bit word: lo in bits 0..15, hi in 16..31 (the
@@ -93,37 +131,6 @@ DF_HD uint32_t dg_pack(float lo, float hi) {
 #else
     return dg_bf16(lo) | (dg_bf16(hi) << 16);
 #endif
-}
-
-// Sum of the five level accumulators (levels 0..3 exact, level 4-5 rounded)
-// times 2^(e - 14), e = Mg - 1023, as an IEEE double.
-DF_HD double dg_combine(float a0, float a1, float a2, float a3, float a4, uint32_t Mg) {
-    // a0 is an integer and a1 a multiple of 2^-9 with |a1| <= 2^14: either
-    // |a0| >= |a1| or the sum is exact, so the quick two-sum is error free
-    df s = quick_two_sum(a0, a1);
-    df t = two_sum(s.h, a2);
-    t.l += s.l;
-    s = quick_two_sum(t.h, t.l);
-    t = two_sum(s.h, a3);
-    t.l += s.l + a4;
-    s = quick_two_sum(t.h, t.l);
-    if (s.h == 0.0f || Mg == 0u) return 0.0;
-    const uint64_t b = df_bits64(df_to_double(s));
-    const int e = (int)((b >> 52) & 0x7ffu) + (int)Mg - 1023 - kDigitExpShift;
-    if (e <= 0) return 0.0;  // below the normal range: flushed
-    return df_from_bits64((b & ~(0x7ffull << 52)) | ((uint64_t)e << 52));
-}
-
-// The six digit slices of a matrix entry u, |u| <= 1 (e = 0, Mg = 1023).
-DF_HD void dg_split_entry(double u, float (&d)[kDigits]) {
-    const uint64_t bits = df_bits64(u);
-    const uint64_t XC = dg_fixed((uint32_t)(bits >> 32), (uint32_t)bits, 1023u);
-    d[0] = dg_digit<0>(XC);
-    d[1] = dg_digit<1>(XC);
-    d[2] = dg_digit<2>(XC);
-    d[3] = dg_digit<3>(XC);
-    d[4] = dg_digit<4>(XC);
-    d[5] = dg_digit<5>(XC);
 }
 
 // Accumulator of the product of slices i and j.

@@ -6,13 +6,18 @@
 //
 //     D (rows = groups, 64 columns) = A (groups x 64) * B^T,
 //
-// a row of A being the group's 64 reals (re, im, re, im, ...).  The doubles
+// a row of A being the group's 64 reals (re, im, re, im, ...).  The reals
 // are cut into six bf16 digit slices against the group's largest exponent,
 // and U's entries into six slices of their own (digits.cuh: the split, the
 // exact level sums and the combination, with their error bounds).  The 21
 // slice products A_i B_j^T with i + j <= 5 run as tcgen05.mma kind::f16
 // (bf16 inputs, FP32 accumulation in tensor memory), accumulated per level
 // (levels 0, 1, 2, 3 exactly, levels 4 and 5 together).
+//
+// Between the blocks of a run the state stays in double-float form: the same
+// 16 bytes of an amplitude hold (re.hi, re.lo, im.hi, im.lo) as floats.  The
+// first block of a run reads IEEE doubles (IN_IEEE) and the last one writes
+// them (OUT_IEEE), converting with integer operations (df64.cuh).
 //
 // One CTA per SM, 512 threads: the four warps of a tensor-memory lane
 // quarter share its 32 groups, each taking one quarter of a group's 32
@@ -109,6 +114,7 @@ __device__ __forceinline__ void sts_u4(uint32_t addr, uint4 v) {
 // barrier of the four warps sharing a tensor-memory lane quarter
 __device__ __forceinline__ void quarter_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
+template <bool IN_IEEE, bool OUT_IEEE>
 __global__ void __launch_bounds__(kThreads128, 1)
     k_fused_tc_c128(double2 *__restrict__ a, TileGeom g, FusedMap fm, const uint16_t *__restrict__ bmat,
                     uint32_t *err, uint64_t ntiles) {
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(kThreads128, 1)
     unsigned char *s_buf0 = smem_raw + kBBytes;       // two tile buffers
     __shared__ __align__(8) uint64_t bar_ld[2], bar_mma, bar_b;
     __shared__ uint32_t tmem_base_s;
-    __shared__ uint32_t s_max[4][128];  // per K quarter, per group: largest exponent field
+    __shared__ uint32_t s_max[4][128];  // per K quarter, per group: largest hi exponent field
     __shared__ int s_hb[kMaxH128];
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
@@ -173,10 +179,10 @@ __global__ void __launch_bounds__(kThreads128, 1)
     uint64_t tile = blockIdx.x;
     // fetches issued (warp 0) and awaited (every thread) per buffer, so that
     // an aborting CTA can let the copies in flight land before it leaves
-    uint32_t n_issued[2] = {0u, 0u}, n_done[2] = {0u, 0u};
+    uint32_t issued0 = 0u, issued1 = 0u, done0 = 0u, done1 = 0u;
     if (warp == 0) {
-        if (tile < ntiles) issue_load(tile, 0), n_issued[0]++;
-        if (tile + stride < ntiles) issue_load(tile + stride, 1), n_issued[1]++;
+        if (tile < ntiles) issue_load(tile, 0), issued0++;
+        if (tile + stride < ntiles) issue_load(tile + stride, 1), issued1++;
     }
     bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128)) != 0;
 
@@ -197,50 +203,44 @@ __global__ void __launch_bounds__(kThreads128, 1)
     uint32_t i = 0;
     for (; tile < ntiles && !aborted; tile += stride, i++) {
         const int b = (int)(i & 1u);
-        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld[b], n_done[b] & 1u, kWaitBudget128)) != 0;
+        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld[b], (b ? done1 : done0) & 1u, kWaitBudget128)) != 0;
         if (aborted) break;
-        n_done[b]++;
+        if (b) done1++; else done0++;
         const uint32_t sbuf = smem_u32(buf(b));
 
-        // ---- split: 8 amplitudes -> 16 fixed-point reals -> 6 digit slices
-        uint32_t hw[16], lw[16];
+        // ---- split: 8 amplitudes -> 16 double-float reals -> 6 digit slices
+        float vh[16], vl[16];
         uint32_t mx = 0;
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const uint4 v = lds_u4(sbuf + 16u * coff[j]);
-            lw[2 * j] = v.x;
-            hw[2 * j] = v.y;
-            lw[2 * j + 1] = v.z;
-            hw[2 * j + 1] = v.w;
-            mx = max(mx, max(v.y & 0x7ff00000u, v.w & 0x7ff00000u));
+            if (IN_IEEE) {
+                const df re = df_from_double(__hiloint2double((int)v.y, (int)v.x));
+                const df im = df_from_double(__hiloint2double((int)v.w, (int)v.z));
+                vh[2 * j] = re.h, vl[2 * j] = re.l, vh[2 * j + 1] = im.h, vl[2 * j + 1] = im.l;
+            } else {
+                vh[2 * j] = __uint_as_float(v.x), vl[2 * j] = __uint_as_float(v.y);
+                vh[2 * j + 1] = __uint_as_float(v.z), vl[2 * j + 1] = __uint_as_float(v.w);
+            }
+            mx = max(mx, max(__float_as_uint(vh[2 * j]) & 0x7f800000u, __float_as_uint(vh[2 * j + 1]) & 0x7f800000u));
         }
         s_max[qq][m] = mx;
         quarter_sync(1u + (uint32_t)lq);
-        const uint32_t Mg = max(max(s_max[0][m], s_max[1][m]), max(s_max[2][m], s_max[3][m])) >> 20;
-        uint64_t xc[16];
-#pragma unroll
-        for (int r = 0; r < 16; r++) xc[r] = dg_fixed(hw[r], lw[r], Mg);
-        const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;
+        const uint32_t Eg = max(max(s_max[0][m], s_max[1][m]), max(s_max[2][m], s_max[3][m])) >> 23;
         {
-            uint32_t w[8];
+            const float sd = dg_scale_down(Eg);
+            uint32_t w[kDigits][8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<0>(xc[2 * j]), dg_digit<0>(xc[2 * j + 1]));
-            tmem_st8(acol + 0, w);
+            for (int j = 0; j < 8; j++) {
+                float dr[kDigits], di[kDigits];
+                dg_split_df(vh[2 * j], vl[2 * j], sd, dr);
+                dg_split_df(vh[2 * j + 1], vl[2 * j + 1], sd, di);
 #pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<1>(xc[2 * j]), dg_digit<1>(xc[2 * j + 1]));
-            tmem_st8(acol + 8, w);
+                for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
+            }
+            const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;
 #pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<2>(xc[2 * j]), dg_digit<2>(xc[2 * j + 1]));
-            tmem_st8(acol + 16, w);
-#pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<3>(xc[2 * j]), dg_digit<3>(xc[2 * j + 1]));
-            tmem_st8(acol + 24, w);
-#pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<4>(xc[2 * j]), dg_digit<4>(xc[2 * j + 1]));
-            tmem_st8(acol + 32, w);
-#pragma unroll
-            for (int j = 0; j < 8; j++) w[j] = dg_pack(dg_digit<5>(xc[2 * j]), dg_digit<5>(xc[2 * j + 1]));
-            tmem_st8(acol + 40, w);
+            for (int d = 0; d < kDigits; d++) tmem_st8(acol + 8u * d, w[d]);
         }
         tmem_st_wait();
         tc_fence_before();
@@ -280,17 +280,24 @@ __global__ void __launch_bounds__(kThreads128, 1)
             for (int lv = 0; lv < kDigitLevels; lv++)
                 tmem_ld16(tmem + lane_off + (uint32_t)(kReals * lv + 16 * qq), acc[lv]);
             tmem_ld_wait();
+            const float su = dg_scale_up(Eg);
 #pragma unroll
             for (int j = 0; j < 8; j++) {
-                const double re = dg_combine(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
-                                             __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]),
-                                             __uint_as_float(acc[4][2 * j]), Mg);
-                const double im = dg_combine(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
-                                             __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
-                                             __uint_as_float(acc[4][2 * j + 1]), Mg);
-                const uint64_t rb = (uint64_t)__double_as_longlong(re), ib = (uint64_t)__double_as_longlong(im);
-                sts_u4(sbuf + 16u * coff[j], make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (uint32_t)ib,
-                                                        (uint32_t)(ib >> 32)));
+                const df re = dg_combine_df(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
+                                            __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]),
+                                            __uint_as_float(acc[4][2 * j]), su);
+                const df im = dg_combine_df(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
+                                            __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
+                                            __uint_as_float(acc[4][2 * j + 1]), su);
+                uint4 o;
+                if (OUT_IEEE) {
+                    const uint64_t rb = df_bits64(df_to_double(re)), ib = df_bits64(df_to_double(im));
+                    o = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (uint32_t)ib, (uint32_t)(ib >> 32));
+                } else {
+                    o = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
+                                   __float_as_uint(im.l));
+                }
+                sts_u4(sbuf + 16u * coff[j], o);
             }
         }
         tc_fence_before();
@@ -307,15 +314,14 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 bulk_wait_read_all();
                 __syncwarp();
                 issue_load(tile + 2 * stride, b);
-                n_issued[b]++;
+                if (b) issued1++; else issued0++;
             }
         }
     }
     if (aborted && tid == 0) atomicExch(err, kErrTimeout);
     if (aborted && warp == 0) {  // let fetches in flight land before the CTA leaves
-#pragma unroll
-        for (int b = 0; b < 2; b++)
-            for (; n_done[b] < n_issued[b]; n_done[b]++) mbar_wait_bounded(&bar_ld[b], n_done[b] & 1u, kWaitBudget128);
+        for (; done0 < issued0; done0++) mbar_wait_bounded(&bar_ld[0], done0 & 1u, kWaitBudget128);
+        for (; done1 < issued1; done1++) mbar_wait_bounded(&bar_ld[1], done1 & 1u, kWaitBudget128);
     }
     if (warp == 0) bulk_wait_all();
     tc_fence_before();
@@ -348,7 +354,7 @@ bool fused_tc128_prepare_b(const double *U, uint16_t *out) {
                 dg_split_entry(v[e], d);
                 for (int j = 0; j < kDigits; j++) {
                     out[(j * kSliceBytes + bcanon_off((uint32_t)nn[e], (uint32_t)kk[e])) / 2] = (uint16_t)dg_bf16(d[j]);
-                    rowsum[nn[e]][j] += std::fabs(std::ldexp((double)d[j], kDigitBits * j));
+                    rowsum[nn[e]][j] += std::fabs(std::ldexp((double)d[j], 7 + kDigitBits * j));  // |c_j|
                 }
             }
         }
@@ -367,16 +373,27 @@ size_t fused_tc128_b_bytes() { return kBBytes; }
 
 bool fused_tc128_supported(int k, int n) { return k == kK && n >= kTileBits; }
 
-cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
-                               uint32_t *err, int sm_count, cudaStream_t s) {
-    if (g.L + g.H != kTileBits || g.H > kMaxH128 || g.L < 1) return cudaErrorInvalidValue;
+template <bool IN_IEEE, bool OUT_IEEE>
+static cudaError_t launch_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat, uint32_t *err,
+                                int sm_count, cudaStream_t s) {
     const size_t smem = kBBytes + 2 * (size_t)kTileBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_fused_tc_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tc_c128<IN_IEEE, OUT_IEEE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t ntiles = 1ull << (g.n - kTileBits);
     uint64_t grid = ntiles < (uint64_t)sm_count ? ntiles : (uint64_t)sm_count;
-    k_fused_tc_c128<<<(unsigned)grid, kThreads128, smem, s>>>(static_cast<double2 *>(amp), g, fm, bmat, err, ntiles);
+    k_fused_tc_c128<IN_IEEE, OUT_IEEE>
+        <<<(unsigned)grid, kThreads128, smem, s>>>(static_cast<double2 *>(amp), g, fm, bmat, err, ntiles);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
+                               uint32_t *err, int sm_count, cudaStream_t s, bool in_ieee, bool out_ieee) {
+    if (g.L + g.H != kTileBits || g.H > kMaxH128 || g.L < 1) return cudaErrorInvalidValue;
+    if (in_ieee && out_ieee) return launch_tc128<true, true>(amp, g, fm, bmat, err, sm_count, s);
+    if (in_ieee) return launch_tc128<true, false>(amp, g, fm, bmat, err, sm_count, s);
+    if (out_ieee) return launch_tc128<false, true>(amp, g, fm, bmat, err, sm_count, s);
+    return launch_tc128<false, false>(amp, g, fm, bmat, err, sm_count, s);
 }
 
 }  // namespace qsim

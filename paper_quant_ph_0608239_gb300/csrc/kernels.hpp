@@ -194,12 +194,14 @@ cudaError_t launch_fused_tc(void *amp, int k, const TileGeom &g, const FusedMap 
 // bf16 digit slices, exact level sums; n >= 12): bmat = device copy of
 // fused_tc128_prepare_b's output (fused_tc128_b_bytes() bytes), which
 // returns false for a matrix the scheme cannot take exactly (an entry
-// outside (-2, 2)).
+// outside (-2, 2)).  in_ieee / out_ieee: the state is read / written as
+// IEEE doubles, else in the double-float form kept between the blocks of a
+// run (re.hi, re.lo, im.hi, im.lo as floats).
 bool fused_tc128_supported(int k, int n);
 size_t fused_tc128_b_bytes();
 bool fused_tc128_prepare_b(const double *U, uint16_t *out);
 cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
-                               uint32_t *err, int sm_count, cudaStream_t s);
+                               uint32_t *err, int sm_count, cudaStream_t s, bool in_ieee, bool out_ieee);
 
 // ------------------------------------------------------------ batches
 struct BatchCircuit {

@@ -1,14 +1,16 @@
 """Digit-slice arithmetic of the complex128 tensor-core blocks, checked on the CPU.
 
-csrc/digits.cuh compiles for the host as well.  A C++ driver cuts groups of
-64 doubles and rows of a 64 x 64 real matrix (the real form of a random 32 x 32
-complex unitary) into the six bf16 digit slices, forms the 21 slice products
-level by level the way the tensor cores do (exact products, FP32 accumulation
-after every 16-element K step), combines the five accumulators and compares
-with the exact dot product of the original doubles in long double:
+csrc/digits.cuh compiles for the host as well.  A C++ driver takes groups of
+64 doubles (in the double-float form the kernel works in) and rows of a 64 x 64
+real matrix (the real form of a random 32 x 32 complex unitary), cuts them into
+the six bf16 digit slices, forms the 21 slice products level by level the way
+the tensor cores do (exact products, FP32 accumulation after every 16-element
+K step), combines the five accumulators and compares with the exact dot
+product of the original doubles in long double:
 
-  * the slices rebuild the fixed-point value exactly and every slice value is
-    a bf16 number (its low 16 bits are zero);
+  * every digit is an integer in [-256, 256] on its grid and a bf16 number
+    (its low 16 bits are zero); the digits rebuild the scaled value to half
+    the last grid step, and a matrix entry to 2^-52;
   * the FP32 accumulators of levels 0..3 equal the exact level sums (the
     sums of |products| stay below 2^24), for random and adversarial inputs;
   * the combined result is within 2^-43 of max|x| * ||u_row||_1 of the exact
@@ -96,36 +98,44 @@ int main() {
     for (int trial = 0; trial < 3000; trial++) {
         rand_unitary_real(B, trial % 7 == 3 ? 1 : trial % 7 == 5 ? 2 : 0);
         group(x, trial % 11 < 6 ? 0 : trial % 11 - 5);
-        // slices of the group (common exponent) and of the matrix
-        uint32_t Mg = 0;
-        for (double v : x) {
-            uint64_t b = df_bits64(v);
-            uint32_t be = dg_bexp((uint32_t)(b >> 32));
-            if (be > Mg) Mg = be;
+        // the group in double-float form (the first block's conversion), its
+        // largest hi exponent, and the slices
+        df v[64];
+        uint32_t E = 0;
+        for (int k = 0; k < 64; k++) {
+            v[k] = df_from_double(x[k]);
+            const uint32_t ek = (df_fbits(v[k].h) >> 23) & 0xffu;
+            if (ek > E) E = ek;
         }
+        const float sd = dg_scale_down(E), su = dg_scale_up(E);
         float A[kDigits][64], Bd[kDigits][64][64];
         for (int k = 0; k < 64; k++) {
-            const uint64_t b = df_bits64(x[k]);
-            const uint64_t XC = dg_fixed((uint32_t)(b >> 32), (uint32_t)b, Mg);
-            A[0][k] = dg_digit<0>(XC); A[1][k] = dg_digit<1>(XC); A[2][k] = dg_digit<2>(XC);
-            A[3][k] = dg_digit<3>(XC); A[4][k] = dg_digit<4>(XC); A[5][k] = dg_digit<5>(XC);
-            // the slices rebuild X exactly: sum d_i 2^(45 - 9i) = XC - C
-            LD X = 0;
+            float d[kDigits];
+            dg_split_df(v[k].h, v[k].l, sd, d);
+            LD sum = 0;
             for (int i = 0; i < kDigits; i++) {
-                X += (LD)A[i][k] * std::ldexp((LD)1, 45);  // d_i 2^(-9i) 2^45
-                if ((df_fbits(A[i][k]) & 0xffffu) != 0u) bad_slice++;
-                if (std::fabs(A[i][k]) > std::ldexp(256.0f, -9 * i)) bad_slice++;
+                A[i][k] = d[i];
+                const LD w = std::ldexp((LD)1, -7 - kDigitBits * i);
+                const LD q = (LD)d[i] / w;
+                if (q != std::floor(q) || std::fabs(q) > 256) bad_slice++;
+                if ((df_fbits(d[i]) & 0xffffu) != 0u) bad_slice++;
+                sum += d[i];
             }
-            if (X != (LD)(int64_t)(XC - kDigitOffset)) bad_slice++;
+            // the digits rebuild the scaled value up to half the last grid step
+            const LD exact = ((LD)v[k].h + (LD)v[k].l) * (LD)sd;
+            if (std::fabs(sum - exact) > std::ldexp((LD)1, -53) + std::ldexp((LD)1, -66)) bad_slice++;
         }
         for (int n = 0; n < 64; n++)
             for (int k = 0; k < 64; k++) {
                 float d[kDigits];
                 dg_split_entry(B[n * 64 + k], d);
+                LD sum = 0;
                 for (int j = 0; j < kDigits; j++) {
                     Bd[j][n][k] = d[j];
+                    sum += d[j];
                     if ((df_fbits(d[j]) & 0xffffu) != 0u) bad_slice++;
                 }
+                if (std::fabs(sum - (LD)B[n * 64 + k]) > std::ldexp((LD)1, -52)) bad_slice++;
             }
         for (int n = 0; n < 64; n++) {
             // the tensor cores: 4 K steps of 16, exact products, FP32 accumulation
@@ -146,20 +156,23 @@ int main() {
                     }
             for (int L = 0; L < 4; L++) {
                 if ((LD)acc[L] != exact[L]) bad_exact++;
-                if (mag[L] * std::ldexp((LD)1, 9 * L) >= std::ldexp((LD)1, 24)) bad_bound++;
+                // in integer units of the level, 2^(-14 - 9L)
+                if (mag[L] * std::ldexp((LD)1, 14 + 9 * L) >= std::ldexp((LD)1, 24)) bad_bound++;
             }
-            const double got = dg_combine(acc[0], acc[1], acc[2], acc[3], acc[4], Mg);
+            const df got = dg_combine_df(acc[0], acc[1], acc[2], acc[3], acc[4], su);
             LD ref = 0, scale = 0, xmax = 0;
             for (int k = 0; k < 64; k++) {
                 ref += (LD)x[k] * (LD)B[n * 64 + k];
                 scale += std::fabs((LD)B[n * 64 + k]);
                 if (std::fabs((LD)x[k]) > xmax) xmax = std::fabs((LD)x[k]);
             }
+            const LD g = (LD)got.h + (LD)got.l;
             if (xmax == 0) {
-                if (got != 0.0) bad_err++;
+                if (g != 0) bad_err++;
                 continue;
             }
-            const double e = (double)(std::fabs((LD)got - ref) / (xmax * scale));
+            if (std::fabs((LD)got.l) > std::fabs((LD)got.h) * std::ldexp((LD)1, -23)) bad_err++;  // normalised
+            const double e = (double)(std::fabs(g - ref) / (xmax * scale));
             if (e > worst) worst = e;
             sum_typ += e;
             cnt++;
