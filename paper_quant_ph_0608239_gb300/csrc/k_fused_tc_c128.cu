@@ -91,6 +91,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r0), "r"(r1),
+                 "r"(r2), "r"(r3)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -114,23 +120,31 @@ __device__ __forceinline__ void sts_u4(uint32_t addr, uint4 v) {
 // barrier of the four warps sharing a tensor-memory lane quarter
 __device__ __forceinline__ void quarter_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
+// barrier of the 512 compute threads (id 5), with an OR vote
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 5, 512;" ::: "memory"); }
+__device__ __forceinline__ bool compute_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 5, 512, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(r) : "r"((uint32_t)v) : "memory");
+    return r != 0;
+}
+
 template <bool IN_IEEE, bool OUT_IEEE>
 __global__ void __launch_bounds__(kThreads128, 1)
     k_fused_tc_c128(double2 *__restrict__ a, TileGeom g, FusedMap fm, const uint16_t *__restrict__ bmat,
                     uint32_t *err, uint64_t ntiles) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *s_b = smem_raw;                    // six B slices
-    unsigned char *s_buf0 = smem_raw + kBBytes;       // two tile buffers
+    unsigned char *s_buf0 = smem_raw + kBBytes;       // two input buffers
     __shared__ __align__(8) uint64_t bar_ld[2], bar_mma, bar_b;
     __shared__ uint32_t tmem_base_s;
-    __shared__ uint32_t s_max[4][128];  // per K quarter, per group: largest hi exponent field
+    __shared__ uint32_t s_max[2][4][128];  // per tile parity, K quarter, group: largest hi exponent field
     __shared__ int s_hb[kMaxH128];
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
     const uint32_t run_bytes = 16u << L;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lq = warp & 3, qq = warp >> 2;  // lane quarter, K quarter
-    const uint32_t m = (uint32_t)(32 * lq + lane);
 
     if (tid == 0) {
 #pragma unroll
@@ -149,9 +163,8 @@ __global__ void __launch_bounds__(kThreads128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
-    const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
 
-    auto run_off = [&](uint32_t j) {
+    auto run_off = [&](uint32_t j) {  // bits of run j deposited at the high tile bits
         uint64_t o = 0;
         for (int k = 0; k < H; k++) o |= (uint64_t)((j >> k) & 1u) << s_hb[k];
         return o;
@@ -162,93 +175,99 @@ __global__ void __launch_bounds__(kThreads128, 1)
         return base;
     };
     auto buf = [&](int b) { return s_buf0 + (size_t)b * kTileBytes; };
-    auto issue_load = [&](uint64_t tile, int b) {  // warp 0
-        const uint64_t base = tile_base(tile);
+    const uint64_t stride = gridDim.x;
+    // this CTA's tiles: blockIdx.x + i * stride, i < count
+    const uint32_t count = blockIdx.x < ntiles ? (uint32_t)((ntiles - 1 - blockIdx.x) / stride + 1) : 0u;
+
+    // fetch of tile i into buffer i & 1 (warp 0); the counts let an aborting
+    // CTA wait for the copies in flight before it leaves
+    uint32_t issued0 = 0u, issued1 = 0u;
+    auto issue_load = [&](uint32_t i) {
+        const int b = (int)(i & 1u);
+        const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * stride);
         if (lane == 0) mbar_arrive_expect_tx(&bar_ld[b], kTileBytes);
         __syncwarp();
         double2 *dst = reinterpret_cast<double2 *>(buf(b));
         for (uint32_t j = lane; j < nruns; j += 32)
             bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[b]);
+        if (b) issued1++; else issued0++;
     };
-
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar_b, kBBytes);
         bulk_g2s(s_b, bmat, kBBytes, &bar_b);
     }
-    const uint64_t stride = gridDim.x;
-    uint64_t tile = blockIdx.x;
-    // fetches issued (warp 0) and awaited (every thread) per buffer, so that
-    // an aborting CTA can let the copies in flight land before it leaves
-    uint32_t issued0 = 0u, issued1 = 0u, done0 = 0u, done1 = 0u;
     if (warp == 0) {
-        if (tile < ntiles) issue_load(tile, 0), issued0++;
-        if (tile + stride < ntiles) issue_load(tile + stride, 1), issued1++;
+        if (count > 0) issue_load(0);
+        if (count > 1) issue_load(1);
     }
-    bool aborted = __syncthreads_or(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128)) != 0;
+    {
+        // ---- group m (tensor-memory lane), K quarter qq
+        const int lq = warp & 3, qq = warp >> 2;
+        const uint32_t m = (uint32_t)(32 * lq + lane);
+        const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
+        uint32_t ibase = 0;
+#pragma unroll
+        for (int b = 0; b < kTileBits - kK; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+        uint32_t wc[kK];
+#pragma unroll
+        for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
+        // this thread's amplitudes: columns 8 qq + j, j < 8; their tile
+        // indices (shared memory) and offsets from the tile's base (global)
+        const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
+        const uint32_t lowmask = (1u << L) - 1u;
+        auto goff = [&](uint32_t t) { return (uint64_t)(t & lowmask) | run_off(t >> L); };
+        const uint64_t gq = goff(qbase), gc0 = goff(wc[0]), gc1 = goff(wc[1]), gc2 = goff(wc[2]);
+        auto coff = [&](int j) {
+            return qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
+        };
 
-    // tile index of group m and of the block's columns
-    uint32_t ibase = 0;
-#pragma unroll
-    for (int b = 0; b < kTileBits - kK; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
-    uint32_t wc[kK];
-#pragma unroll
-    for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
-    // this thread's amplitudes are columns 8 qq + j, j < 8
-    const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
-    uint32_t coff[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++)
-        coff[j] = qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
+        bool aborted = compute_any(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128));
+        uint32_t Eg_next = 0, Eg = 0;
+        const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;  // this thread's A columns
 
-    uint32_t i = 0;
-    for (; tile < ntiles && !aborted; tile += stride, i++) {
-        const int b = (int)(i & 1u);
-        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_ld[b], (b ? done1 : done0) & 1u, kWaitBudget128)) != 0;
-        if (aborted) break;
-        if (b) done1++; else done0++;
-        const uint32_t sbuf = smem_u32(buf(b));
-
-        // ---- split: 8 amplitudes -> 16 double-float reals -> 6 digit slices
-        float vh[16], vl[16];
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const uint4 v = lds_u4(sbuf + 16u * coff[j]);
-            if (IN_IEEE) {
-                const df re = df_from_double(__hiloint2double((int)v.y, (int)v.x));
-                const df im = df_from_double(__hiloint2double((int)v.w, (int)v.z));
-                vh[2 * j] = re.h, vl[2 * j] = re.l, vh[2 * j + 1] = im.h, vl[2 * j + 1] = im.l;
-            } else {
-                vh[2 * j] = __uint_as_float(v.x), vl[2 * j] = __uint_as_float(v.y);
-                vh[2 * j + 1] = __uint_as_float(v.z), vl[2 * j + 1] = __uint_as_float(v.w);
-            }
-            mx = max(mx, max(__float_as_uint(vh[2 * j]) & 0x7f800000u, __float_as_uint(vh[2 * j + 1]) & 0x7f800000u));
-        }
-        s_max[qq][m] = mx;
-        quarter_sync(1u + (uint32_t)lq);
-        const uint32_t Eg = max(max(s_max[0][m], s_max[1][m]), max(s_max[2][m], s_max[3][m])) >> 23;
-        {
-            const float sd = dg_scale_down(Eg);
-            uint32_t w[kDigits][8];
+        // split of tile i straight into the A slices (lane m, K quarter qq),
+        // four amplitudes at a time; Eg_next = the group's exponent field.
+        // false if the fetch did not arrive in time.
+        auto split = [&](uint32_t i) -> bool {
+            const int b = (int)(i & 1u);
+            if (compute_any(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget128))) return false;
+            const uint32_t sbuf = smem_u32(buf(b));
+            uint4 v[8];
+            uint32_t mx = 0;
 #pragma unroll
             for (int j = 0; j < 8; j++) {
-                float dr[kDigits], di[kDigits];
-                dg_split_df(vh[2 * j], vl[2 * j], sd, dr);
-                dg_split_df(vh[2 * j + 1], vl[2 * j + 1], sd, di);
-#pragma unroll
-                for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
+                v[j] = lds_u4(sbuf + 16u * coff(j));
+                if (IN_IEEE) {  // (a double2 -> re.h, re.l, im.h, im.l)
+                    const df re = df_from_double(__hiloint2double((int)v[j].y, (int)v[j].x));
+                    const df im = df_from_double(__hiloint2double((int)v[j].w, (int)v[j].z));
+                    v[j] = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
+                                      __float_as_uint(im.l));
+                }
+                mx = max(mx, max(v[j].x & 0x7f800000u, v[j].z & 0x7f800000u));
             }
-            const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;
+            s_max[b][qq][m] = mx;
+            quarter_sync(1u + (uint32_t)lq);
+            Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
+            const float sd = dg_scale_down(Eg_next);
 #pragma unroll
-            for (int d = 0; d < kDigits; d++) tmem_st8(acol + 8u * d, w[d]);
-        }
-        tmem_st_wait();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-
-        // ---- the 21 slice products, 4 K steps each
-        if (tid == 0) {
+            for (int h = 0; h < 2; h++) {
+                uint32_t w[kDigits][4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint4 x = v[4 * h + j];
+                    float dr[kDigits], di[kDigits];
+                    dg_split_df(__uint_as_float(x.x), __uint_as_float(x.y), sd, dr);
+                    dg_split_df(__uint_as_float(x.z), __uint_as_float(x.w), sd, di);
+#pragma unroll
+                    for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
+                }
+#pragma unroll
+                for (int d = 0; d < kDigits; d++)
+                    tmem_st4(acol + 8u * d + 4u * h, w[d][0], w[d][1], w[d][2], w[d][3]);
+            }
+            return true;
+        };
+        auto issue_mma = [&]() {  // one thread: the 21 slice products, 4 K steps each
             const uint32_t idesc = idesc_bf16(128, kReals);
             const uint32_t bb = smem_u32(s_b);
 #pragma unroll
@@ -265,22 +284,52 @@ __global__ void __launch_bounds__(kThreads128, 1)
                                      idesc, first ? 0u : 1u);
                     }
             umma_commit(&bar_mma);
-        }
-        aborted = __syncthreads_or(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128)) != 0;
-        tc_fence_after();
-        if (aborted) {
-            if (tid == 0) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs still in flight
-            break;
-        }
+        };
 
-        // ---- epilogue: output reals 16 qq .. 16 qq + 15 of group m
-        {
+        // prologue: tile 0 into tensor memory, its MMAs started
+        if (!aborted && count > 0) {
+            aborted = !split(0);
+            if (!aborted) {
+                tmem_st_wait();
+                tc_fence_before();
+                compute_sync();
+                tc_fence_after();
+                if (tid == 0) issue_mma();
+                if (warp == 0 && count > 2) issue_load(2);  // tile 0 has left buffer 0
+            }
+        }
+        // steady state, MMAs of tile i in flight: once they are done, tile
+        // i + 1 is split into the A slices and tile i's accumulators are read
+        // out; then tile i + 1's MMAs start and tile i is combined and stored
+        // while they run
+        for (uint32_t i = 0; i < count && !aborted; i++) {
+            Eg = Eg_next;
+            const bool next = i + 1 < count;
+            if (compute_any(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128))) {
+                aborted = true;
+                if (tid == 0) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs in flight
+                break;
+            }
+            tc_fence_after();
+            if (next && !split(i + 1)) {
+                aborted = true;
+                break;
+            }
             uint32_t acc[kDigitLevels][16];
 #pragma unroll
             for (int lv = 0; lv < kDigitLevels; lv++)
                 tmem_ld16(tmem + lane_off + (uint32_t)(kReals * lv + 16 * qq), acc[lv]);
             tmem_ld_wait();
+            tmem_st_wait();
+            tc_fence_before();
+            compute_sync();
+            tc_fence_after();
+            if (tid == 0 && next) issue_mma();
+            if (warp == 0 && i + 3 < count) issue_load(i + 3);  // tile i + 1 has left its buffer
+            // combine tile i: output reals 16 qq .. 16 qq + 15 of group m,
+            // straight from registers to global memory
             const float su = dg_scale_up(Eg);
+            double2 *gt = a + tile_base(blockIdx.x + (uint64_t)i * stride);
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const df re = dg_combine_df(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
@@ -289,41 +338,20 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 const df im = dg_combine_df(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
                                             __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
                                             __uint_as_float(acc[4][2 * j + 1]), su);
-                uint4 o;
+                const uint64_t go = gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
                 if (OUT_IEEE) {
-                    const uint64_t rb = df_bits64(df_to_double(re)), ib = df_bits64(df_to_double(im));
-                    o = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (uint32_t)ib, (uint32_t)(ib >> 32));
+                    gt[go] = make_double2(df_to_double(re), df_to_double(im));
                 } else {
-                    o = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
-                                   __float_as_uint(im.l));
+                    *reinterpret_cast<float4 *>(gt + go) = make_float4(re.h, re.l, im.h, im.l);
                 }
-                sts_u4(sbuf + 16u * coff[j], o);
             }
         }
-        tc_fence_before();
-        fence_proxy_async_smem();
-        __syncthreads();
-
-        // ---- store, then fetch the tile two ahead into the same buffer
-        if (warp == 0) {
-            const uint64_t base = tile_base(tile);
-            const double2 *src = reinterpret_cast<const double2 *>(buf(b));
-            for (uint32_t j = lane; j < nruns; j += 32) bulk_s2g(a + (base | run_off(j)), src + ((size_t)j << L), run_bytes);
-            bulk_commit();
-            if (tile + 2 * stride < ntiles) {
-                bulk_wait_read_all();
-                __syncwarp();
-                issue_load(tile + 2 * stride, b);
-                if (b) issued1++; else issued0++;
-            }
-        }
+        if (aborted && tid == 0) atomicExch(err, kErrTimeout);
     }
-    if (aborted && tid == 0) atomicExch(err, kErrTimeout);
-    if (aborted && warp == 0) {  // let fetches in flight land before the CTA leaves
-        for (; done0 < issued0; done0++) mbar_wait_bounded(&bar_ld[0], done0 & 1u, kWaitBudget128);
-        for (; done1 < issued1; done1++) mbar_wait_bounded(&bar_ld[1], done1 & 1u, kWaitBudget128);
+    if (warp == 0) {  // every fetch has landed before the CTA leaves
+        if (issued0) mbar_wait_bounded(&bar_ld[0], (issued0 - 1u) & 1u, kWaitBudget128);
+        if (issued1) mbar_wait_bounded(&bar_ld[1], (issued1 - 1u) & 1u, kWaitBudget128);
     }
-    if (warp == 0) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
