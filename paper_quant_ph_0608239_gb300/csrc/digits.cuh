@@ -25,7 +25,8 @@
 // (L + 1) 64 2^16 integer units (level 0 at most 2^18, since |c_0| <= 128
 // and a unitary row has unit norm): below 2^24 for L <= 3, so the FP32
 // accumulators of levels 0..3 hold their sums exactly.  Levels 4 and 5 share
-// one accumulator; its rounding stays below 2^-50 of the result.  The dropped
+// one accumulator, folded into level 3's before the combination; their
+// rounding stays below 2^-50 of the result.  The dropped
 // levels 6..10 and the last remainder bound an output's error by about 2^-44
 // of the group's largest magnitude (typically 2^-48), the class of the
 // double-float tile passes.
@@ -33,8 +34,8 @@
 // The state is read and written in double-float form (hi + lo, two floats):
 // the split runs on FP32 additions (round to the grid by adding and
 // subtracting 1.5 * 2^23 * w_i, the remainder carried exactly as a pair), the
-// five accumulators are added in double-float (Knuth's two-sum) and scaled
-// back by 2^e.  The first block of a run converts IEEE doubles to this form
+// accumulators are added in double-float (Knuth's two-sum) and scaled back by
+// 2^e.  The first block of a run converts IEEE doubles to this form
 // and the last one converts back, with the integer conversions of df64.cuh.
 //
 // Everything compiles for the host as well, so the split, the exact level
@@ -104,9 +105,15 @@ DF_HD void dg_split_df(float h, float l, float scale, float (&d)[kDigits]) {
     d[5] = dg_step<5>(rh, rl);
 }
 
-// Sum of the five level accumulators (levels 0..3 exact, level 4-5 rounded)
-// as a normalised double-float, times scale = dg_scale_up(E).
-DF_HD df dg_combine_df(float a0, float a1, float a2, float a3, float a4, float scale) {
+// The accumulators of level 3 (exact) and levels 4-5 folded into one FP32
+// value: the rounding is below 2^-24 of level 3, which is itself below 2^-27
+// of the result.
+DF_HD float dg_fold_high(float a3, float a45) { return a3 + a45; }
+
+// Sum of the level accumulators (levels 0..2 exact, a3 = dg_fold_high of
+// levels 3 and 4-5) as a normalised double-float, times scale =
+// dg_scale_up(E).
+DF_HD df dg_combine_df(float a0, float a1, float a2, float a3, float scale) {
     // a0 is a multiple of 2^-14 with |a0| <= 16, a1 a multiple of 2^-23 with
     // |a1| < 0.6: either |a0| >= |a1| or the sum is exact, so the quick
     // two-sum is error free
@@ -115,7 +122,7 @@ DF_HD df dg_combine_df(float a0, float a1, float a2, float a3, float a4, float s
     t.l += s.l;
     s = quick_two_sum(t.h, t.l);
     t = two_sum(s.h, a3);
-    t.l += s.l + a4;
+    t.l += s.l;
     s = quick_two_sum(t.h, t.l);
     return df{s.h * scale, s.l * scale};
 }

@@ -222,22 +222,25 @@ __global__ void __launch_bounds__(kThreads128, 1)
         };
 
         bool aborted = compute_any(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128));
-        uint32_t Eg_next = 0, Eg = 0;
+        uint32_t Eg_next = 0;
         const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;  // this thread's A columns
 
-        // split of tile i straight into the A slices (lane m, K quarter qq),
-        // four amplitudes at a time; Eg_next = the group's exponent field.
-        // false if the fetch did not arrive in time.
-        auto split = [&](uint32_t i) -> bool {
+        // Split of a tile in two steps.  fetch(i): wait for its copy, read
+        // this thread's 8 amplitudes into registers (double-float form) and
+        // agree with the group's other threads on the exponent field Eg_next
+        // (false if the copy did not arrive in time).  digits(): the six
+        // slices of the held amplitudes straight into the A slices (lane m,
+        // K quarter qq), four amplitudes at a time.
+        uint4 v[8];
+        auto fetch = [&](uint32_t i) -> bool {
             const int b = (int)(i & 1u);
             if (compute_any(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget128))) return false;
             const uint32_t sbuf = smem_u32(buf(b));
-            uint4 v[8];
             uint32_t mx = 0;
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 v[j] = lds_u4(sbuf + 16u * coff(j));
-                if (IN_IEEE) {  // (a double2 -> re.h, re.l, im.h, im.l)
+                if (IN_IEEE) {  // a double2 -> (re.h, re.l, im.h, im.l)
                     const df re = df_from_double(__hiloint2double((int)v[j].y, (int)v[j].x));
                     const df im = df_from_double(__hiloint2double((int)v[j].w, (int)v[j].z));
                     v[j] = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
@@ -248,6 +251,9 @@ __global__ void __launch_bounds__(kThreads128, 1)
             s_max[b][qq][m] = mx;
             quarter_sync(1u + (uint32_t)lq);
             Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
+            return true;
+        };
+        auto digits = [&]() {
             const float sd = dg_scale_down(Eg_next);
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -265,7 +271,6 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 for (int d = 0; d < kDigits; d++)
                     tmem_st4(acol + 8u * d + 4u * h, w[d][0], w[d][1], w[d][2], w[d][3]);
             }
-            return true;
         };
         auto issue_mma = [&]() {  // one thread: the 21 slice products, 4 K steps each
             const uint32_t idesc = idesc_bf16(128, kReals);
@@ -286,24 +291,27 @@ __global__ void __launch_bounds__(kThreads128, 1)
             umma_commit(&bar_mma);
         };
 
-        // prologue: tile 0 into tensor memory, its MMAs started
+        // prologue: tile 0 into tensor memory, its MMAs started, tile 1 fetched
+        uint32_t Eg = 0;  // exponent fields of the tile whose MMAs run
         if (!aborted && count > 0) {
-            aborted = !split(0);
+            aborted = !fetch(0);
             if (!aborted) {
+                digits();
                 tmem_st_wait();
                 tc_fence_before();
                 compute_sync();
                 tc_fence_after();
                 if (tid == 0) issue_mma();
                 if (warp == 0 && count > 2) issue_load(2);  // tile 0 has left buffer 0
+                Eg = Eg_next;
+                if (count > 1) aborted = !fetch(1);
             }
         }
-        // steady state, MMAs of tile i in flight: once they are done, tile
-        // i + 1 is split into the A slices and tile i's accumulators are read
-        // out; then tile i + 1's MMAs start and tile i is combined and stored
-        // while they run
+        // steady state, the MMAs of tile i in flight and tile i + 1 fetched:
+        // once the MMAs are done, tile i + 1's digits go into the A slices and
+        // tile i's accumulators are read out; tile i + 1's MMAs start; tile i
+        // is combined and stored and tile i + 2 fetched while they run
         for (uint32_t i = 0; i < count && !aborted; i++) {
-            Eg = Eg_next;
             const bool next = i + 1 < count;
             if (compute_any(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128))) {
                 aborted = true;
@@ -311,13 +319,25 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 break;
             }
             tc_fence_after();
-            if (next && !split(i + 1)) {
-                aborted = true;
-                break;
+            const uint32_t Eg_i = Eg;  // tile i's exponent field
+            if (next) {
+                digits();
+                Eg = Eg_next;
             }
-            uint32_t acc[kDigitLevels][16];
+            // the accumulators of levels 3 and 4-5 first, folded into one
+            // (rounding below 2^-50 of the result), then levels 0, 1, 2
+            uint32_t acc[kDigitLevels - 1][16];
+            {
+                uint32_t a4[16];
+                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * 3 + 16 * qq), acc[3]);
+                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * 4 + 16 * qq), a4);
+                tmem_ld_wait();
 #pragma unroll
-            for (int lv = 0; lv < kDigitLevels; lv++)
+                for (int c = 0; c < 16; c++)
+                    acc[3][c] = __float_as_uint(dg_fold_high(__uint_as_float(acc[3][c]), __uint_as_float(a4[c])));
+            }
+#pragma unroll
+            for (int lv = 0; lv < 3; lv++)
                 tmem_ld16(tmem + lane_off + (uint32_t)(kReals * lv + 16 * qq), acc[lv]);
             tmem_ld_wait();
             tmem_st_wait();
@@ -328,16 +348,15 @@ __global__ void __launch_bounds__(kThreads128, 1)
             if (warp == 0 && i + 3 < count) issue_load(i + 3);  // tile i + 1 has left its buffer
             // combine tile i: output reals 16 qq .. 16 qq + 15 of group m,
             // straight from registers to global memory
-            const float su = dg_scale_up(Eg);
+            const float su = dg_scale_up(Eg_i);
             double2 *gt = a + tile_base(blockIdx.x + (uint64_t)i * stride);
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const df re = dg_combine_df(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
-                                            __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]),
-                                            __uint_as_float(acc[4][2 * j]), su);
+                                            __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]), su);
                 const df im = dg_combine_df(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
                                             __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
-                                            __uint_as_float(acc[4][2 * j + 1]), su);
+                                            su);
                 const uint64_t go = gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
                 if (OUT_IEEE) {
                     gt[go] = make_double2(df_to_double(re), df_to_double(im));
@@ -345,6 +364,7 @@ __global__ void __launch_bounds__(kThreads128, 1)
                     *reinterpret_cast<float4 *>(gt + go) = make_float4(re.h, re.l, im.h, im.l);
                 }
             }
+            if (i + 2 < count && !fetch(i + 2)) aborted = true;
         }
         if (aborted && tid == 0) atomicExch(err, kErrTimeout);
     }

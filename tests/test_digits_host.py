@@ -159,7 +159,7 @@ int main() {
                 // in integer units of the level, 2^(-14 - 9L)
                 if (mag[L] * std::ldexp((LD)1, 14 + 9 * L) >= std::ldexp((LD)1, 24)) bad_bound++;
             }
-            const df got = dg_combine_df(acc[0], acc[1], acc[2], acc[3], acc[4], su);
+            const df got = dg_combine_df(acc[0], acc[1], acc[2], dg_fold_high(acc[3], acc[4]), su);
             LD ref = 0, scale = 0, xmax = 0;
             for (int k = 0; k < 64; k++) {
                 ref += (LD)x[k] * (LD)B[n * 64 + k];
