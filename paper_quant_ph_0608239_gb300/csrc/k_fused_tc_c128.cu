@@ -28,7 +28,8 @@
 //   2. split: each thread reads its 8 amplitudes, the four threads of a group
 //      agree on its largest exponent, and the thread writes its digits into
 //      the A slices in tensor memory (its lane, 8 columns per slice);
-//   3. one thread issues the 84 MMAs (21 products x 4 K steps of 16);
+//   3. one thread issues the MMAs (21 products x 4 K steps of 16, in 48
+//      instructions: slices of B side by side along N);
 //   4. epilogue: each thread reads the five accumulators of its 16 output
 //      reals, combines them into doubles and writes them into the same
 //      buffer at the groups' positions (its input there was consumed in 2);
@@ -272,22 +273,32 @@ __global__ void __launch_bounds__(kThreads128, 1)
                     tmem_st4(acol + 8u * d + 4u * h, w[d][0], w[d][1], w[d][2], w[d][3]);
             }
         };
-        auto issue_mma = [&]() {  // one thread: the 21 slice products, 4 K steps each
-            const uint32_t idesc = idesc_bf16(128, kReals);
-            const uint32_t bb = smem_u32(s_b);
+        // One thread issues the 21 slice products, 4 K steps each.  The B
+        // slices lie one after another along N (64 rows each, same layout),
+        // and the accumulators of levels 0..4 one after another along the
+        // columns, so slice i of A times B_0 .. B_(4-i) is a single MMA of
+        // N = 64 (5 - i) into accumulators i .. 4 (two for i = 0: N <= 256);
+        // the level-5 products (i + j = 5) go into accumulator 4 one by one:
+        // 12 MMAs per K step.
+        const uint64_t bdesc0 = umma_desc(smem_u32(s_b), 128, 1024);
+        auto issue_mma = [&]() {
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++)
+            for (int ks = 0; ks < 4; ks++) {
+                const uint32_t at = tmem + kAccCols + 48u * ks;    // A slice 0, K step ks
+                const uint64_t bd = bdesc0 + (uint64_t)(ks * 256 / 16);  // B slice 0, K step ks
+                const uint32_t acc0 = ks > 0 ? 1u : 0u;
+                // i = 0: levels 0..3 (N = 256) and level 4 (N = 64), both start their accumulators
+                umma_bf16_ts(tmem, at, bd, idesc_bf16(128, 256), acc0);
+                umma_bf16_ts(tmem + 4u * kReals, at, bd + 4u * kSliceBytes / 16, idesc_bf16(128, kReals), acc0);
 #pragma unroll
-                for (int si = 0; si < kDigits; si++)
+                for (int si = 1; si < kDigitLevels; si++)  // levels si .. 4 of slice si
+                    umma_bf16_ts(tmem + (uint32_t)(si * kReals), at + 8u * si, bd,
+                                 idesc_bf16(128, kReals * (kDigitLevels - si)), 1u);
 #pragma unroll
-                    for (int sj = 0; si + sj < kDigits; sj++) {
-                        const int lv = dg_level_acc(si, sj);
-                        // the first product of a level at K step 0 starts its accumulator
-                        const bool first = ks == 0 && (lv < kDigitLevels - 1 ? si == 0 : si == 0 && sj == lv);
-                        umma_bf16_ts(tmem + (uint32_t)(kReals * lv), tmem + kAccCols + 48u * ks + 8u * si,
-                                     umma_desc(bb + (uint32_t)sj * kSliceBytes + (uint32_t)ks * 256u, 128, 1024),
-                                     idesc, first ? 0u : 1u);
-                    }
+                for (int si = 0; si < kDigits; si++)  // level 5 into accumulator 4
+                    umma_bf16_ts(tmem + 4u * kReals, at + 8u * si, bd + (uint64_t)((kDigits - 1 - si) * kSliceBytes / 16),
+                                 idesc_bf16(128, kReals), 1u);
+            }
             umma_commit(&bar_mma);
         };
 
@@ -301,7 +312,7 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 tc_fence_before();
                 compute_sync();
                 tc_fence_after();
-                if (tid == 0) issue_mma();
+                if (tid == 32) issue_mma();
                 if (warp == 0 && count > 2) issue_load(2);  // tile 0 has left buffer 0
                 Eg = Eg_next;
                 if (count > 1) aborted = !fetch(1);
@@ -315,7 +326,7 @@ __global__ void __launch_bounds__(kThreads128, 1)
             const bool next = i + 1 < count;
             if (compute_any(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128))) {
                 aborted = true;
-                if (tid == 0) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs in flight
+                if (tid == 32) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs in flight
                 break;
             }
             tc_fence_after();
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(kThreads128, 1)
             tc_fence_before();
             compute_sync();
             tc_fence_after();
-            if (tid == 0 && next) issue_mma();
+            if (tid == 32 && next) issue_mma();
             if (warp == 0 && i + 3 < count) issue_load(i + 3);  // tile i + 1 has left its buffer
             // combine tile i: output reals 16 qq .. 16 qq + 15 of group m,
             // straight from registers to global memory
