@@ -94,15 +94,32 @@ def workload_gates(w):
     raise ValueError(w["kind"])
 
 
-def dtype_label(dt, pst=None):
+def dtype_label(dt, kernel=None):
     """Arithmetic type of the path: complex64 computes in FP32; complex128
     keeps IEEE doubles in memory and computes in double-float (two FP32
-    values, ~48 significand bits) in the tile passes and per-gate sweeps."""
+    values, ~48 significand bits) in the tile passes and per-gate sweeps, and
+    as exact bf16 digit-slice products on the tensor cores (double-float
+    accumulation) in the fused 5-qubit blocks."""
     if dt == "c64":
         return "f32"
-    if pst and pst.get("fuse_k"):
-        return "f64"  # dense blocks on the CUDA cores compute in FP64
+    if kernel == "dense_cuda_core":
+        return "f64"
+    if kernel == "fused_tc_digits":
+        return "df64 (IEEE f64 storage; exact bf16 digit-slice products on the tensor cores, double-float sums)"
     return "df64 (IEEE f64 storage, double-float arithmetic)"
+
+
+def path_label(dt, pst, pergate=False):
+    if pergate:
+        return "one sweep per gate"
+    k = pst["fuse_k"]
+    if not k:
+        return "planner (tile passes)"
+    if dt == "c64" and k in (4, 5):
+        return "planner (fused %d-qubit blocks on the tensor cores, 3xTF32)" % k
+    if dt == "c128" and k == 5:
+        return "planner (fused 5-qubit blocks on the tensor cores, bf16 digit slices)"
+    return "planner (fused %d-qubit blocks on the CUDA cores)" % k
 
 
 def peaks():
@@ -382,6 +399,18 @@ def run_ours(args, w, ws, rank, local):
                                     else "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz"),
                     "alg_flops_per_launch": fl / nl, "launches": nl, "avg_launch_ms": ms / nl}
     frac_alu = alu_roof["frac"] or 0.0
+    if fam == "fused_tc_digits":
+        # 21 bf16 slice products per algorithmic product (digits.cuh); the
+        # tensor pipe executes 21x the algorithmic flops in bf16
+        bp = tf32_peak()[0] / TF32_OVER_BF16
+        ach = 21.0 * tflops
+        alu_roof = {"bound": "tensor", "kernel": fam, "achieved": ach, "peak": bp, "unit": "TFLOP/s (bf16)",
+                    "frac": ach / bp, "traffic": traffic,
+                    "peak_source": "bf16 dense: measured burst GEMM (MEASURED_PEAKS.json); 21 bf16 slice products "
+                                   "per algorithmic product",
+                    "alg_flops_per_launch": fl / nl, "alg_tflops": tflops, "launches": nl,
+                    "avg_launch_ms": ms / nl}
+        frac_alu = ach / bp
     if fam == "fused_tensor_core":
         # 3xTF32: three TF32 products per algorithmic product; the achieved
         # figure counts algorithmic flops once
@@ -401,14 +430,10 @@ def run_ours(args, w, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": dtype_label(w["dtype"], pst),
+        "dtype": dtype_label(w["dtype"], fam),
         "data": "synthetic: seeded generator (inputs/circuits.py), no dataset",
         "config": {"workload": w["text"], "name": args.workload, "n": n, "gates": ng, "dtype": w["dtype"],
-                   "path": ("one sweep per gate" if args.pergate else
-                            "planner (fused %d-qubit blocks on the %s)" % (
-                                pst["fuse_k"], "tensor cores" if w["dtype"] == "c64" and pst["fuse_k"] in (4, 5)
-                                else "CUDA cores") if pst["fuse_k"]
-                            else "planner (tile passes)"), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
+                   "path": path_label(w["dtype"], pst, args.pergate), "tile_passes": pst["passes"], "tile_bits": pst["tile_bits"],
                    "autotune": [dict(c, chosen=(i == pst["chosen"])) for i, c in enumerate(pst["autotune"])],
                    "state_bytes": st.nbytes, "l2": "inputs larger than L2 (state %d MiB >> 129 MB)" % (st.nbytes >> 20),
                    "parallelism": "replicas x%d" % ws},
@@ -428,7 +453,9 @@ def run_ours(args, w, ws, rank, local):
     torch.cuda.empty_cache()
 
     if rank == 0 and ws == 1 and not args.no_companions and w["kind"] == "random":
-        out["companions"] = companions(q, w, gates, x0, args)
+        main = {"gates_per_s": value, "ms_per_run": max_el / args.steps * 1e3, "runs": args.steps,
+                "path": out["config"]["path"]}
+        out["configs"] = config_lines(q, main, args)
         out["single_gate_sweeps"] = single_gate_sweeps(q)
         out["qubit_interchange_sweeps"] = qubit_interchange_sweeps(q)
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -525,70 +552,104 @@ def qubit_interchange_sweeps(q, n=30, Ks=(1, 2, 4)):
     return out
 
 
-def companions(q, w, gates, x0, args):
-    """Same circuit through the FP32 planner path and a per-gate FP64 sample."""
+def _event_runs(fn, reps):
+    """Per-run milliseconds of fn() over reps runs, CUDA events on the current
+    stream around each run (after the caller's warm-up)."""
     import torch
-    res = {}
-    n, ng = w["n"], len(gates)
-    for dt in (["c64"] if w["dtype"] == "c128" else ["c128"]):
-        st = q.State(n, dt)
-        plan = st.plan(gates)
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for r in range(reps):
+        fn()
+        evs[r + 1].record(stream)
+    torch.cuda.synchronize()
+    return [evs[r].elapsed_time(evs[r + 1]) for r in range(reps)]
+
+
+def _timed_circuit(q, n, dt, gates, x0, reps, **plan_kw):
+    """A planned circuit timed as a bench step (set the basis state, run the
+    plan, read <Q_q>): tuning runs and one warm-up untimed, then reps runs,
+    each bracketed by CUDA events; median ms, gates/s and the plan's path."""
+    import torch
+    st = q.State(n, dt)
+    plan = st.plan(gates, **plan_kw)
+
+    def step():
         st.set_basis(x0)
         plan.run()
         st.qubit_probs()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(max(1, args.steps)):
-            st.set_basis(x0)
-            plan.run()
-            st.qubit_probs()
-        torch.cuda.synchronize()
-        el = (time.perf_counter() - t0) / max(1, args.steps)
-        res["fused_" + ("fp32_c64" if dt == "c64" else "fp64_c128")] = {
-            "gates_per_s": ng / el, "ms_per_step": el * 1e3, "passes": plan.stats()["passes"]}
-        plan.free()
-        st.free()
-        torch.cuda.empty_cache()
-    # the same circuit fused into 5-qubit blocks on the tensor cores (complex64)
-    st = q.State(n, "c64")
-    plan = st.plan(gates, fuse_k=5)
-    st.set_basis(x0)
-    plan.run()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st.set_basis(x0)
-    plan.run()
-    st.qubit_probs()
-    el = time.perf_counter() - t0
-    res["fused_tensor_core_k5_c64"] = {"gates_per_s": ng / el, "ms_per_step": el * 1e3,
-                                       "blocks": plan.stats()["passes"]}
+
+    for _ in range(plan.stats()["candidates"] + 1):
+        step()
+    ms = statistics.median(_event_runs(step, reps))
+    pst = plan.stats()
+    out = {"gates_per_s": len(gates) / (ms / 1e3), "ms_per_run": ms, "runs": reps,
+           "path": path_label(dt, pst, plan_kw.get("mode") == q.MODE_PERGATE),
+           "passes": pst["passes"] if pst["mode"] != q.MODE_PERGATE else pst["sweeps"]}
     plan.free()
     st.free()
+    del st
     torch.cuda.empty_cache()
-    # per-gate FP64 path, timed on the first two layers of the circuit
-    sub = gates[: 2 * (n + n // 2)] if w["kind"] == "random" else gates[:64]
-    st = q.State(n, "c128")
-    st.run(sub, mode=q.MODE_PERGATE)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st.run(sub, mode=q.MODE_PERGATE)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    res["pergate_fp64_c128_sample"] = {"gates_per_s": len(sub) / el, "sample": "first %d gates" % len(sub)}
-    # the same gates fused into dense 5-qubit blocks applied in FP64 on the
-    # CUDA cores (GB300's FP64 rate is ~1/58 of FP32: slow by design), first layer
-    sub1 = gates[: n + n // 2] if w["kind"] == "random" else gates[:32]
-    plan = st.plan(sub1, fuse_k=5)
-    plan.run()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plan.run()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    res["fused_fp64_k5_c128_sample"] = {"gates_per_s": len(sub1) / el, "blocks": plan.stats()["passes"],
-                                        "sample": "first %d gates" % len(sub1)}
-    plan.free()
+    return out
+
+
+def config_lines(q, main, args):
+    """The other configurations of the benchmark and the arms of the fused
+    complex64 vs per-gate complex128 comparison, each event-timed over
+    repeated runs (median): the 10-qubit QFT, the 30-qubit random circuit on
+    every path, the adder of two 15-qubit registers (with its output index
+    checked), the 34-qubit circuit (complex64, 128 GiB) and the batch of 512
+    circuits."""
+    res = {}
+    reps = max(3, min(args.steps, 5))
+    # 10-qubit QFT, complex128
+    x, g = inputs.qft_circuit(10, seed=1)
+    res["qft10_c128"] = {"pergate": _timed_circuit(q, 10, "c128", g, x, 20, mode=q.MODE_PERGATE),
+                         "planner": _timed_circuit(q, 10, "c128", g, x, 20, mode=q.MODE_AUTO)}
+    # 30-qubit random circuit, depth 40: every path
+    g = inputs.random_circuit(30, 40, 2)
+    x = inputs.random_basis(30, 2)
+    c2 = {"c128_autotuned": main,
+          "c64_tile_passes": _timed_circuit(q, 30, "c64", g, x, reps, tile_bits=12),
+          "c64_tensor_cores_k5": _timed_circuit(q, 30, "c64", g, x, reps, fuse_k=5),
+          "c128_tensor_cores_k5": _timed_circuit(q, 30, "c128", g, x, reps, fuse_k=5),
+          "c128_tile_passes": _timed_circuit(q, 30, "c128", g, x, 2, tile_bits=12),
+          "c128_pergate": _timed_circuit(q, 30, "c128", g, x, 2, mode=q.MODE_PERGATE)}
+    c2["fused_c64_over_pergate_c128"] = c2["c128_pergate"]["ms_per_run"] / c2["c64_tensor_cores_k5"]["ms_per_run"]
+    res["random30"] = c2
+    # adder of two 15-qubit registers (complex64): first seeded pair, output index checked
+    a, b = inputs.adder_pairs(15, 8, seed=3)[0]
+    g = inputs.adder_circuit([a, b], 15)
+    ad = {"tile_passes": _timed_circuit(q, 30, "c64", g, 0, reps),
+          "tensor_cores_k5": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=5)}
+    st = q.State(30, "c64")
+    st.run(g, fuse_k=5)
+    qp = st.qubit_probs()
     st.free()
+    ad["output_index_exact"] = sum(1 << i for i in range(30) if qp[i] > 0.5) == inputs.adder_expected_index([a, b], 15)
+    res["adder2x15_c64"] = ad
+    # 34 qubits, depth 20, complex64 (128 GiB): 5-qubit tensor-core blocks
+    # (the autotuner's pick there; its other candidates take 2-4x longer)
+    g = inputs.random_circuit(34, 20, 4)
+    res["random34_c64"] = {"tensor_cores_k5": _timed_circuit(q, 34, "c64", g, inputs.random_basis(34, 4), 3,
+                                                             fuse_k=5)}
+    # batch of 512 circuits: one graph replay per run
+    import torch
+    circs = inputs.batch_circuits()
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=3000 + i) for i, (n, _) in enumerate(circs)]
+    bt = q.Batch(states, x0s, [gg for _, gg in circs])
+    bt.run()
+    bt.sync()
+    ms = statistics.median(_event_runs(bt.run, reps))
+    bst = bt.stats()
+    res["batch512_c64"] = {"gates_per_s": bst["gates"] / (ms / 1e3), "ms_per_run": ms, "runs": reps,
+                           "cuda_graph": bst["graph"], "eff_hbm_frac": bst["alg_bytes"] / (ms / 1e3) / 1e9 / peaks()[0]}
+    bt.free()
+    for st in states:
+        st.free()
+    del states
     torch.cuda.empty_cache()
     return res
 
