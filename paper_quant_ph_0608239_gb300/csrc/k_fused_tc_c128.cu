@@ -50,7 +50,8 @@ namespace qsim {
 
 namespace {
 
-constexpr int kThreads128 = 512;
+constexpr int kThreads128 = 512;            // compute threads: 16 warps
+constexpr int kThreadsAll128 = 640;         // + 4 duty warps (MMA issue, fetch issue, 2 idle), one per scheduler
 constexpr int kK = 5;                          // qubits of a block
 constexpr int kAmps = 1 << kK;                 // 32 amplitudes of a group
 constexpr int kReals = 2 * kAmps;              // 64: K and N of the product
@@ -98,6 +99,17 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t r0, uint32_t r
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t r0, uint32_t r1) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0), "r"(r1) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -132,13 +144,16 @@ __device__ __forceinline__ bool compute_any(bool v) {
 }
 
 template <bool IN_IEEE, bool OUT_IEEE>
-__global__ void __launch_bounds__(kThreads128, 1)
+__global__ void __launch_bounds__(kThreadsAll128, 1)
     k_fused_tc_c128(double2 *__restrict__ a, TileGeom g, FusedMap fm, const uint16_t *__restrict__ bmat,
                     uint32_t *err, uint64_t ntiles) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *s_b = smem_raw;                    // six B slices
     unsigned char *s_buf0 = smem_raw + kBBytes;       // two input buffers
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma, bar_b;
+    // bar_ld: tile arrived in buffer b; bar_free: the compute warps left
+    // buffer b; bar_ready: tile's A slices written and the last tile's
+    // accumulators read (MMAs may start); bar_mma: MMAs done; bar_b: B loaded
+    __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mma, bar_b;
     __shared__ uint32_t tmem_base_s;
     __shared__ uint32_t s_max[2][4][128];  // per tile parity, K quarter, group: largest hi exponent field
     __shared__ int s_hb[kMaxH128];
@@ -150,8 +165,11 @@ __global__ void __launch_bounds__(kThreads128, 1)
     if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < kMaxH128; k++) s_hb[k] = k < H ? g.hb[k] : 0;
-        mbar_init(&bar_ld[0], 1);
-        mbar_init(&bar_ld[1], 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar_ld[b], 1);
+            mbar_init(&bar_free[b], kThreads128 / 32);
+        }
+        mbar_init(&bar_ready, kThreads128 / 32);
         mbar_init(&bar_mma, 1);
         mbar_init(&bar_b, 1);
         fence_mbar_init();
@@ -180,99 +198,8 @@ __global__ void __launch_bounds__(kThreads128, 1)
     // this CTA's tiles: blockIdx.x + i * stride, i < count
     const uint32_t count = blockIdx.x < ntiles ? (uint32_t)((ntiles - 1 - blockIdx.x) / stride + 1) : 0u;
 
-    // fetch of tile i into buffer i & 1 (warp 0); the counts let an aborting
-    // CTA wait for the copies in flight before it leaves
-    uint32_t issued0 = 0u, issued1 = 0u;
-    auto issue_load = [&](uint32_t i) {
-        const int b = (int)(i & 1u);
-        const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * stride);
-        if (lane == 0) mbar_arrive_expect_tx(&bar_ld[b], kTileBytes);
-        __syncwarp();
-        double2 *dst = reinterpret_cast<double2 *>(buf(b));
-        for (uint32_t j = lane; j < nruns; j += 32)
-            bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[b]);
-        if (b) issued1++; else issued0++;
-    };
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar_b, kBBytes);
-        bulk_g2s(s_b, bmat, kBBytes, &bar_b);
-    }
-    if (warp == 0) {
-        if (count > 0) issue_load(0);
-        if (count > 1) issue_load(1);
-    }
-    {
-        // ---- group m (tensor-memory lane), K quarter qq
-        const int lq = warp & 3, qq = warp >> 2;
-        const uint32_t m = (uint32_t)(32 * lq + lane);
-        const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
-        uint32_t ibase = 0;
-#pragma unroll
-        for (int b = 0; b < kTileBits - kK; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
-        uint32_t wc[kK];
-#pragma unroll
-        for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
-        // this thread's amplitudes: columns 8 qq + j, j < 8; their tile
-        // indices (shared memory) and offsets from the tile's base (global)
-        const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
-        const uint32_t lowmask = (1u << L) - 1u;
-        auto goff = [&](uint32_t t) { return (uint64_t)(t & lowmask) | run_off(t >> L); };
-        const uint64_t gq = goff(qbase), gc0 = goff(wc[0]), gc1 = goff(wc[1]), gc2 = goff(wc[2]);
-        auto coff = [&](int j) {
-            return qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
-        };
-
-        bool aborted = compute_any(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128));
-        uint32_t Eg_next = 0;
-        const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;  // this thread's A columns
-
-        // Split of a tile in two steps.  fetch(i): wait for its copy, read
-        // this thread's 8 amplitudes into registers (double-float form) and
-        // agree with the group's other threads on the exponent field Eg_next
-        // (false if the copy did not arrive in time).  digits(): the six
-        // slices of the held amplitudes straight into the A slices (lane m,
-        // K quarter qq), four amplitudes at a time.
-        uint4 v[8];
-        auto fetch = [&](uint32_t i) -> bool {
-            const int b = (int)(i & 1u);
-            if (compute_any(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget128))) return false;
-            const uint32_t sbuf = smem_u32(buf(b));
-            uint32_t mx = 0;
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                v[j] = lds_u4(sbuf + 16u * coff(j));
-                if (IN_IEEE) {  // a double2 -> (re.h, re.l, im.h, im.l)
-                    const df re = df_from_double(__hiloint2double((int)v[j].y, (int)v[j].x));
-                    const df im = df_from_double(__hiloint2double((int)v[j].w, (int)v[j].z));
-                    v[j] = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
-                                      __float_as_uint(im.l));
-                }
-                mx = max(mx, max(v[j].x & 0x7f800000u, v[j].z & 0x7f800000u));
-            }
-            s_max[b][qq][m] = mx;
-            quarter_sync(1u + (uint32_t)lq);
-            Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
-            return true;
-        };
-        auto digits = [&]() {
-            const float sd = dg_scale_down(Eg_next);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                uint32_t w[kDigits][4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const uint4 x = v[4 * h + j];
-                    float dr[kDigits], di[kDigits];
-                    dg_split_df(__uint_as_float(x.x), __uint_as_float(x.y), sd, dr);
-                    dg_split_df(__uint_as_float(x.z), __uint_as_float(x.w), sd, di);
-#pragma unroll
-                    for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
-                }
-#pragma unroll
-                for (int d = 0; d < kDigits; d++)
-                    tmem_st4(acol + 8u * d + 4u * h, w[d][0], w[d][1], w[d][2], w[d][3]);
-            }
-        };
+    if (warp == kThreads128 / 32 && lane == 0) {
+        // ---- MMA warp: tile t's products once its A slices are in place
         // One thread issues the 21 slice products, 4 K steps each.  The B
         // slices lie one after another along N (64 rows each, same layout),
         // and the accumulators of levels 0..4 one after another along the
@@ -302,18 +229,134 @@ __global__ void __launch_bounds__(kThreads128, 1)
             umma_commit(&bar_mma);
         };
 
-        // prologue: tile 0 into tensor memory, its MMAs started, tile 1 fetched
+        uint32_t issued = 0;
+        bool ok = mbar_wait_bounded(&bar_b, 0, kWaitBudget128);
+        for (uint32_t t = 0; t < count && ok; t++) {
+            ok = mbar_wait_bounded(&bar_ready, t & 1u, kWaitBudget128);
+            if (!ok) break;
+            tc_fence_after();
+            issue_mma();
+            issued++;
+        }
+        // the last products have finished before the CTA may free tensor memory
+        if (issued) mbar_wait_bounded(&bar_mma, (issued - 1u) & 1u, kWaitBudget128);
+        if (!ok) atomicExch(err, kErrTimeout);
+    } else if (warp == kThreads128 / 32 + 1) {
+        // ---- fetch warp: tile k into buffer k & 1 once tile k - 2 left it
+        uint32_t issued0 = 0u, issued1 = 0u;
+        auto issue_load = [&](uint32_t i) {
+            const int b = (int)(i & 1u);
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * stride);
+            if (lane == 0) mbar_arrive_expect_tx(&bar_ld[b], kTileBytes);
+            __syncwarp();
+            double2 *dst = reinterpret_cast<double2 *>(buf(b));
+            for (uint32_t j = lane; j < nruns; j += 32)
+                bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[b]);
+            if (b) issued1++; else issued0++;
+        };
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bar_b, kBBytes);
+            bulk_g2s(s_b, bmat, kBBytes, &bar_b);
+        }
+        bool ok = true;
+        for (uint32_t k = 0; k < count && ok; k++) {
+            if (k >= 2) ok = mbar_wait_bounded(&bar_free[k & 1u], ((k - 2) >> 1) & 1u, kWaitBudget128);
+            if (ok) issue_load(k);
+        }
+        // every fetch has landed before the CTA may leave
+        if (issued0) mbar_wait_bounded(&bar_ld[0], (issued0 - 1u) & 1u, kWaitBudget128);
+        if (issued1) mbar_wait_bounded(&bar_ld[1], (issued1 - 1u) & 1u, kWaitBudget128);
+    } else if (warp < kThreads128 / 32) {
+        // ---- compute warps: group m (tensor-memory lane), K quarter qq
+        const int lq = warp & 3, qq = warp >> 2;
+        const uint32_t m = (uint32_t)(32 * lq + lane);
+        const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
+        uint32_t ibase = 0;
+#pragma unroll
+        for (int b = 0; b < kTileBits - kK; b++) ibase |= ((m >> b) & 1u) << fm.row[b];
+        uint32_t wc[kK];
+#pragma unroll
+        for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
+        // this thread's amplitudes: columns 8 qq + j, j < 8; their tile
+        // indices (shared memory) and offsets from the tile's base (global)
+        const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
+        const uint32_t lowmask = (1u << L) - 1u;
+        auto goff = [&](uint32_t t) { return (uint64_t)(t & lowmask) | run_off(t >> L); };
+        const uint64_t gq = goff(qbase), gc0 = goff(wc[0]), gc1 = goff(wc[1]), gc2 = goff(wc[2]);
+        auto coff = [&](int j) {
+            return qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
+        };
+
+        bool aborted = compute_any(!mbar_wait_bounded(&bar_b, 0, kWaitBudget128));
+        uint32_t Eg_next = 0;
+        const uint32_t acol = tmem + lane_off + kAccCols + 48u * (uint32_t)qq;  // this thread's A columns
+
+        // Split of a tile in two steps.  fetch(i): wait for its copy, read
+        // this thread's 8 amplitudes into registers (double-float form) and
+        // agree with the group's other threads on the exponent field Eg_next
+        // (false if the copy did not arrive in time).  digits(): the six
+        // slices of the held amplitudes straight into the A slices (lane m,
+        // K quarter qq), two amplitudes at a time.
+        uint4 v[8];
+        auto fetch = [&](uint32_t i) -> bool {
+            const int b = (int)(i & 1u);
+            if (compute_any(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget128))) return false;
+            const uint32_t sbuf = smem_u32(buf(b));
+            uint32_t mx = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                v[j] = lds_u4(sbuf + 16u * coff(j));
+                if (IN_IEEE) {  // a double2 -> (re.h, re.l, im.h, im.l)
+                    const df re = df_from_double(__hiloint2double((int)v[j].y, (int)v[j].x));
+                    const df im = df_from_double(__hiloint2double((int)v[j].w, (int)v[j].z));
+                    v[j] = make_uint4(__float_as_uint(re.h), __float_as_uint(re.l), __float_as_uint(im.h),
+                                      __float_as_uint(im.l));
+                }
+                mx = max(mx, max(v[j].x & 0x7f800000u, v[j].z & 0x7f800000u));
+            }
+            s_max[b][qq][m] = mx;
+            quarter_sync(1u + (uint32_t)lq);
+            Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
+            return true;
+        };
+        auto digits = [&]() {
+            const float sd = dg_scale_down(Eg_next);
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                uint32_t w[kDigits][2];
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const uint4 x = v[2 * h + j];
+                    float dr[kDigits], di[kDigits];
+                    dg_split_df(__uint_as_float(x.x), __uint_as_float(x.y), sd, dr);
+                    dg_split_df(__uint_as_float(x.z), __uint_as_float(x.w), sd, di);
+#pragma unroll
+                    for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
+                }
+#pragma unroll
+                for (int d = 0; d < kDigits; d++) tmem_st2(acol + 8u * d + 2u * h, w[d][0], w[d][1]);
+            }
+        };
+        // tile t's A slices are written (and tile t - 1's accumulators read):
+        // one arrival per warp on bar_ready, and on bar_free of the buffer
+        // tile t came from (its amplitudes were read in fetch(t))
+        auto arrive_ready = [&](uint32_t t) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bar_free[t & 1u]);
+                mbar_arrive(&bar_ready);
+            }
+        };
+
+        // prologue: tile 0 into tensor memory (its MMAs start), tile 1 fetched
         uint32_t Eg = 0;  // exponent fields of the tile whose MMAs run
         if (!aborted && count > 0) {
             aborted = !fetch(0);
             if (!aborted) {
                 digits();
                 tmem_st_wait();
-                tc_fence_before();
-                compute_sync();
-                tc_fence_after();
-                if (tid == 32) issue_mma();
-                if (warp == 0 && count > 2) issue_load(2);  // tile 0 has left buffer 0
+                arrive_ready(0);
                 Eg = Eg_next;
                 if (count > 1) aborted = !fetch(1);
             }
@@ -326,7 +369,6 @@ __global__ void __launch_bounds__(kThreads128, 1)
             const bool next = i + 1 < count;
             if (compute_any(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128))) {
                 aborted = true;
-                if (tid == 32) mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128);  // MMAs in flight
                 break;
             }
             tc_fence_after();
@@ -335,53 +377,58 @@ __global__ void __launch_bounds__(kThreads128, 1)
                 digits();
                 Eg = Eg_next;
             }
-            // the accumulators of levels 3 and 4-5 first, folded into one
-            // (rounding below 2^-50 of the result), then levels 0, 1, 2
-            uint32_t acc[kDigitLevels - 1][16];
-            {
-                uint32_t a4[16];
-                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * 3 + 16 * qq), acc[3]);
-                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * 4 + 16 * qq), a4);
-                tmem_ld_wait();
-#pragma unroll
-                for (int c = 0; c < 16; c++)
-                    acc[3][c] = __float_as_uint(dg_fold_high(__uint_as_float(acc[3][c]), __uint_as_float(a4[c])));
-            }
-#pragma unroll
-            for (int lv = 0; lv < 3; lv++)
-                tmem_ld16(tmem + lane_off + (uint32_t)(kReals * lv + 16 * qq), acc[lv]);
-            tmem_ld_wait();
-            tmem_st_wait();
-            tc_fence_before();
-            compute_sync();
-            tc_fence_after();
-            if (tid == 32 && next) issue_mma();
-            if (warp == 0 && i + 3 < count) issue_load(i + 3);  // tile i + 1 has left its buffer
-            // combine tile i: output reals 16 qq .. 16 qq + 15 of group m,
-            // straight from registers to global memory
+            // Tile i's accumulators in two halves of 8 output reals (4
+            // amplitudes): levels 3 and 4-5 folded into one on arrival
+            // (rounding below 2^-50 of the result), then levels 0, 1, 2.
+            // Once the second half is in registers (and the digits above are
+            // written), tile i + 1's MMAs may start; its combination runs
+            // while they do.
             const float su = dg_scale_up(Eg_i);
             double2 *gt = a + tile_base(blockIdx.x + (uint64_t)i * stride);
+            uint32_t acc[kDigitLevels - 1][8];
+            auto drain = [&](int hf) {
+                uint32_t a4[8];
+                const uint32_t c0 = tmem + lane_off + (uint32_t)(16 * qq + 8 * hf);
+                tmem_ld8(c0 + kReals * 3, acc[3]);
+                tmem_ld8(c0 + kReals * 4, a4);
+                tmem_ld8(c0 + kReals * 0, acc[0]);
+                tmem_ld8(c0 + kReals * 1, acc[1]);
+                tmem_ld8(c0 + kReals * 2, acc[2]);
+                tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const df re = dg_combine_df(__uint_as_float(acc[0][2 * j]), __uint_as_float(acc[1][2 * j]),
-                                            __uint_as_float(acc[2][2 * j]), __uint_as_float(acc[3][2 * j]), su);
-                const df im = dg_combine_df(__uint_as_float(acc[0][2 * j + 1]), __uint_as_float(acc[1][2 * j + 1]),
-                                            __uint_as_float(acc[2][2 * j + 1]), __uint_as_float(acc[3][2 * j + 1]),
-                                            su);
-                const uint64_t go = gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
-                if (OUT_IEEE) {
-                    gt[go] = make_double2(df_to_double(re), df_to_double(im));
-                } else {
-                    *reinterpret_cast<float4 *>(gt + go) = make_float4(re.h, re.l, im.h, im.l);
+                for (int c = 0; c < 8; c++)
+                    acc[3][c] = __float_as_uint(dg_fold_high(__uint_as_float(acc[3][c]), __uint_as_float(a4[c])));
+            };
+            // the combination of one half: output amplitudes 8 qq + 4 hf + jj,
+            // straight from registers to global memory
+            auto combine = [&](int hf) {
+#pragma unroll
+                for (int jj = 0; jj < 4; jj++) {
+                    const int j = 4 * hf + jj;
+                    const df re = dg_combine_df(__uint_as_float(acc[0][2 * jj]), __uint_as_float(acc[1][2 * jj]),
+                                                __uint_as_float(acc[2][2 * jj]), __uint_as_float(acc[3][2 * jj]), su);
+                    const df im = dg_combine_df(__uint_as_float(acc[0][2 * jj + 1]),
+                                                __uint_as_float(acc[1][2 * jj + 1]),
+                                                __uint_as_float(acc[2][2 * jj + 1]),
+                                                __uint_as_float(acc[3][2 * jj + 1]), su);
+                    const uint64_t go =
+                        gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
+                    if (OUT_IEEE) {
+                        gt[go] = make_double2(df_to_double(re), df_to_double(im));
+                    } else {
+                        *reinterpret_cast<float4 *>(gt + go) = make_float4(re.h, re.l, im.h, im.l);
+                    }
                 }
-            }
+            };
+            drain(0);
+            combine(0);
+            drain(1);
+            tmem_st_wait();
+            if (next) arrive_ready(i + 1);
+            combine(1);
             if (i + 2 < count && !fetch(i + 2)) aborted = true;
         }
         if (aborted && tid == 0) atomicExch(err, kErrTimeout);
-    }
-    if (warp == 0) {  // every fetch has landed before the CTA leaves
-        if (issued0) mbar_wait_bounded(&bar_ld[0], (issued0 - 1u) & 1u, kWaitBudget128);
-        if (issued1) mbar_wait_bounded(&bar_ld[1], (issued1 - 1u) & 1u, kWaitBudget128);
     }
     tc_fence_before();
     __syncthreads();
@@ -442,7 +489,7 @@ static cudaError_t launch_tc128(void *amp, const TileGeom &g, const FusedMap &fm
     const uint64_t ntiles = 1ull << (g.n - kTileBits);
     uint64_t grid = ntiles < (uint64_t)sm_count ? ntiles : (uint64_t)sm_count;
     k_fused_tc_c128<IN_IEEE, OUT_IEEE>
-        <<<(unsigned)grid, kThreads128, smem, s>>>(static_cast<double2 *>(amp), g, fm, bmat, err, ntiles);
+        <<<(unsigned)grid, kThreadsAll128, smem, s>>>(static_cast<double2 *>(amp), g, fm, bmat, err, ntiles);
     return cudaGetLastError();
 }
 
