@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *s_b = smem_raw;                    // six B slices
     unsigned char *s_buf0 = smem_raw + kBBytes;       // two input buffers
-    // bar_ld: tile arrived in buffer b; bar_free: the compute warps left
-    // buffer b; bar_ready: tile's A slices written and the last tile's
+    // bar_ld: tile arrived in buffer b; bar_free: the compute warps have read
+    // buffer b into registers; bar_ready: tile's A slices written and the last tile's
     // accumulators read (MMAs may start); bar_mma: MMAs done; bar_b: B loaded
     __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mma, bar_b;
     __shared__ uint32_t tmem_base_s;
@@ -316,6 +316,8 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             }
             s_max[b][qq][m] = mx;
             quarter_sync(1u + (uint32_t)lq);
+            // this warp's amplitudes are in registers: its share of the buffer is free
+            if (lane == 0) mbar_arrive(&bar_free[b]);
             Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
             return true;
         };
@@ -338,15 +340,11 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             }
         };
         // tile t's A slices are written (and tile t - 1's accumulators read):
-        // one arrival per warp on bar_ready, and on bar_free of the buffer
-        // tile t came from (its amplitudes were read in fetch(t))
-        auto arrive_ready = [&](uint32_t t) {
+        // one arrival per warp on bar_ready
+        auto arrive_ready = [&]() {
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&bar_free[t & 1u]);
-                mbar_arrive(&bar_ready);
-            }
+            if (lane == 0) mbar_arrive(&bar_ready);
         };
 
         // prologue: tile 0 into tensor memory (its MMAs start), tile 1 fetched
@@ -356,7 +354,7 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             if (!aborted) {
                 digits();
                 tmem_st_wait();
-                arrive_ready(0);
+                arrive_ready();
                 Eg = Eg_next;
                 if (count > 1) aborted = !fetch(1);
             }
@@ -424,7 +422,7 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             combine(0);
             drain(1);
             tmem_st_wait();
-            if (next) arrive_ready(i + 1);
+            if (next) arrive_ready();
             combine(1);
             if (i + 2 < count && !fetch(i + 2)) aborted = true;
         }
