@@ -19,22 +19,31 @@
 // first block of a run reads IEEE doubles (IN_IEEE) and the last one writes
 // them (OUT_IEEE), converting with integer operations (df64.cuh).
 //
-// One CTA per SM, 512 threads: the four warps of a tensor-memory lane
-// quarter share its 32 groups, each taking one quarter of a group's 32
-// amplitudes -- which is one K step (16 reals) of the product.  Per tile of
-// 128 groups (4096 amplitudes, 64 KiB):
-//   1. the tile arrives by bulk asynchronous copies (TMA engine) into one of
-//      two shared-memory buffers, fetched two tiles ahead;
-//   2. split: each thread reads its 8 amplitudes, the four threads of a group
-//      agree on its largest exponent, and the thread writes its digits into
-//      the A slices in tensor memory (its lane, 8 columns per slice);
-//   3. one thread issues the MMAs (21 products x 4 K steps of 16, in 48
-//      instructions: slices of B side by side along N);
-//   4. epilogue: each thread reads the five accumulators of its 16 output
-//      reals, combines them into doubles and writes them into the same
-//      buffer at the groups' positions (its input there was consumed in 2);
-//   5. bulk stores write the tile back; once they have read the buffer, the
-//      fetch of the tile two ahead reuses it.
+// One CTA per SM, 640 threads (20 warps, five per scheduler, 96 registers
+// each): 16 compute warps -- the four warps of a tensor-memory lane quarter
+// share its 32 groups, each taking one quarter of a group's 32 amplitudes,
+// which is one K step (16 reals) of the product -- and one duty warp per
+// scheduler: the MMA warp, the fetch warp and two idle ones.  The duty warps
+// issue work whose issue stalls (the tensor pipe and the bulk-copy engine
+// take instructions only as fast as they execute them), so no compute warp
+// waits for it.  Per tile of 128 groups (4096 amplitudes, 64 KiB):
+//   1. the fetch warp copies the tile (bulk asynchronous copies, TMA engine)
+//      into one of two shared-memory buffers, as soon as the compute warps
+//      have read the tile two before out of it;
+//   2. fetch: each compute thread reads its 8 amplitudes into registers and
+//      the four threads of a group agree on its largest exponent;
+//   3. digits: the thread writes the six slices of its amplitudes into the A
+//      slices in tensor memory (its lane, 8 columns per slice);
+//   4. the MMA warp issues the 21 products x 4 K steps of 16 as 48
+//      instructions (slices of B side by side along N);
+//   5. combination: each thread reads the accumulators of its 16 output
+//      reals in two halves of 8, adds the levels in double-float and stores
+//      the amplitudes from registers to global memory.
+// The compute warps run tile i + 1's digits and tile i's combination around
+// tile i + 1's MMAs: once the second half of tile i's accumulators is read,
+// the next MMAs may start and the rest of the combination runs beside them.
+// Hand-offs go through mbarriers (tile fetched, buffer read, A slices ready,
+// MMAs done), every wait bounded.
 // Tensor memory: accumulators at columns 0..319 (level L at 64 L), the A
 // slices at 320 + 48 s + 8 i (K step s, slice i): all 512 columns.
 #include <cstring>
@@ -87,18 +96,6 @@ __device__ __forceinline__ void umma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, u
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r0), "r"(r1),
-                 "r"(r2), "r"(r3)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t r0, uint32_t r1) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0), "r"(r1) : "memory");
 }
@@ -110,31 +107,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
 __device__ __forceinline__ uint4 lds_u4(uint32_t addr) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
     return v;
 }
-__device__ __forceinline__ void sts_u4(uint32_t addr, uint4 v) {
-    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
 
 // barrier of the four warps sharing a tensor-memory lane quarter
 __device__ __forceinline__ void quarter_sync(uint32_t id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
-// barrier of the 512 compute threads (id 5), with an OR vote
-__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 5, 512;" ::: "memory"); }
+// OR vote of the 512 compute threads (named barrier 5)
 __device__ __forceinline__ bool compute_any(bool v) {
     uint32_t r;
     asm volatile(
