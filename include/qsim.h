@@ -60,8 +60,12 @@ typedef enum {
                                Per-gate sweeps and tile passes compute in
                                double-float (an unevaluated sum of two FP32
                                values, about 48 significand bits; magnitudes
-                               below 2^-126 flush to zero), dense blocks on the
-                               CUDA cores in FP64.  Sec. III.A asks for 13-15
+                               below 2^-126 flush to zero).  Dense 5-qubit
+                               blocks run on the tensor cores as exact bf16
+                               digit-slice products summed in double-float
+                               (an output's error below 2^-43.7 of its group's
+                               largest magnitude); other dense blocks in FP64
+                               on the CUDA cores.  Sec. III.A asks for 13-15
                                significant digits; double-float keeps ~14.4. */
 } qsim_dtype;
 
@@ -98,8 +102,9 @@ enum {
     QSIM_MODE_PERGATE = 0, /* one sweep of the state per gate (Sec. III.A) */
     QSIM_MODE_FUSED = 1,   /* planner: shared-memory tile passes, qubit
                               interchanges and dense fused blocks */
-    QSIM_MODE_AUTO = 2     /* plans: one candidate per tile size (and, for
-                              complex64, tensor-core fusion width 4 and 5);
+    QSIM_MODE_AUTO = 2     /* plans: one candidate per tile size and per
+                              tensor-core fusion width (complex64: 4 and 5;
+                              complex128: 5);
                               the plan's first runs time each candidate with
                               CUDA events on the handle's stream, every later
                               run uses the fastest.  Every run applies the
@@ -112,8 +117,9 @@ typedef struct {
     int32_t tile_bits;  /* T, qubits held per shared-memory tile; 0 = default */
     int32_t fuse_k;     /* > 0: apply the circuit as dense blocks of at most fuse_k qubits
                            (1..6), each the FP64 product of its gates: complex64 with
-                           k = 4 or 5 on the tensor cores (3xTF32), other widths and
-                           complex128 (in FP64) on the CUDA cores.  A block may take a
+                           k = 4 or 5 on the tensor cores (3xTF32), complex128 with
+                           k = 5 on the tensor cores (exact bf16 digit slices), other
+                           widths on the CUDA cores (FP64 for complex128).  A block may take a
                            gate past earlier gates on other qubits (they commute).
                            QSIM_EINVAL if a gate acts on more than fuse_k qubits
                            (controls included).  0 or -1: tile passes */
@@ -191,7 +197,9 @@ QSIM_API qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g);
  * only in those qubits, a'_r = sum_c U_rc a_c.  1 <= k <= min(6, n), else
  * EINVAL.  A product of
  * the paper's gates on k qubits, built on the host in FP64, applied in one
- * pass of the state. */
+ * pass of the state: on the tensor cores for complex64 with k = 4, 5 and for
+ * complex128 with k = 5 when every entry of U lies in (-2, 2) (n >= k + 7),
+ * otherwise on the CUDA cores. */
 QSIM_API qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U);
 
 /* qsim_swap_qubits: the SWAP command of App. A (Sec. III.B): interchange the
