@@ -117,6 +117,8 @@ def path_label(dt, pst, pergate=False):
         return "planner (tile passes)"
     if dt == "c64" and k in (4, 5):
         return "planner (fused %d-qubit blocks on the tensor cores, 3xTF32)" % k
+    if dt == "c64" and k == 6:
+        return "planner (fused 6-qubit blocks on the tensor cores, bf16x3)"
     if dt == "c128" and k == 5:
         return "planner (fused 5-qubit blocks on the tensor cores, bf16 digit slices)"
     return "planner (fused %d-qubit blocks on the CUDA cores)" % k
@@ -411,6 +413,17 @@ def run_ours(args, w, ws, rank, local):
                     "alg_flops_per_launch": fl / nl, "alg_tflops": tflops, "launches": nl,
                     "avg_launch_ms": ms / nl}
         frac_alu = ach / bp
+    if fam == "fused_tc_bf16x3":
+        # six bf16 slice products per algorithmic product
+        bp = tf32_peak()[0] / TF32_OVER_BF16
+        ach = 6.0 * tflops
+        alu_roof = {"bound": "tensor", "kernel": fam, "achieved": ach, "peak": bp, "unit": "TFLOP/s (bf16)",
+                    "frac": ach / bp, "traffic": traffic,
+                    "peak_source": "bf16 dense: measured burst GEMM (MEASURED_PEAKS.json); 6 bf16 slice products "
+                                   "per algorithmic product",
+                    "alg_flops_per_launch": fl / nl, "alg_tflops": tflops, "launches": nl,
+                    "avg_launch_ms": ms / nl}
+        frac_alu = ach / bp
     if fam == "fused_tensor_core":
         # 3xTF32: three TF32 products per algorithmic product; the achieved
         # figure counts algorithmic flops once
@@ -613,6 +626,7 @@ def config_lines(q, main, args):
     c2 = {"c128_autotuned": main,
           "c64_tile_passes": _timed_circuit(q, 30, "c64", g, x, reps, tile_bits=12),
           "c64_tensor_cores_k5": _timed_circuit(q, 30, "c64", g, x, reps, fuse_k=5),
+          "c64_tensor_cores_k6": _timed_circuit(q, 30, "c64", g, x, reps, fuse_k=6),
           "c128_tensor_cores_k5": _timed_circuit(q, 30, "c128", g, x, reps, fuse_k=5),
           "c128_tile_passes": _timed_circuit(q, 30, "c128", g, x, 2, tile_bits=12),
           "c128_pergate": _timed_circuit(q, 30, "c128", g, x, 2, mode=q.MODE_PERGATE)}
@@ -622,7 +636,8 @@ def config_lines(q, main, args):
     a, b = inputs.adder_pairs(15, 8, seed=3)[0]
     g = inputs.adder_circuit([a, b], 15)
     ad = {"tile_passes": _timed_circuit(q, 30, "c64", g, 0, reps),
-          "tensor_cores_k5": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=5)}
+          "tensor_cores_k5": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=5),
+          "tensor_cores_k6": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=6)}
     st = q.State(30, "c64")
     st.run(g, fuse_k=5)
     qp = st.qubit_probs()

@@ -103,7 +103,7 @@ enum {
     QSIM_MODE_FUSED = 1,   /* planner: shared-memory tile passes, qubit
                               interchanges and dense fused blocks */
     QSIM_MODE_AUTO = 2     /* plans: one candidate per tile size and per
-                              tensor-core fusion width (complex64: 4 and 5;
+                              tensor-core fusion width (complex64: 4, 5, 6;
                               complex128: 5);
                               the plan's first runs time each candidate with
                               CUDA events on the handle's stream, every later
@@ -117,7 +117,8 @@ typedef struct {
     int32_t tile_bits;  /* T, qubits held per shared-memory tile; 0 = default */
     int32_t fuse_k;     /* > 0: apply the circuit as dense blocks of at most fuse_k qubits
                            (1..6), each the FP64 product of its gates: complex64 with
-                           k = 4 or 5 on the tensor cores (3xTF32), complex128 with
+                           k = 4 or 5 on the tensor cores (3xTF32) and k = 6 (bf16 in
+                           three slices, six products), complex128 with
                            k = 5 on the tensor cores (exact bf16 digit slices), other
                            widths on the CUDA cores (FP64 for complex128).  A block may take a
                            gate past earlier gates on other qubits (they commute).
@@ -197,7 +198,7 @@ QSIM_API qsim_status qsim_apply_gate(qsim_handle h, const qsim_gate *g);
  * only in those qubits, a'_r = sum_c U_rc a_c.  1 <= k <= min(6, n), else
  * EINVAL.  A product of
  * the paper's gates on k qubits, built on the host in FP64, applied in one
- * pass of the state: on the tensor cores for complex64 with k = 4, 5 and for
+ * pass of the state: on the tensor cores for complex64 with k = 4, 5, 6 and for
  * complex128 with k = 5 when every entry of U lies in (-2, 2) (n >= k + 7),
  * otherwise on the CUDA cores. */
 QSIM_API qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const double *U);

@@ -83,10 +83,10 @@ struct qsim_state {
 
 // Kernel families reported by qsim_profile_read.
 enum Fam { F_INIT, F_PAIR, F_DIAG, F_DENSE, F_TILE, F_NORM, F_BITS, F_PROBS, F_GATHER, F_SAMPLE, F_FUSED_TC,
-           F_BATCH, F_FUSED_TC128, F_COUNT };
+           F_BATCH, F_FUSED_TC128, F_FUSED_TC6, F_COUNT };
 static const char *kFamName[F_COUNT] = {"init_basis", "pair_sweep", "diag_sweep", "dense_cuda_core", "tile_pass",
                                         "norm", "bit_probs", "probs", "gather", "sample", "fused_tensor_core",
-                                        "batch", "fused_tc_digits"};
+                                        "batch", "fused_tc_digits", "fused_tc_bf16x3"};
 
 static cudaEvent_t take_event(qsim_state *h) {
     if (!h->pool.empty()) {
@@ -496,6 +496,7 @@ struct qsim_plan_s {
     // run on the CUDA cores (k_dense): their matrices in the state's precision
     bool cuda_core = false;
     bool tc128 = false;  // complex128 blocks on the tensor cores (bmats holds bf16 slices)
+    bool tc6 = false;    // complex64 6-qubit blocks on the tensor cores (bmats holds bf16 slices)
     std::vector<unsigned char> cmats;
     size_t cmat_stride = 0;
     void *d_cmats = nullptr;
@@ -563,6 +564,26 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         P.blocks.clear();
         P.bmats.clear();
         P.stats.alg_flops = 0.0;
+    }
+    if (o.fuse_k == 6 && h->dt == QSIM_C64 && fused_tc6_supported(h->n)) {
+        // complex64 6-qubit blocks on the tensor cores (bf16 hi/mid/lo slices)
+        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+            return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
+        const size_t per = fused_tc6_b_bytes() / sizeof(float);
+        P.bmats.resize(per * P.blocks.size());
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            TileGeom g;
+            FusedMap fm;
+            if (!fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm))
+                return fail(QSIM_EUNSUPPORTED, "no tile geometry for a fused block");
+            fused_tc6_prepare_b(P.blocks[b].U.data(), reinterpret_cast<uint16_t *>(P.bmats.data() + per * b));
+            P.stats.alg_flops += P.blocks[b].flops;
+        }
+        P.tc6 = true;
+        P.stats.passes = (int)P.blocks.size();
+        P.stats.tile_bits = o.fuse_k + 7;
+        P.stats.alg_bytes = 2.0 * (double)state_bytes(h) * P.stats.passes;
+        return QSIM_OK;
     }
     if (o.fuse_k > 0 && (h->dt == QSIM_C128 || !fused_tc_supported((int)h->dt, o.fuse_k, h->n))) {
         // dense blocks on the CUDA cores (complex128, k = 1..6, small registers)
@@ -640,6 +661,20 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
                       [&] { return launch_dense(h->amp, (int)h->dt, h->n, k, P.blocks[b].pos, dU, h->stream); },
                       P.blocks[b].flops),
                "fused block (CUDA cores)");
+        }
+        return QSIM_OK;
+    }
+    if (P.tc6) {
+        const size_t per = fused_tc6_b_bytes() / sizeof(float);
+        for (size_t b = 0; b < P.blocks.size(); b++) {
+            TileGeom g;
+            FusedMap fm;
+            fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
+            const uint16_t *bm = reinterpret_cast<const uint16_t *>(d_bmats + per * b);
+            CK(launch(h, F_FUSED_TC6, 2.0 * (double)state_bytes(h), 1,
+                      [&] { return launch_fused_tc6(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream); },
+                      P.blocks[b].flops),
+               "fused block (tensor cores, 6 qubits)");
         }
         return QSIM_OK;
     }
@@ -804,6 +839,7 @@ qsim_status qsim_plan_create(qsim_handle h, const qsim_gate *gates, size_t ng, c
         for (int T : {12, 13}) add(T, 0);
         for (int k : {4, 5})
             if (fused_tc_supported((int)h->dt, k, h->n)) add(0, k);
+        if (fused_tc6_supported(h->n)) add(0, 6);
     }
     qsim_plan_s *A = new qsim_plan_s;
     A->n = h->n;
@@ -994,6 +1030,24 @@ qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, const doub
                "fused gate (tensor cores, complex128)");
             return QSIM_OK;
         }
+    }
+    if (h->dt == QSIM_C64 && k == 6 && fused_tc6_supported(h->n) && fused_geometry(h->n, k, pos, g, fm)) {
+        std::vector<uint16_t> b(fused_tc6_b_bytes() / sizeof(uint16_t));
+        fused_tc6_prepare_b(U, b.data());
+        const size_t bytes = fused_tc6_b_bytes();
+        qsim_status st = ensure_dense(h, bytes);
+        if (st != QSIM_OK) return st;
+        CK(cudaMemcpyAsync(h->d_dense, b.data(), bytes, cudaMemcpyHostToDevice, h->stream), "upload U");
+        CK(cudaStreamSynchronize(h->stream), "sync");  // b is freed on return
+        h->h2d += bytes;
+        CK(launch(h, F_FUSED_TC6, 2.0 * (double)state_bytes(h), 1,
+                  [&] {
+                      return launch_fused_tc6(h->amp, g, fm, static_cast<const uint16_t *>(h->d_dense), h->d_err,
+                                              h->sm_count, h->stream);
+                  },
+                  flops),
+           "fused gate (tensor cores, 6 qubits)");
+        return QSIM_OK;
     }
     if (h->dt == QSIM_C64 && fused_tc_supported((int)h->dt, k, h->n) && fused_geometry(h->n, k, pos, g, fm)) {
         // tensor cores: B operand (3xTF32 head and tail) from U

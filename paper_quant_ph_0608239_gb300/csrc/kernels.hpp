@@ -203,6 +203,15 @@ bool fused_tc128_prepare_b(const double *U, uint16_t *out);
 cudaError_t launch_fused_tc128(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat,
                                uint32_t *err, int sm_count, cudaStream_t s, bool in_ieee, bool out_ieee);
 
+// Dense 6-qubit gate on the tensor cores for complex64 (k_fused_tc6.cu: bf16
+// hi/mid/lo slices, six products, FP32 accumulation; n >= 13): bmat = device
+// copy of fused_tc6_prepare_b's output (fused_tc6_b_bytes() bytes).
+bool fused_tc6_supported(int n);
+size_t fused_tc6_b_bytes();
+void fused_tc6_prepare_b(const double *U, uint16_t *out);
+cudaError_t launch_fused_tc6(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat, uint32_t *err,
+                             int sm_count, cudaStream_t s);
+
 // ------------------------------------------------------------ batches
 struct BatchCircuit {
     void *amp;            // complex64 state of the circuit

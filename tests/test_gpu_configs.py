@@ -103,7 +103,7 @@ def test_c2_prefix_elementwise_every_autotune_candidate(q, c2_prefix, dt):
 
     def check(c, prof):
         if c["fuse_k"]:
-            assert "fused_tensor_core" in prof or "fused_tc_digits" in prof, prof
+            assert "fused_tensor_core" in prof or "fused_tc_digits" in prof or "fused_tc_bf16x3" in prof, prof
         else:
             assert "tile_pass" in prof, prof
         e, rel, fid = compare(st.get_state(), ref)
@@ -117,7 +117,7 @@ def test_c2_prefix_elementwise_every_autotune_candidate(q, c2_prefix, dt):
 
     seen = run_candidates(q, st, plan, x0, check)
     # the tensor-core widths are among the candidates
-    assert ({4, 5} if dt == "c64" else {5}) <= {c["fuse_k"] for c in seen}, seen
+    assert ({4, 5, 6} if dt == "c64" else {5}) <= {c["fuse_k"] for c in seen}, seen
     plan.free()
     st.free()
 
@@ -137,9 +137,11 @@ def test_c4_slice_every_autotune_candidate(q):
         assert e < TOL["c64"] and rel < 1e-4 and 1 - fid < 1e-8, (c, e, rel, fid)
         if c["fuse_k"] in (4, 5):
             assert "fused_tensor_core" in prof and "tile_pass" not in prof, prof
+        if c["fuse_k"] == 6:
+            assert "fused_tc_bf16x3" in prof and "tile_pass" not in prof, prof
 
     seen = run_candidates(q, st, plan, x0, check)
-    assert {4, 5} <= {c["fuse_k"] for c in seen}
+    assert {4, 5, 6} <= {c["fuse_k"] for c in seen}
     plan.free()
     st.free()
 
@@ -210,7 +212,7 @@ def _outcome(qp):
     return sum(1 << b for b in range(qp.size) if qp[b] > 0.5), float(np.max(np.minimum(qp, 1 - qp)))
 
 
-@pytest.mark.parametrize("k", [5])
+@pytest.mark.parametrize("k", [5, 6])
 def test_adder_2x15_eight_pairs_tensor_cores(q, k):
     m = 15
     st = q.State(2 * m, "c64")
@@ -220,7 +222,7 @@ def test_adder_2x15_eight_pairs_tensor_cores(q, k):
         st.profile(True)
         st.run(gates, fuse_k=k)
         prof = st.profile_read()
-        assert "fused_tensor_core" in prof and "tile_pass" not in prof, prof
+        assert ("fused_tensor_core" if k < 6 else "fused_tc_bf16x3") in prof and "tile_pass" not in prof, prof
         got, spread = _outcome(st.qubit_probs())
         assert got == inputs.adder_expected_index([a, b], m), (a, b, got)
         assert spread < 1e-4, (a, b, spread)

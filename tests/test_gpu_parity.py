@@ -588,7 +588,52 @@ def test_fused_blocks_circuit_c128_tensor_cores(q, n):
     st.free()
 
 
-@pytest.mark.parametrize("dt,k", [("c128", 3), ("c128", 6), ("c64", 6)])
+@pytest.mark.parametrize("n,where", [(13, "low"), (16, "high"), (16, "mixed"), (20, "mixed"), (22, "high")])
+def test_fused_tensor_cores_c64_k6(q, n, where):
+    # 6-qubit blocks: bf16 hi/mid/lo slices, six products on the tensor cores
+    k = 6
+    rng = np.random.default_rng(270 + n + len(where))
+    if where == "low":
+        qs = list(rng.permutation(k))
+    elif where == "high":
+        qs = [int(x) for x in rng.permutation(np.arange(n - k, n))]
+    else:
+        qs = [int(x) for x in rng.permutation(n)[:k]]
+    Z = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+    U, _ = np.linalg.qr(Z)
+    psi = rand_state(n, 290 + n)
+    ref = oracle.apply_dense(psi.astype(np.complex64).astype(np.complex128), n, qs, U)
+    st = q.State(n, "c64")
+    st.set_state(psi)
+    st.profile(True)
+    st.apply_fused(qs, U)
+    prof = st.profile_read()
+    assert "fused_tc_bf16x3" in prof, prof
+    e = err(st.get_state(), ref)
+    # bf16x3 keeps about 2^-24 relative per product and FP32 sums of 128 terms
+    assert e < 2e-5, e
+    st.free()
+
+
+@pytest.mark.parametrize("n", [13, 18])
+def test_fused_blocks_circuit_c64_k6(q, n):
+    gates = inputs.random_circuit(n, 6, seed=600 + n)
+    rng = np.random.default_rng(n + 60)
+    gates += [g for g in controlled_gates(rng, n, 12) if len(g.controls) + len(g.targets) <= 6]
+    x0 = inputs.random_basis(n, seed=n + 7)
+    ref = oracle.run(n, gates, x0=x0)
+    st = q.State(n, "c64")
+    st.set_basis(x0)
+    st.profile(True)
+    st.run(gates, fuse_k=6)
+    prof = st.profile_read()
+    assert "fused_tc_bf16x3" in prof and "tile_pass" not in prof and "dense_cuda_core" not in prof, prof
+    e = err(st.get_state(), ref)
+    assert e < 2e-5, e
+    st.free()
+
+
+@pytest.mark.parametrize("dt,k", [("c128", 3), ("c128", 6), ("c64", 3)])
 def test_fused_blocks_cuda_cores(q, dt, k):
     # fusion widths and precisions the tensor-core kernel does not take run
     # as dense blocks on the CUDA cores (FP64 for complex128)
