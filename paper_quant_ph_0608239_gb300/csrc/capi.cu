@@ -83,10 +83,10 @@ struct qsim_state {
 
 // Kernel families reported by qsim_profile_read.
 enum Fam { F_INIT, F_PAIR, F_DIAG, F_DENSE, F_TILE, F_NORM, F_BITS, F_PROBS, F_GATHER, F_SAMPLE, F_FUSED_TC,
-           F_BATCH, F_FUSED_TC128, F_FUSED_TC6, F_COUNT };
+           F_BATCH, F_FUSED_TC128, F_FUSED_TC6, F_PERM, F_COUNT };
 static const char *kFamName[F_COUNT] = {"init_basis", "pair_sweep", "diag_sweep", "dense_cuda_core", "tile_pass",
                                         "norm", "bit_probs", "probs", "gather", "sample", "fused_tensor_core",
-                                        "batch", "fused_tc_digits", "fused_tc_bf16x3"};
+                                        "batch", "fused_tc_digits", "fused_tc_bf16x3", "interchange"};
 
 static cudaEvent_t take_event(qsim_state *h) {
     if (!h->pool.empty()) {
@@ -1102,7 +1102,7 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
     int T, L, RB;
     qsim_opts po;
     qsim_default_opts(&po);
-    po.tile_bits = h->dt == QSIM_C64 ? 12 : 11;  // shared-memory kernel: one in-tile permutation
+    po.tile_bits = permute_tile_bits((int)amp_bytes(h->dt));
     tile_defaults(h, &po, T, L, RB);
     uint64_t need = 0;
     for (int i = 0; i < K; i++) need |= (1ull << l[i]) | (1ull << hb[i]);
@@ -1140,6 +1140,20 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
             if (g.hb[k] == b) return g.L + k;
         return -1;
     };
+    if (K <= kMaxPermPairs && g.H <= 10 && g.L >= 1) {
+        // the interchange kernel: tile in shared memory, elements gathered
+        // through the permutation, coalesced stores
+        PermPairs pp{};
+        pp.K = K;
+        for (int i = 0; i < K; i++) {
+            pp.lo[i] = (int8_t)local(l[i]);
+            pp.hi[i] = (int8_t)local(hb[i]);
+        }
+        CK(launch(h, F_PERM, 2.0 * (double)state_bytes(h), 1,
+                  [&] { return launch_permute(h->amp, (int)amp_bytes(h->dt), g, pp, h->d_err, h->sm_count, h->stream); }),
+           "interchange pass");
+        return QSIM_OK;
+    }
     Plan plan;
     TileOp op{};
     op.kind = TOP_PERM;

@@ -212,6 +212,20 @@ void fused_tc6_prepare_b(const double *U, uint16_t *out);
 cudaError_t launch_fused_tc6(void *amp, const TileGeom &g, const FusedMap &fm, const uint16_t *bmat, uint32_t *err,
                              int sm_count, cudaStream_t s);
 
+// ------------------------------------------------------------ interchange
+// K pairs of local (tile) bits exchanged by the interchange pass
+// (k_permute.cu): lo[i] <-> hi[i], tile-local bit positions.
+constexpr int kMaxPermPairs = 6;
+struct PermPairs {
+    int32_t K;
+    int8_t lo[8];
+    int8_t hi[8];
+};
+// Tile bits of the interchange pass for elements of elem_bytes (8 or 16).
+int permute_tile_bits(int elem_bytes);
+cudaError_t launch_permute(void *amp, int elem_bytes, const TileGeom &g, const PermPairs &pp, uint32_t *err,
+                           int sm_count, cudaStream_t s);
+
 // ------------------------------------------------------------ batches
 struct BatchCircuit {
     void *amp;            // complex64 state of the circuit
