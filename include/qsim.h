@@ -207,8 +207,12 @@ QSIM_API qsim_status qsim_apply_fused(qsim_handle h, int k, const int *qubits, c
  * index-bit positions that hold logical qubits a[i] and b[i], i < K, moving
  * the amplitudes in one pass (Eqs. onequbitchange, twoqubitchange0-5 and the
  * K-pair generalisation) and updating the qubit-to-bit map.  The logical state
- * is unchanged; only its layout in memory changes.  1 <= K <= n/2, all 2K
- * qubits distinct. */
+ * is unchanged; only its layout in memory changes.  1 <= K <= min(8, n/2),
+ * all 2K qubits distinct.  K = 1: one sweep over the half of the state whose
+ * two bits differ.  K >= 2: one pass reading and writing the state once
+ * (tiles of 2^11 complex64 or 2^10 complex128 amplitudes holding all 2K bits
+ * in shared memory); when the 2K bits do not fit one tile the pairs are
+ * exchanged in groups, one pass per group. */
 QSIM_API qsim_status qsim_swap_qubits(qsim_handle h, int K, const int *a, const int *b);
 
 /* qsim_permute_bits: the raw data movement of an interchange: exchange the

@@ -1104,6 +1104,7 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
     qsim_default_opts(&po);
     po.tile_bits = permute_tile_bits((int)amp_bytes(h->dt));
     tile_defaults(h, &po, T, L, RB);
+    L = T;  // runs as long as the tile allows (L shrinks below for pair bits above it)
     uint64_t need = 0;
     for (int i = 0; i < K; i++) need |= (1ull << l[i]) | (1ull << hb[i]);
     if (h->n <= T) {
@@ -1120,7 +1121,14 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
             for (int b = 0; b < 64; b++)
                 if (((need >> b) & 1ull) && b >= L) above++;
         }
-        if (above > T - L || above > 10) return fail(QSIM_EUNSUPPORTED, "too many pairs for one tile");
+        if (above > T - L || above > 10) {
+            // more pair bits than one tile holds: the pairs commute, so
+            // exchange them in two groups, one pass each
+            if (K < 2) return fail(QSIM_EUNSUPPORTED, "pair does not fit a tile");
+            const qsim_status st = permute_phys(h, K / 2, l, hb);
+            if (st != QSIM_OK) return st;
+            return permute_phys(h, K - K / 2, l + K / 2, hb + K / 2);
+        }
     }
     TileGeom g{};
     g.n = h->n;
@@ -1140,7 +1148,7 @@ static qsim_status permute_phys(qsim_state *h, int K, const int *l, const int *h
             if (g.hb[k] == b) return g.L + k;
         return -1;
     };
-    if (K <= kMaxPermPairs && g.H <= 10 && g.L >= 1) {
+    if (K <= kMaxPermPairs && g.H <= kPermMaxH && g.L >= 1 && g.L + g.H >= 8) {
         // the interchange kernel: tile in shared memory, elements gathered
         // through the permutation, coalesced stores
         PermPairs pp{};

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "perm_layout.hpp"
 
 namespace qsim {
 
@@ -214,13 +215,8 @@ cudaError_t launch_fused_tc6(void *amp, const TileGeom &g, const FusedMap &fm, c
 
 // ------------------------------------------------------------ interchange
 // K pairs of local (tile) bits exchanged by the interchange pass
-// (k_permute.cu): lo[i] <-> hi[i], tile-local bit positions.
-constexpr int kMaxPermPairs = 6;
-struct PermPairs {
-    int32_t K;
-    int8_t lo[8];
-    int8_t hi[8];
-};
+// (k_permute.cu): PermPairs in perm_layout.hpp; launch_permute fills its
+// lane and skew layout.  Needs T = g.L + g.H >= 8, g.H <= kPermMaxH, g.L >= 1.
 // Tile bits of the interchange pass for elements of elem_bytes (8 or 16).
 int permute_tile_bits(int elem_bytes);
 cudaError_t launch_permute(void *amp, int elem_bytes, const TileGeom &g, const PermPairs &pp, uint32_t *err,

@@ -409,6 +409,38 @@ def test_permute_bits_vs_oracle(q, dt, pairs):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("kind,K", [("cross", 2), ("cross", 3), ("cross", 6), ("any", 4), ("any", 5), ("low", 2)])
+def test_permute_bits_random_pairs_many_tiles(q, dt, kind, K):
+    """The interchange pass at 22 qubits (1024 to 4096 tiles, several laps of
+    each CTA's four-stage ring): pairs from the low bits to high ones at random
+    places ("cross"), anywhere ("any") or all among the lowest 11 bits ("low",
+    the slow in-run layout).  Bit-exact against the oracle's permutation."""
+    n = 22
+    rng = np.random.default_rng(100 * K + len(kind))
+    if kind == "cross":
+        lo = rng.choice(np.arange(0, 8), K, replace=False)
+        hi = rng.choice(np.arange(12, n), K, replace=False)
+    elif kind == "low":
+        b = rng.choice(np.arange(0, 11), 2 * K, replace=False)
+        lo, hi = b[:K], b[K:]
+    else:
+        b = rng.choice(np.arange(n), 2 * K, replace=False)
+        lo, hi = b[:K], b[K:]
+    pairs = [(int(a), int(c)) for a, c in zip(lo, hi)]
+    psi = rand_state(n, 11).astype(np.complex128)
+    if dt == "c64":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    st = q.State(n, dt)
+    st.set_state(psi)
+    st.permute_bits([p[0] for p in pairs], [p[1] for p in pairs])
+    got = st.get_state()
+    assert np.array_equal(got, oracle.permute_bits(psi, n, pairs).astype(got.dtype)), pairs
+    st.permute_bits([p[0] for p in pairs], [p[1] for p in pairs])  # an involution: back to the start
+    assert np.array_equal(st.get_state(), psi.astype(got.dtype))
+    st.free()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 def test_swap_qubits_keeps_logical_state(q, dt):
     n = 15
     gates = inputs.random_circuit(n, 6, seed=5)

@@ -180,7 +180,7 @@ def test_planner_mutants_are_caught(emu, name, tmp_path):
     d.mkdir(parents=True)
     (tmp_path / "include").mkdir()
     shutil.copy(os.path.join(ROOT, "include", "qsim.h"), tmp_path / "include" / "qsim.h")
-    for f in ("planner.hpp", "kernels.hpp"):
+    for f in ("planner.hpp", "kernels.hpp", "perm_layout.hpp"):
         shutil.copy(os.path.join(ROOT, "paper_quant_ph_0608239_gb300", "csrc", f), d / f)
     (d / "planner.cpp").write_text(src.replace(old, new))
     emu_src = open(os.path.join(ROOT, "tests", "host", "plan_emu.cpp")).read().replace(
