@@ -45,6 +45,7 @@
 #include <cstdint>
 
 #include "df64.cuh"
+#include "fpair.cuh"
 
 namespace qsim {
 
@@ -105,6 +106,29 @@ DF_HD void dg_split_df(float h, float l, float scale, float (&d)[kDigits]) {
     d[5] = dg_step<5>(rh, rl);
 }
 
+// The same for the real and imaginary parts of an amplitude at once, in
+// packed FP32x2 operations (fpair.cuh: lane by lane the scalar roundings).
+template <int I>
+DF_HD fpair dg_step2(fpair &rh, fpair rl) {
+    constexpr float M = 12582912.0f / (float)(1ull << (7 + kDigitBits * I));
+    const fpair Mp = fp_splat(M);
+    const fpair s = fp_add(rh, rl);
+    const fpair d = fp_sub(fp_add(s, Mp), Mp);
+    if (I < kDigits - 1) rh = fp_sub(rh, d);
+    return d;
+}
+DF_HD void dg_split_df2(fpair h, fpair l, float scale, fpair (&d)[kDigits]) {
+    const fpair sc = fp_splat(scale);
+    fpair rh = fp_mul(h, sc);
+    const fpair rl = fp_mul(l, sc);
+    d[0] = dg_step2<0>(rh, rl);
+    d[1] = dg_step2<1>(rh, rl);
+    d[2] = dg_step2<2>(rh, rl);
+    d[3] = dg_step2<3>(rh, rl);
+    d[4] = dg_step2<4>(rh, rl);
+    d[5] = dg_step2<5>(rh, rl);
+}
+
 // The accumulators of level 3 (exact) and levels 4-5 folded into one FP32
 // value: the rounding is below 2^-24 of level 3, which is itself below 2^-27
 // of the result.
@@ -113,18 +137,46 @@ DF_HD float dg_fold_high(float a3, float a45) { return a3 + a45; }
 // Sum of the level accumulators (levels 0..2 exact, a3 = dg_fold_high of
 // levels 3 and 4-5) as a normalised double-float, times scale =
 // dg_scale_up(E).
+//
+// Dekker's fast two-sum (a + b = s + t, s = fl(a + b), t = b - (s - a)) is
+// error free whenever a and b can be written as M_a 2^e_a and M_b 2^e_b with
+// |M_a|, |M_b| < 2^24 and e_a >= e_b (Boldo and Daumas; Muller et al.,
+// Handbook of Floating-Point Arithmetic, Sec. 4.3.1), whatever the
+// magnitudes.  Here a0 is a multiple of 2^-14 with |a0| <= 2^4 (2^18 units),
+// a1 of 2^-23 below 2^1, a2 of 2^-32 below 2^-8: fl(a0 + a1) is a multiple of
+// 2^-23 and fl(of that + a2) one of 2^-32, so e_a >= -23 > -32 = e_b in the
+// second step and e_a >= -32 > e_b in the third (|a3| < 2^-16, so its
+// exponent is below -39).  The three heads are therefore exact; only the
+// two additions of the tails round, below 2^-47 of the result.
 DF_HD df dg_combine_df(float a0, float a1, float a2, float a3, float scale) {
-    // a0 is a multiple of 2^-14 with |a0| <= 16, a1 a multiple of 2^-23 with
-    // |a1| < 0.6: either |a0| >= |a1| or the sum is exact, so the quick
-    // two-sum is error free
     df s = quick_two_sum(a0, a1);
-    df t = two_sum(s.h, a2);
-    t.l += s.l;
-    s = quick_two_sum(t.h, t.l);
-    t = two_sum(s.h, a3);
-    t.l += s.l;
-    s = quick_two_sum(t.h, t.l);
+    df t = quick_two_sum(s.h, a2);
+    float l = s.l + t.l;
+    s = quick_two_sum(t.h, a3);
+    l += s.l;
+    s = quick_two_sum(s.h, l);
     return df{s.h * scale, s.l * scale};
+}
+
+// dg_combine_df for two outputs at once (packed FP32x2): heads in h, tails
+// in l.
+DF_HD void dg_combine_df2(fpair a0, fpair a1, fpair a2, fpair a3, float scale, fpair &h, fpair &l) {
+    auto fast_two_sum = [](fpair a, fpair b, fpair &t) {
+        const fpair s = fp_add(a, b);
+        t = fp_sub(b, fp_sub(s, a));
+        return s;
+    };
+    fpair l1, l2, l3;
+    fpair s = fast_two_sum(a0, a1, l1);
+    s = fast_two_sum(s, a2, l2);
+    fpair lt = fp_add(l1, l2);
+    s = fast_two_sum(s, a3, l3);
+    lt = fp_add(lt, l3);
+    fpair t;
+    s = fast_two_sum(s, lt, t);
+    const fpair sc = fp_splat(scale);
+    h = fp_mul(s, sc);
+    l = fp_mul(t, sc);
 }
 
 // bf16 bit pattern of a float that bf16 holds exactly (its top half).

@@ -40,10 +40,14 @@
 //      reals in two halves of 8, adds the levels in double-float and stores
 //      the amplitudes from registers to global memory.
 // The compute warps run tile i + 1's digits and tile i's combination around
-// tile i + 1's MMAs: once the second half of tile i's accumulators is read,
-// the next MMAs may start and the rest of the combination runs beside them.
+// the MMAs: the MMA warp commits each K step of a tile on its own mbarrier, so
+// the warps of a K quarter write the next tile's digits into their A slices
+// as soon as the current tile's MMAs of that K step are done; once all are
+// done and tile i's accumulators are read into registers (the first half
+// combined meanwhile), tile i + 1's MMAs start, and the rest of tile i's
+// combination, its stores and tile i + 2's fetch run beside them.
 // Hand-offs go through mbarriers (tile fetched, buffer read, A slices ready,
-// MMAs done), every wait bounded.
+// K step done), every wait bounded.
 // Tensor memory: accumulators at columns 0..319 (level L at 64 L), the A
 // slices at 320 + 48 s + 8 i (K step s, slice i): all 512 columns.
 #include <cstring>
@@ -60,7 +64,7 @@ namespace qsim {
 namespace {
 
 constexpr int kThreads128 = 512;            // compute threads: 16 warps
-constexpr int kThreadsAll128 = 640;         // + 4 duty warps (MMA issue, fetch issue, 2 idle), one per scheduler
+constexpr int kThreadsAll128 = 576;         // + the MMA-issue warp and the fetch-issue warp
 constexpr int kK = 5;                          // qubits of a block
 constexpr int kAmps = 1 << kK;                 // 32 amplitudes of a group
 constexpr int kReals = 2 * kAmps;              // 64: K and N of the product
@@ -100,6 +104,12 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t r0, uint32_t r
     asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0), "r"(r1) : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -134,8 +144,9 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
     unsigned char *s_buf0 = smem_raw + kBBytes;       // two input buffers
     // bar_ld: tile arrived in buffer b; bar_free: the compute warps have read
     // buffer b into registers; bar_ready: tile's A slices written and the last tile's
-    // accumulators read (MMAs may start); bar_mma: MMAs done; bar_b: B loaded
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mma, bar_b;
+    // accumulators read (MMAs may start); bar_mks[s]: the MMAs of K steps
+    // 0..s done (bar_mks[3]: all); bar_b: B loaded
+    __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mks[4], bar_b;
     __shared__ uint32_t tmem_base_s;
     __shared__ uint32_t s_max[2][4][128];  // per tile parity, K quarter, group: largest hi exponent field
     __shared__ int s_hb[kMaxH128];
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             mbar_init(&bar_free[b], kThreads128 / 32);
         }
         mbar_init(&bar_ready, kThreads128 / 32);
-        mbar_init(&bar_mma, 1);
+        for (int ks = 0; ks < 4; ks++) mbar_init(&bar_mks[ks], 1);
         mbar_init(&bar_b, 1);
         fence_mbar_init();
     }
@@ -207,8 +218,10 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                 for (int si = 0; si < kDigits; si++)  // level 5 into accumulator 4
                     umma_bf16_ts(tmem + 4u * kReals, at + 8u * si, bd + (uint64_t)((kDigits - 1 - si) * kSliceBytes / 16),
                                  idesc_bf16(128, kReals), 1u);
+                // K step ks read its A slices: the compute warps of that K
+                // quarter may write the next tile's
+                umma_commit(&bar_mks[ks]);
             }
-            umma_commit(&bar_mma);
         };
 
         uint32_t issued = 0;
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             issued++;
         }
         // the last products have finished before the CTA may free tensor memory
-        if (issued) mbar_wait_bounded(&bar_mma, (issued - 1u) & 1u, kWaitBudget128);
+        if (issued) mbar_wait_bounded(&bar_mks[3], (issued - 1u) & 1u, kWaitBudget128);
         if (!ok) atomicExch(err, kErrTimeout);
     } else if (warp == kThreads128 / 32 + 1) {
         // ---- fetch warp: tile k into buffer k & 1 once tile k - 2 left it
@@ -303,23 +316,25 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
             return true;
         };
-        auto digits = [&]() {
+        // split(): the six slices of the held amplitudes as packed bf16
+        // words (slice d, amplitude j: re and im digit), held in registers
+        // until the A slices are free; put(): into the A slices (lane m,
+        // K quarter qq), 8 columns per slice.
+        uint32_t wd[kDigits][8];
+        auto split = [&]() {
             const float sd = dg_scale_down(Eg_next);
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                uint32_t w[kDigits][2];
+            for (int j = 0; j < 8; j++) {  // re and im together (packed FP32x2)
+                fpair dd[kDigits];
+                dg_split_df2(fpair{__uint_as_float(v[j].x), __uint_as_float(v[j].z)},
+                             fpair{__uint_as_float(v[j].y), __uint_as_float(v[j].w)}, sd, dd);
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const uint4 x = v[2 * h + j];
-                    float dr[kDigits], di[kDigits];
-                    dg_split_df(__uint_as_float(x.x), __uint_as_float(x.y), sd, dr);
-                    dg_split_df(__uint_as_float(x.z), __uint_as_float(x.w), sd, di);
-#pragma unroll
-                    for (int d = 0; d < kDigits; d++) w[d][j] = dg_pack(dr[d], di[d]);
-                }
-#pragma unroll
-                for (int d = 0; d < kDigits; d++) tmem_st2(acol + 8u * d + 2u * h, w[d][0], w[d][1]);
+                for (int d = 0; d < kDigits; d++) wd[d][j] = dg_pack(dd[d].x, dd[d].y);
             }
+        };
+        auto put = [&]() {
+#pragma unroll
+            for (int d = 0; d < kDigits; d++) tmem_st8(acol + 8u * d, wd[d]);
         };
         // tile t's A slices are written (and tile t - 1's accumulators read):
         // one arrival per warp on bar_ready
@@ -329,41 +344,39 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             if (lane == 0) mbar_arrive(&bar_ready);
         };
 
-        // prologue: tile 0 into tensor memory (its MMAs start), tile 1 fetched
-        uint32_t Eg = 0;  // exponent fields of the tile whose MMAs run
+        // prologue: tile 0 into tensor memory (its MMAs start), tile 1
+        // fetched and split
+        uint32_t Ecur = 0, Enext = 0;  // exponent fields of the tile whose MMAs run and of the next
         if (!aborted && count > 0) {
             aborted = !fetch(0);
             if (!aborted) {
-                digits();
+                split();
+                put();
                 tmem_st_wait();
                 arrive_ready();
-                Eg = Eg_next;
-                if (count > 1) aborted = !fetch(1);
+                Ecur = Eg_next;
+                if (count > 1) {
+                    aborted = !fetch(1);
+                    if (!aborted) {
+                        split();
+                        Enext = Eg_next;
+                    }
+                }
             }
         }
-        // steady state, the MMAs of tile i in flight and tile i + 1 fetched:
-        // once the MMAs are done, tile i + 1's digits go into the A slices and
-        // tile i's accumulators are read out; tile i + 1's MMAs start; tile i
-        // is combined and stored and tile i + 2 fetched while they run
-        for (uint32_t i = 0; i < count && !aborted; i++) {
-            const bool next = i + 1 < count;
-            if (compute_any(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget128))) {
-                aborted = true;
-                break;
-            }
+        // finish(i, next, bad): once tile i's MMAs are all done, its
+        // accumulators are read out (then tile i + 1's MMAs may start, if
+        // next), combined and stored; false if a wait gave up here or in a
+        // warp (bad).
+        auto finish = [&](uint32_t i, bool next, bool bad) -> bool {
+            if (compute_any(bad || !mbar_wait_bounded(&bar_mks[3], i & 1u, kWaitBudget128))) return false;
             tc_fence_after();
-            const uint32_t Eg_i = Eg;  // tile i's exponent field
-            if (next) {
-                digits();
-                Eg = Eg_next;
-            }
-            // Tile i's accumulators in two halves of 8 output reals (4
-            // amplitudes): levels 3 and 4-5 folded into one on arrival
-            // (rounding below 2^-50 of the result), then levels 0, 1, 2.
-            // Once the second half is in registers (and the digits above are
-            // written), tile i + 1's MMAs may start; its combination runs
-            // while they do.
-            const float su = dg_scale_up(Eg_i);
+            // Tile i's accumulators, 16 output reals (8 amplitudes) in two
+            // halves: levels 3 and 4-5 folded into one on arrival (rounding
+            // below 2^-50 of the result), then levels 0, 1, 2.  The first
+            // half is combined before the second is read; once both are in
+            // registers, tile i + 1's MMAs may start.
+            const float su = dg_scale_up(Ecur);
             double2 *gt = a + tile_base(blockIdx.x + (uint64_t)i * stride);
             uint32_t acc[kDigitLevels - 1][8];
             auto drain = [&](int hf) {
@@ -376,21 +389,33 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                 tmem_ld8(c0 + kReals * 2, acc[2]);
                 tmem_ld_wait();
 #pragma unroll
-                for (int c = 0; c < 8; c++)
-                    acc[3][c] = __float_as_uint(dg_fold_high(__uint_as_float(acc[3][c]), __uint_as_float(a4[c])));
+                for (int c = 0; c < 8; c += 2) {
+                    const fpair f = fp_add(fpair{__uint_as_float(acc[3][c]), __uint_as_float(acc[3][c + 1])},
+                                           fpair{__uint_as_float(a4[c]), __uint_as_float(a4[c + 1])});
+                    acc[3][c] = __float_as_uint(f.x);
+                    acc[3][c + 1] = __float_as_uint(f.y);
+                }
             };
-            // the combination of one half: output amplitudes 8 qq + 4 hf + jj,
-            // straight from registers to global memory
-            auto combine = [&](int hf) {
+            // the 8 output reals of the half in acc as double-floats, the re
+            // and im parts of an amplitude together (packed FP32x2)
+            auto combine = [&](df (&o)[8]) {
+                auto pr = [&](int L, int c) {
+                    return fpair{__uint_as_float(acc[L][c]), __uint_as_float(acc[L][c + 1])};
+                };
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    fpair h, l;
+                    dg_combine_df2(pr(0, c), pr(1, c), pr(2, c), pr(3, c), su, h, l);
+                    o[c] = df{h.x, l.x};
+                    o[c + 1] = df{h.y, l.y};
+                }
+            };
+            // output amplitudes 8 qq + 4 hf + jj, from registers to global memory
+            auto store = [&](int hf, const df (&o)[8]) {
 #pragma unroll
                 for (int jj = 0; jj < 4; jj++) {
                     const int j = 4 * hf + jj;
-                    const df re = dg_combine_df(__uint_as_float(acc[0][2 * jj]), __uint_as_float(acc[1][2 * jj]),
-                                                __uint_as_float(acc[2][2 * jj]), __uint_as_float(acc[3][2 * jj]), su);
-                    const df im = dg_combine_df(__uint_as_float(acc[0][2 * jj + 1]),
-                                                __uint_as_float(acc[1][2 * jj + 1]),
-                                                __uint_as_float(acc[2][2 * jj + 1]),
-                                                __uint_as_float(acc[3][2 * jj + 1]), su);
+                    const df re = o[2 * jj], im = o[2 * jj + 1];
                     const uint64_t go =
                         gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
                     if (OUT_IEEE) {
@@ -400,14 +425,48 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                     }
                 }
             };
+            df o0[8], o1[8];
             drain(0);
-            combine(0);
+            combine(o0);
             drain(1);
             tmem_st_wait();
-            if (next) arrive_ready();
-            combine(1);
-            if (i + 2 < count && !fetch(i + 2)) aborted = true;
+            if (next) arrive_ready();  // tile i + 1's digits written, tile i's accumulators read
+            store(0, o0);
+            combine(o1);
+            store(1, o1);
+            return true;
+        };
+        // steady state, the MMAs of tile i in flight and tile i + 1 split in
+        // registers: as soon as K step qq of tile i's MMAs is done, the warps
+        // of K quarter qq put tile i + 1's digits into its A slices; once all
+        // MMAs are done, tile i's accumulators are read out and tile i + 1's
+        // MMAs may start; tile i is combined and stored, and tile i + 2
+        // fetched and split, while they run.  (The loop always ends with a
+        // split and always starts with a put, so the digit words are not
+        // held across the combination; a split without a fetch splits zeros.)
+        uint32_t i = 0;
+        for (; i + 1 < count && !aborted; i++) {
+            const bool bad = !__all_sync(0xffffffffu, mbar_wait_bounded(&bar_mks[qq], i & 1u, kWaitBudget128));
+            tc_fence_after();
+            put();
+            if (!finish(i, true, bad)) {
+                aborted = true;
+                break;
+            }
+            Ecur = Enext;
+            if (i + 2 < count) {
+                if (!fetch(i + 2)) {
+                    aborted = true;
+                    break;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; j++) v[j] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            split();
+            Enext = Eg_next;
         }
+        if (!aborted && count > 0 && !finish(count - 1, false, false)) aborted = true;
         if (aborted && tid == 0) atomicExch(err, kErrTimeout);
     }
     tc_fence_before();

@@ -15,7 +15,13 @@ product of the original doubles in long double:
     sums of |products| stay below 2^24), for random and adversarial inputs;
   * the combined result is within 2^-43 of max|x| * ||u_row||_1 of the exact
     dot product (the dropped levels and the fixed-point truncation), and the
-    typical error is near 2^-48 of the output's magnitude scale.
+    typical error is near 2^-48 of the output's magnitude scale;
+  * the combination alone, for accumulators anywhere on their grids within
+    their bounds (cancelling ones too), is within 2^-46 of the largest of
+    them from their exact sum, as a normalised double-float;
+  * the packed (FP32x2) split and combination give the scalar results lane
+    by lane (on the CPU both are scalar code: this pins the order of the
+    operations; the GPU parity tests pin the packed instructions).
 """
 import os
 import subprocess
@@ -91,7 +97,7 @@ static void group(std::vector<double> &x, int kind) {
 }
 
 int main() {
-    int bad_exact = 0, bad_slice = 0, bad_bound = 0, bad_err = 0;
+    int bad_exact = 0, bad_slice = 0, bad_bound = 0, bad_err = 0, bad_pair = 0;
     double worst = 0.0, sum_typ = 0.0;
     long cnt = 0;
     std::vector<double> B, x;
@@ -112,6 +118,15 @@ int main() {
         for (int k = 0; k < 64; k++) {
             float d[kDigits];
             dg_split_df(v[k].h, v[k].l, sd, d);
+            {  // the packed split of (this value, the next one) against the scalar one
+                const int k2 = (k + 1) % 64;
+                fpair dp[kDigits];
+                float d2[kDigits];
+                dg_split_df2(fpair{v[k].h, v[k2].h}, fpair{v[k].l, v[k2].l}, sd, dp);
+                dg_split_df(v[k2].h, v[k2].l, sd, d2);
+                for (int i = 0; i < kDigits; i++)
+                    if (dp[i].x != d[i] || dp[i].y != d2[i]) bad_pair++;
+            }
             LD sum = 0;
             for (int i = 0; i < kDigits; i++) {
                 A[i][k] = d[i];
@@ -179,7 +194,39 @@ int main() {
             if (e > std::ldexp(1.0, -43)) bad_err++;
         }
     }
-    std::printf("%d %d %d %d %.3e %.3e\n", bad_exact, bad_slice, bad_bound, bad_err, worst, sum_typ / cnt);
+    // the combination alone: accumulators anywhere on their grids within their
+    // bounds (cancellations included), against the exact sum in long double
+    int bad_comb = 0;  // (bad_pair: the packed forms differ from the scalar ones)
+    std::uniform_int_distribution<int64_t> I0(-(1ll << 18), 1ll << 18), I1(-(1ll << 23), 1ll << 23),
+        I2(-(3ll << 22), 3ll << 22), I3(-(1ll << 24) + 1, (1ll << 24) - 1);
+    for (int trial = 0; trial < 2000000; trial++) {
+        int64_t m0 = I0(g), m1 = I1(g), m2 = I2(g), m3 = I3(g);
+        const int shape = trial % 8;
+        if (shape == 1) m1 = -m0 * 512 + (m1 >> 12);  // a1 cancels a0 to a few units
+        if (shape == 2) { m0 = 0; m1 = 0; }
+        if (shape == 3) { m0 = 0; m1 >>= 16; m2 = -m1 * 512 + (m2 >> 14); }
+        if (shape == 4) { m1 = -m0 * 512; m2 = 0; }
+        if (m1 > (1ll << 23)) m1 = 1ll << 23;
+        if (m1 < -(1ll << 23)) m1 = -(1ll << 23);
+        if (m2 > (3ll << 22)) m2 = 3ll << 22;
+        if (m2 < -(3ll << 22)) m2 = -(3ll << 22);
+        const float a0 = std::ldexp((float)m0, -14), a1 = std::ldexp((float)m1, -23), a2 = std::ldexp((float)m2, -32);
+        // a3: level 3 folded with a small rounded level 4-5 term
+        const float a3 = (float)(std::ldexp((double)m3, -41) + std::ldexp(N01(g), -50));
+        const df r = dg_combine_df(a0, a1, a2, a3, 1.0f);
+        {  // the packed form, with the lanes swapped in the second output
+            fpair h, l;
+            dg_combine_df2(fpair{a0, a1}, fpair{a1, a0}, fpair{a2, a2}, fpair{a3, a3}, 1.0f, h, l);
+            const df r2 = dg_combine_df(a1, a0, a2, a3, 1.0f);
+            if (h.x != r.h || l.x != r.l || h.y != r2.h || l.y != r2.l) bad_pair++;
+        }
+        const LD exact = (LD)a0 + (LD)a1 + (LD)a2 + (LD)a3;
+        const LD mag = std::max(std::max(std::fabs((LD)a0), std::fabs((LD)a1)), std::max(std::fabs((LD)a2), std::fabs((LD)a3)));
+        if (std::fabs((LD)r.h + (LD)r.l - exact) > mag * std::ldexp((LD)1, -46)) bad_comb++;
+        if (std::fabs((LD)r.l) > std::fabs((LD)r.h) * std::ldexp((LD)1, -24)) bad_comb++;
+    }
+    std::printf("%d %d %d %d %.3e %.3e %d %d\n", bad_exact, bad_slice, bad_bound, bad_err, worst, sum_typ / cnt, bad_comb,
+                bad_pair);
     return 0;
 }
 '''
@@ -196,6 +243,8 @@ def test_digit_slices_exact_levels_and_combination():
         out = subprocess.check_output([exe], timeout=600).decode().split()
     bad_exact, bad_slice, bad_bound, bad_err = (int(v) for v in out[:4])
     worst, mean = float(out[4]), float(out[5])
+    assert int(out[6]) == 0, out  # the combination alone
+    assert int(out[7]) == 0, out  # packed FP32x2 forms = scalar forms
     print("worst %.3e (2^%.1f), mean %.3e (2^%.1f)" % (worst, __import__("math").log2(worst or 1e-300),
                                                         mean, __import__("math").log2(mean or 1e-300)))
     assert bad_slice == 0, out
