@@ -28,15 +28,18 @@
 //   4. the MMA warp issues 6 products x 8 K steps = 48 MMAs (N = 128);
 //   5. the thread reads its 32 output reals from the accumulator and stores
 //      them from registers to global memory.
-// Tile i + 1's slices are written once tile i's MMAs are done; tile i's
-// accumulator is read before tile i + 1's MMAs start and stored while they
-// run.  Hand-offs go through mbarriers, every wait bounded.
-// Tensor memory: the accumulator at columns 0..127, the A slices at
-// 128 + 8 (3 ks + s) (K step ks, slice s = hi, mid, lo).
+// The A slices are double-buffered in tensor memory: tile i + 2's slices
+// are written while tile i + 1's MMAs run, so the MMAs of consecutive tiles
+// are separated only by the read-out of the accumulator.  Hand-offs go
+// through mbarriers, every wait bounded.
+// Tensor memory: the accumulator at columns 0..127, the A slices of tile t
+// at 128 + 192 (t & 1) + 8 (3 ks + s) (K step ks, slice s = hi, mid, lo).
+// All 512 columns.
 #include <cstring>
 #include <cmath>
 
 #include "common.cuh"
+#include "fpair.cuh"
 #include "kernels.hpp"
 #include "ptx.cuh"
 #include "tcgen05.cuh"
@@ -53,6 +56,7 @@ constexpr uint32_t kTileBytes6 = 8u << kTileBits6;            // 64 KiB
 constexpr uint32_t kSliceBytes6 = kReals6 * kReals6 * 2;      // 32 KiB per B slice
 constexpr uint32_t kBBytes6 = 3 * kSliceBytes6;               // 96 KiB
 constexpr uint32_t kAcc6 = kReals6;                           // accumulator columns
+constexpr uint32_t kABuf6 = 8u * 3u * 8u;                     // A slice columns of one tile (192)
 constexpr uint32_t kTmemCols6 = 512;
 constexpr int kCompute6 = 512;
 constexpr int kThreads6 = 640;
@@ -124,15 +128,27 @@ __host__ __device__ __forceinline__ float bf16_rn(float x) {
 #endif
 }
 
-// the three bf16 slices of a pair of reals (re, im) packed as K-adjacent words
+// two floats rounded to bf16 (nearest, ties to even) in one word: lo in
+// bits 0..15, hi in 16..31 (the order of K-adjacent operand elements)
+__device__ __forceinline__ uint32_t pack_bf16_rn(float lo, float hi) {
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+    return w;
+}
+__device__ __forceinline__ fpair unpack_bf16(uint32_t w) {
+    return fpair{__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u)};
+}
+
+// the three bf16 slices of a pair of reals (re, im) packed as K-adjacent
+// words: each slice the bf16 rounding of the remainder (the remainders are
+// exact), re and im together
 __device__ __forceinline__ void split3(float re, float im, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
-    const float rh = bf16_rn(re), ih = bf16_rn(im);
-    const float rr = re - rh, ir = im - ih;  // exact
-    const float rm = bf16_rn(rr), im_ = bf16_rn(ir);
-    const float rl = bf16_rn(rr - rm), il = bf16_rn(ir - im_);
-    w0 = __byte_perm(__float_as_uint(rh), __float_as_uint(ih), 0x7632);
-    w1 = __byte_perm(__float_as_uint(rm), __float_as_uint(im_), 0x7632);
-    w2 = __byte_perm(__float_as_uint(rl), __float_as_uint(il), 0x7632);
+    fpair x{re, im};
+    w0 = pack_bf16_rn(x.x, x.y);
+    x = fp_sub(x, unpack_bf16(w0));
+    w1 = pack_bf16_rn(x.x, x.y);
+    x = fp_sub(x, unpack_bf16(w1));
+    w2 = pack_bf16_rn(x.x, x.y);
 }
 
 __global__ void __launch_bounds__(kThreads6, 1)
@@ -142,8 +158,9 @@ __global__ void __launch_bounds__(kThreads6, 1)
     unsigned char *s_b = smem_raw;                   // B slices hi, mid, lo
     unsigned char *s_buf0 = smem_raw + kBBytes6;     // two input buffers
     // bar_ld: tile arrived in buffer b; bar_free: the compute warps have read
-    // buffer b into registers; bar_ready: A slices written and the last
-    // accumulator read (MMAs may start); bar_mma: MMAs done; bar_b: B loaded
+    // buffer b into registers; bar_ready: the tile's A slices written and the
+    // last tile's accumulator read (its MMAs may start); bar_mma: MMAs done;
+    // bar_b: B loaded
     __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mma, bar_b;
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_hb[kMaxH6];
@@ -198,11 +215,12 @@ __global__ void __launch_bounds__(kThreads6, 1)
             ok = mbar_wait_bounded(&bar_ready, t & 1u, kWaitBudget6);
             if (!ok) break;
             tc_fence_after();
+            const uint32_t abuf = tmem + kAcc6 + kABuf6 * (t & 1u);
 #pragma unroll
             for (int ks = 0; ks < 8; ks++)
 #pragma unroll
                 for (int p = 0; p < 6; p++)
-                    mma6(tmem, tmem + kAcc6 + 8u * (3 * ks + PA[p]),
+                    mma6(tmem, abuf + 8u * (3 * ks + PA[p]),
                          bdesc0 + (uint64_t)((PB[p] * kSliceBytes6 + ks * 256) / 16), (ks | p) ? 1u : 0u);
             umma_commit(&bar_mma);
             issued++;
@@ -257,14 +275,16 @@ __global__ void __launch_bounds__(kThreads6, 1)
             return qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u) |
                    ((j & 8) ? wc[3] : 0u);
         };
-        const uint32_t acol = tmem + lane_off + kAcc6;  // A slices of this lane
+        const uint32_t acol = tmem + lane_off + kAcc6;  // A slices of this lane (buffer 0)
 
         bool aborted = vote6(!mbar_wait_bounded(&bar_b, 0, kWaitBudget6));
         float2 v[16];
-        // fetch(i): this thread's 16 amplitudes of tile i into registers
+        // fetch(i): this thread's 16 amplitudes of tile i into registers;
+        // false (for the whole warp) if the copy did not arrive in time --
+        // the caller folds that into the next block-wide vote
         auto fetch = [&](uint32_t i) -> bool {
             const int b = (int)(i & 1u);
-            if (vote6(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget6))) return false;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget6));
             const uint32_t sbuf = smem_u32(buf(b));
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
@@ -278,17 +298,17 @@ __global__ void __launch_bounds__(kThreads6, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_free[b]);  // this warp's share of the buffer is read
-            return true;
+            return ok;
         };
-        // slices(): the three bf16 slices of the held amplitudes into tensor
-        // memory, K steps 2 qq and 2 qq + 1
-        auto slices = [&]() {
+        // slices(t): the three bf16 slices of the held amplitudes (tile t)
+        // into tile t's A buffer, K steps 2 qq and 2 qq + 1
+        auto slices = [&](uint32_t t) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 uint32_t w[3][8];
 #pragma unroll
                 for (int j = 0; j < 8; j++) split3(v[8 * h + j].x, v[8 * h + j].y, w[0][j], w[1][j], w[2][j]);
-                const uint32_t kcol = acol + 8u * 3u * (uint32_t)(2 * qq + h);
+                const uint32_t kcol = acol + kABuf6 * (t & 1u) + 8u * 3u * (uint32_t)(2 * qq + h);
 #pragma unroll
                 for (int s = 0; s < 3; s++) tst8(kcol + 8u * s, w[s]);
             }
@@ -299,23 +319,32 @@ __global__ void __launch_bounds__(kThreads6, 1)
             if (lane == 0) mbar_arrive(&bar_ready);
         };
 
+        // prologue: tile 0's slices (its MMAs start), tile 1's slices into
+        // the other buffer
         if (!aborted && count > 0) {
-            aborted = !fetch(0);
+            aborted = vote6(!fetch(0));
             if (!aborted) {
-                slices();
+                slices(0);
                 tmem_st_wait();
                 arrive_ready();
-                if (count > 1) aborted = !fetch(1);
+                if (count > 1) {
+                    aborted = vote6(!fetch(1));
+                    if (!aborted) slices(1);
+                }
             }
         }
+        bool bad = false;  // a fetch of this warp gave up (voted on with the next wait)
+        // steady state, tile i's MMAs in flight and tile i + 1's slices in
+        // place: once the MMAs are done, the accumulator is read out and tile
+        // i + 1's MMAs may start; tile i is stored and tile i + 2 fetched and
+        // split into the A buffer tile i's MMAs used, while they run
         for (uint32_t i = 0; i < count && !aborted; i++) {
             const bool next = i + 1 < count;
-            if (vote6(!mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget6))) {
+            if (vote6(bad || !mbar_wait_bounded(&bar_mma, i & 1u, kWaitBudget6))) {
                 aborted = true;
                 break;
             }
             tc_fence_after();
-            if (next) slices();
             // tile i's 32 output reals of this thread: columns 32 qq .. 32 qq + 31
             uint32_t acc[2][16];
             tld16(tmem + lane_off + (uint32_t)(32 * qq), acc[0]);
@@ -331,7 +360,11 @@ __global__ void __launch_bounds__(kThreads6, 1)
                 gt[go] = make_float2(__uint_as_float(acc[j >> 3][(2 * j) & 15]),
                                      __uint_as_float(acc[j >> 3][(2 * j + 1) & 15]));
             }
-            if (i + 2 < count && !fetch(i + 2)) aborted = true;
+            if (i + 2 < count) {
+                bad = !fetch(i + 2);
+                tc_fence_after();
+                slices(i + 2);
+            }
         }
         if (aborted && tid == 0) atomicExch(err, kErrTimeout);
     }
