@@ -583,7 +583,8 @@ def _event_runs(fn, reps):
 def _timed_circuit(q, n, dt, gates, x0, reps, **plan_kw):
     """A planned circuit timed as a bench step (set the basis state, run the
     plan, read <Q_q>): tuning runs and one warm-up untimed, then reps runs,
-    each bracketed by CUDA events; median ms, gates/s and the plan's path."""
+    each bracketed by CUDA events; median ms, gates/s, the plan's path and its
+    algorithmic bytes per run as a fraction of the measured HBM copy rate."""
     import torch
     st = q.State(n, dt)
     plan = st.plan(gates, **plan_kw)
@@ -599,7 +600,9 @@ def _timed_circuit(q, n, dt, gates, x0, reps, **plan_kw):
     pst = plan.stats()
     out = {"gates_per_s": len(gates) / (ms / 1e3), "ms_per_run": ms, "runs": reps,
            "path": path_label(dt, pst, plan_kw.get("mode") == q.MODE_PERGATE),
-           "passes": pst["passes"] if pst["mode"] != q.MODE_PERGATE else pst["sweeps"]}
+           "passes": pst["passes"] if pst["mode"] != q.MODE_PERGATE else pst["sweeps"],
+           # the plan's algorithmic bytes per run over the measured copy rate
+           "hbm_frac": pst["alg_bytes"] / (ms / 1e3) / 1e9 / peaks()[0]}
     plan.free()
     st.free()
     del st
@@ -624,18 +627,22 @@ def config_lines(q, main, args):
     g = inputs.random_circuit(30, 40, 2)
     x = inputs.random_basis(30, 2)
     c2 = {"c128_autotuned": main,
+          "c64_autotuned": _timed_circuit(q, 30, "c64", g, x, reps, mode=q.MODE_AUTO),
           "c64_tile_passes": _timed_circuit(q, 30, "c64", g, x, reps, tile_bits=12),
           "c64_tensor_cores_k5": _timed_circuit(q, 30, "c64", g, x, reps, fuse_k=5),
           "c64_tensor_cores_k6": _timed_circuit(q, 30, "c64", g, x, reps, fuse_k=6),
           "c128_tensor_cores_k5": _timed_circuit(q, 30, "c128", g, x, reps, fuse_k=5),
           "c128_tile_passes": _timed_circuit(q, 30, "c128", g, x, 2, tile_bits=12),
           "c128_pergate": _timed_circuit(q, 30, "c128", g, x, 2, mode=q.MODE_PERGATE)}
-    c2["fused_c64_over_pergate_c128"] = c2["c128_pergate"]["ms_per_run"] / c2["c64_tensor_cores_k5"]["ms_per_run"]
+    # fused FP32 (the fastest complex64 fused path) over one FP64 sweep per gate
+    fused64 = min(c2["c64_tensor_cores_k5"]["ms_per_run"], c2["c64_tensor_cores_k6"]["ms_per_run"])
+    c2["fused_c64_over_pergate_c128"] = c2["c128_pergate"]["ms_per_run"] / fused64
     res["random30"] = c2
     # adder of two 15-qubit registers (complex64): first seeded pair, output index checked
     a, b = inputs.adder_pairs(15, 8, seed=3)[0]
     g = inputs.adder_circuit([a, b], 15)
-    ad = {"tile_passes": _timed_circuit(q, 30, "c64", g, 0, reps),
+    ad = {"autotuned": _timed_circuit(q, 30, "c64", g, 0, reps, mode=q.MODE_AUTO),
+          "tile_passes": _timed_circuit(q, 30, "c64", g, 0, reps),
           "tensor_cores_k5": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=5),
           "tensor_cores_k6": _timed_circuit(q, 30, "c64", g, 0, reps, fuse_k=6)}
     st = q.State(30, "c64")
