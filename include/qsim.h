@@ -323,16 +323,23 @@ typedef struct {
 } qsim_circuit;
 
 /* qsim_run_batch: run nc independent circuits (complex64 states of up to 24
- * qubits, on one device) in one persistent launch on the stream of
- * cs[0].state; every state is set to its |x0> and its gates applied.  Waits
- * for completion.  ETIMEOUT if a device-side wait between passes expired (the
- * states are then undefined).  Equivalent to qsim_batch_create + one
- * qsim_batch_run + qsim_batch_free. */
+ * qubits, on one device) on the stream of cs[0].state; every state is set to
+ * its |x0> (in the identity qubit layout) and its gates applied.  Circuits of
+ * fewer than 20 qubits run as tile passes in one persistent launch; circuits
+ * of 20 qubits or more, which carry nearly all the bytes of a mixed batch,
+ * run after it as dense blocks on the tensor cores (6 qubits, or opts->fuse_k
+ * = 4 or 5; opts->fuse_k = -1 keeps them in the persistent launch, as does a
+ * gate wider than the block).  Waits for completion.  ETIMEOUT if a
+ * device-side wait expired (the states are then undefined); opts->
+ * wait_budget_us bounds the waits between passes of the persistent launch.
+ * Equivalent to qsim_batch_create + one qsim_batch_run + qsim_batch_free,
+ * without the graph capture (its launches are enqueued directly). */
 QSIM_API qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts);
 
-/* A planned batch: the circuits' tile programs and the ordered work list are
- * uploaded once and the launch is captured in a CUDA graph, so every
- * qsim_batch_run is one graph launch.  The circuits' states must stay alive. */
+/* A planned batch: the circuits' tile programs, the ordered work list and the
+ * dense blocks are uploaded once and the runs' launches are captured in a
+ * CUDA graph, so every qsim_batch_run is one graph launch.  The circuits'
+ * states must stay alive. */
 typedef struct qsim_batch_s *qsim_batch;
 
 typedef struct {
@@ -341,9 +348,11 @@ typedef struct {
     int64_t passes;      /* tile passes over all circuits */
     int64_t items;       /* (circuit, pass, tile) work items of one run */
     int32_t graph;       /* 1 if runs replay a captured CUDA graph */
-    int32_t reserved;
-    double alg_bytes;    /* algorithmic bytes of one run: each pass reads and writes its state once */
+    int32_t fused;       /* circuits on the tensor-core lane (dense blocks) */
+    double alg_bytes;    /* algorithmic bytes of one run: each pass or block reads and writes its state once */
     double alg_flops;    /* algorithmic real flops of one run (same count as the plan statistics) */
+    int64_t blocks;      /* dense blocks of the tensor-core lane */
+    int64_t kernels;     /* kernel launches of one run */
 } qsim_batch_stats;
 
 QSIM_API qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out);

@@ -270,10 +270,13 @@ def _circuit_array(states, x0s, gate_lists):
     return arr, keep
 
 
-def run_batch(states, x0s, gate_lists, wait_budget_us=0):
-    """Run independent circuits (complex64 states) in one persistent launch."""
+def run_batch(states, x0s, gate_lists, wait_budget_us=0, fuse_k=0):
+    """Run independent circuits (complex64 states): one persistent launch,
+    and circuits of 20 qubits or more as dense blocks on the tensor cores
+    (6-qubit blocks, or fuse_k; fuse_k=-1 keeps them in the persistent
+    launch)."""
     arr, keep = _circuit_array(states, x0s, gate_lists)
-    o = opts()
+    o = opts(fuse_k=fuse_k)
     o.wait_budget_us = int(wait_budget_us)
     _capi.call("qsim_run_batch", arr, len(states), ctypes.byref(o))
 
@@ -281,9 +284,9 @@ def run_batch(states, x0s, gate_lists, wait_budget_us=0):
 class Batch:
     """A planned batch (qsim_batch_create): every run() is one graph launch."""
 
-    def __init__(self, states, x0s, gate_lists, wait_budget_us=0):
+    def __init__(self, states, x0s, gate_lists, wait_budget_us=0, fuse_k=0):
         arr, keep = _circuit_array(states, x0s, gate_lists)
-        o = opts()
+        o = opts(fuse_k=fuse_k)
         o.wait_budget_us = int(wait_budget_us)
         p = ctypes.c_void_p()
         _capi.call("qsim_batch_create", arr, len(states), ctypes.byref(o), ctypes.byref(p))
@@ -300,7 +303,8 @@ class Batch:
         s = _capi.QsimBatchStats()
         _capi.call("qsim_batch_get_stats", self.ptr, ctypes.byref(s))
         return {"circuits": s.circuits, "gates": s.gates, "passes": s.passes, "items": s.items,
-                "graph": bool(s.graph), "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
+                "graph": bool(s.graph), "fused": s.fused, "blocks": s.blocks, "kernels": s.kernels,
+                "alg_bytes": s.alg_bytes, "alg_flops": s.alg_flops}
 
     def free(self):
         if self.ptr is not None and self.ptr.value:

@@ -35,8 +35,9 @@ class QsimOpts(ctypes.Structure):
 
 class QsimBatchStats(ctypes.Structure):
     _fields_ = [("circuits", ctypes.c_int64), ("gates", ctypes.c_int64), ("passes", ctypes.c_int64),
-                ("items", ctypes.c_int64), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
+                ("items", ctypes.c_int64), ("graph", ctypes.c_int32), ("fused", ctypes.c_int32),
+                ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double), ("blocks", ctypes.c_int64),
+                ("kernels", ctypes.c_int64)]
 
 
 class QsimCircuit(ctypes.Structure):

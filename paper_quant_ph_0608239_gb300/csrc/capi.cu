@@ -8,6 +8,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <thread>
+#include <atomic>
 
 #include <cuda_runtime.h>
 
@@ -756,12 +758,26 @@ static void plan_release(qsim_plan_s *P) {
     delete P;
 }
 
+// The device copies of a built plan's tables (tile program, block
+// matrices) and its final statistics; P is released on failure.
+static qsim_status upload_plan(qsim_state *h, qsim_plan_s *P, qsim_plan_s *&out);
+
 static qsim_status create_one(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
                               qsim_plan_s *&out) {
     out = nullptr;
     qsim_plan_s *P = new qsim_plan_s;
-    qsim_status st = build_plan(h, gates, ng, opts, *P);
-    if (st == QSIM_OK && !P->plan.ops.empty()) {
+    const qsim_status st = build_plan(h, gates, ng, opts, *P);
+    if (st != QSIM_OK) {
+        plan_release(P);
+        return st;
+    }
+    return upload_plan(h, P, out);
+}
+
+static qsim_status upload_plan(qsim_state *h, qsim_plan_s *P, qsim_plan_s *&out) {
+    out = nullptr;
+    qsim_status st = QSIM_OK;
+    if (!P->plan.ops.empty()) {
         cudaError_t e = cudaMalloc(&P->d_ops, P->plan.ops.size() * sizeof(TileOp));
         if (e == cudaSuccess)
             e = cudaMemcpy(P->d_ops, P->plan.ops.data(), P->plan.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice);
@@ -1378,10 +1394,21 @@ struct qsim_batch_s {
     cudaGraphExec_t exec = nullptr;
     uint32_t *h_err = nullptr;       // pinned
     qsim_batch_stats stats{};
+    // circuits run as dense blocks on the tensor cores after the persistent
+    // launch: their state, basis index and plan
+    std::vector<qsim_handle> fused_states;
+    std::vector<uint64_t> fused_x0;
+    std::vector<qsim_plan_s *> fused_plans;
 };
+
+// Circuits of at least this many qubits take the tensor-core lane of a batch
+// (they carry almost all of a mixed batch's bytes; below it a block's launch
+// costs more than its pass).
+constexpr int kBatchFusedMinQubits = 20;
 
 static void batch_release(qsim_batch_s *b) {
     if (!b) return;
+    for (qsim_plan_s *P : b->fused_plans) plan_release(P);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->dbuf) cudaFree(b->dbuf);
@@ -1393,11 +1420,36 @@ static void batch_release(qsim_batch_s *b) {
 static cudaError_t batch_enqueue(qsim_batch_s *b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->zero_bytes, s);
     if (e != cudaSuccess) return e;
-    return launch_batch(b->d_circs, b->d_passes, b->d_ops, b->d_phases, b->d_items, b->nitems, b->d_counters,
-                        b->d_counters + 2, b->d_err, b->budget, b->sm_count, s);
+    if (b->nitems) {
+        e = launch_batch(b->d_circs, b->d_passes, b->d_ops, b->d_phases, b->d_items, b->nitems, b->d_counters,
+                         b->d_counters + 2, b->d_err, b->budget, b->sm_count, s);
+        if (e != cudaSuccess) return e;
+    }
+    // the tensor-core lane: |x0> and the blocks of every such circuit, on the
+    // same stream, with the batch's error word (so a timeout there is
+    // reported like one in the persistent launch)
+    for (size_t i = 0; i < b->fused_plans.size(); i++) {
+        qsim_state *h = b->fused_states[i];
+        const cudaStream_t hs = h->stream;
+        uint32_t *const herr = h->d_err;
+        const bool prof = h->prof;
+        h->stream = s;
+        h->d_err = b->d_err;
+        h->prof = false;
+        e = launch_init_basis(h->amp, (int)h->dt, h->n, b->fused_x0[i], s);
+        if (e == cudaSuccess && run_built(h, *b->fused_plans[i], nullptr, nullptr) != QSIM_OK) e = cudaErrorUnknown;
+        h->stream = hs;
+        h->d_err = herr;
+        h->prof = prof;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out) {
+// capture: record the runs' launches in a CUDA graph (a planned batch replays
+// it; a one-shot batch enqueues its launches directly).
+static qsim_status batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out,
+                                bool capture) {
     if (!out) return fail(QSIM_EINVAL, "out is NULL");
     *out = nullptr;
     if (nc == 0 || !cs) return fail(QSIM_EINVAL, "empty batch");
@@ -1426,13 +1478,79 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     double alg_bytes = 0.0, alg_flops = 0.0;
     int ident[64];
     for (int q = 0; q < 64; q++) ident[q] = q;
+    std::vector<qsim_plan_s *> fplans(nc, nullptr), built(nc, nullptr);  // uploaded / planned on the host only
+    auto free_fplans = [&]() {
+        for (qsim_plan_s *P : fplans) plan_release(P);
+        for (qsim_plan_s *P : built) plan_release(P);
+    };
+    // The tensor-core lane: 6-qubit blocks (or fuse_k) for the largest
+    // circuits, unless fuse_k = -1.  Their FP64 block products are planned on
+    // the host in parallel threads (the planner is pure host code); a circuit
+    // with a gate wider than the block stays in the persistent launch.
+    const int fk = o.fuse_k > 0 ? o.fuse_k : 6;
+    std::vector<size_t> lane;
     for (size_t i = 0; i < nc; i++) {
         const qsim_handle h = cs[i].state;
+        if (o.fuse_k >= 0 && h->n >= kBatchFusedMinQubits && cs[i].ng > 0 &&
+            ((fk == 6 && fused_tc6_supported(h->n)) || (fk != 6 && fused_tc_supported(0, fk, h->n)))) {
+            for (int q = 0; q < 64; q++) h->phys[q] = q;  // every run starts from the identity layout
+            lane.push_back(i);
+        }
+    }
+    std::vector<qsim_status> built_st(nc, QSIM_OK);
+    {
+        qsim_opts fo = o;
+        fo.mode = QSIM_MODE_FUSED;
+        fo.tile_bits = 0;
+        fo.fuse_k = fk;
+        std::atomic<size_t> next{0};
+        auto work = [&]() {
+            for (size_t j = next++; j < lane.size(); j = next++) {
+                const size_t i = lane[j];
+                qsim_plan_s *P = new qsim_plan_s;
+                built_st[i] = build_plan(cs[i].state, cs[i].gates, cs[i].ng, &fo, *P);
+                if (built_st[i] == QSIM_OK) built[i] = P;
+                else plan_release(P);
+            }
+        };
+        const size_t nthr = std::min<size_t>(lane.size(), std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < nthr; t++) pool.emplace_back(work);
+        work();
+        for (std::thread &t : pool) t.join();
+    }
+    int64_t nfused = 0;
+    for (size_t i = 0; i < nc; i++) {
+        const qsim_handle h = cs[i].state;
+        if (built[i] || built_st[i] != QSIM_OK) {
+            qsim_plan_s *P = nullptr;
+            qsim_status fst = built_st[i];
+            if (built[i]) fst = upload_plan(h, built[i], P);
+            built[i] = nullptr;
+            if (fst == QSIM_OK) {
+                fplans[i] = P;
+                ngates += (int64_t)cs[i].ng;
+                alg_bytes += P->stats.alg_bytes;
+                alg_flops += P->stats.alg_flops;
+                circs[i].amp = h->amp;
+                circs[i].x0 = cs[i].x0;
+                circs[i].pass_begin = (int32_t)passes.size();
+                circs[i].npasses = 0;  // no items in the persistent launch
+                nfused++;
+                continue;
+            }
+            if (fst != QSIM_EINVAL && fst != QSIM_EUNSUPPORTED) {
+                free_fplans();
+                return fail(fst, "circuit %zu: planning its dense blocks failed", i);
+            }
+        }
         std::vector<PGate> pg(cs[i].ng);
         std::string msg;
         for (size_t k = 0; k < cs[i].ng; k++)
-            if (!prepare_gate(cs[i].gates[k], h->n, ident, pg[k], msg))
+            if (!prepare_gate(cs[i].gates[k], h->n, ident, pg[k], msg)) {
+                free_fplans();
                 return fail(QSIM_EINVAL, "circuit %zu gate %zu: %s", i, k, msg.c_str());
+            }
         ngates += (int64_t)cs[i].ng;
         const int T = h->n < Tmax ? h->n : Tmax;
         const int L = T < 5 ? T : 5;
@@ -1452,8 +1570,10 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
             plan.passes.push_back(pp);
         }
         for (const PassPlan &pp : plan.passes) {
-            if (pp.op_count > kRegMaxOps || pp.phase_count > kRegMaxPhases)  // the planner's cap guarantees this
+            if (pp.op_count > kRegMaxOps || pp.phase_count > kRegMaxPhases) {  // the planner's cap guarantees this
+                free_fplans();
                 return fail(QSIM_EUNSUPPORTED, "circuit %zu: a pass exceeds the staged program capacity", i);
+            }
             alg_bytes += 2.0 * (double)state_bytes(h);  // each pass reads and writes the state once
             alg_flops += pp.flops;
             BatchPass bp{};
@@ -1485,6 +1605,11 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     for (size_t i = 0; i < nc; i++) {
         b->states.push_back(cs[i].state);
         b->x0.push_back(cs[i].x0);
+        if (fplans[i]) {
+            b->fused_states.push_back(cs[i].state);
+            b->fused_x0.push_back(cs[i].x0);
+            b->fused_plans.push_back(fplans[i]);  // owned by the batch from here on
+        }
     }
     b->stream = cs[0].state->stream;
     b->sm_count = cs[0].state->sm_count;
@@ -1522,8 +1647,9 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
         batch_release(b);
         return cuda_fail(e, "batch upload");
     }
-    // capture: counter reset + the persistent launch, replayed by every run
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+    // capture: counter reset, the persistent launch and the tensor-core lane,
+    // replayed by every run
+    if (capture && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
         cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         cudaError_t le = batch_enqueue(b, b->cap);
         cudaGraph_t g = nullptr;
@@ -1539,13 +1665,22 @@ qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts
     cudaGetLastError();  // a refused capture leaves no sticky error: fall back to direct launches
     b->stats.circuits = (int64_t)nc;
     b->stats.gates = ngates;
+    int64_t nblocks = 0;
+    for (qsim_plan_s *P : b->fused_plans) nblocks += (int64_t)P->blocks.size();
     b->stats.passes = (int64_t)passes.size();
+    b->stats.blocks = nblocks;
     b->stats.items = (int64_t)items.size();
+    b->stats.fused = (int32_t)nfused;
+    b->stats.kernels = (items.empty() ? 0 : 1) + nfused + nblocks;  // persistent launch, |x0> and blocks
     b->stats.alg_bytes = alg_bytes;
     b->stats.alg_flops = alg_flops;
     b->stats.graph = b->exec ? 1 : 0;
     *out = b;
     return QSIM_OK;
+}
+
+qsim_status qsim_batch_create(const qsim_circuit *cs, size_t nc, const qsim_opts *opts, qsim_batch *out) {
+    return batch_create(cs, nc, opts, out, true);
 }
 
 qsim_status qsim_batch_run(qsim_batch b) {
@@ -1585,7 +1720,7 @@ qsim_status qsim_batch_free(qsim_batch b) {
 qsim_status qsim_run_batch(const qsim_circuit *cs, size_t nc, const qsim_opts *opts) {
     if (nc == 0) return QSIM_OK;
     qsim_batch b = nullptr;
-    qsim_status st = qsim_batch_create(cs, nc, opts, &b);
+    qsim_status st = batch_create(cs, nc, opts, &b, false);  // one run: no graph to build
     if (st != QSIM_OK) return st;
     st = qsim_batch_run(b);
     if (st == QSIM_OK) st = qsim_batch_sync(b);

@@ -1,6 +1,7 @@
-"""Batches of independent circuits in one persistent launch (qsim_run_batch,
-qsim_batch_*): parity with the oracle, CUDA-graph replay, and the bounded
-wait between passes (forced to expire: an error status, not a fault)."""
+"""Batches of independent circuits (qsim_run_batch, qsim_batch_*): one
+persistent launch plus the tensor-core lane for circuits of 20 qubits or more;
+parity with the oracle, CUDA-graph replay, and the bounded wait between passes
+(forced to expire: an error status, not a fault)."""
 import numpy as np
 import pytest
 
@@ -93,21 +94,47 @@ def test_batch_graph_replay_is_repeatable(q):
 
 
 def test_batch_wait_budget_expiry_is_reported(q):
-    # 20-qubit circuits need many passes of 256 tiles; with a 1 microsecond
-    # budget the waits between passes must expire.  The call returns
-    # QSIM_ETIMEOUT, the device stays usable, and a normal run afterwards is
-    # correct.
+    # 20-qubit circuits kept in the persistent launch (fuse_k = -1) need many
+    # passes of 256 tiles; with a 1 microsecond budget the waits between
+    # passes must expire.  The call returns QSIM_ETIMEOUT, the device stays
+    # usable, and a normal run afterwards is correct.
     circs = inputs.batch_circuits(count=4, seed0=50, nmin=20, nmax=20, dmin=12, dmax=12)
     states = [q.State(n, "c64") for n, _ in circs]
     x0s = [0] * len(states)
     with pytest.raises(q.QsimError) as ei:
-        q.run_batch(states, x0s, [g for _, g in circs], wait_budget_us=1)
+        q.run_batch(states, x0s, [g for _, g in circs], wait_budget_us=1, fuse_k=-1)
     assert ei.value.status == q.QSIM_ETIMEOUT
     q.run_batch(states, x0s, [g for _, g in circs])
     n, g = circs[0]
     assert _err(states[0].get_state(), oracle.run(n, g, x0=0)) < 2e-5
     for st in states:
         st.free()
+
+
+def test_batch_tensor_core_lane(q):
+    """Circuits of 20 qubits or more run as 6-qubit tensor-core blocks after
+    the persistent launch (the others in it), in one captured graph: every
+    state against the oracle, twice in a row, and the same circuits kept in
+    the persistent launch (fuse_k = -1) agree."""
+    circs = (inputs.batch_circuits(count=3, seed0=70, nmin=12, nmax=16, dmin=6, dmax=12) +
+             inputs.batch_circuits(count=3, seed0=80, nmin=20, nmax=21, dmin=8, dmax=14))
+    states = [q.State(n, "c64") for n, _ in circs]
+    x0s = [inputs.random_basis(n, seed=90 + i) for i, (n, _) in enumerate(circs)]
+    b = q.Batch(states, x0s, [g for _, g in circs])
+    st = b.stats()
+    assert st["fused"] == sum(1 for n, _ in circs if n >= 20) == 3
+    assert st["graph"]
+    refs = [oracle.run(n, g, x0=x0) for (n, g), x0 in zip(circs, x0s)]
+    for rep in range(2):
+        b.run()
+        b.sync()
+        for s_, ref, (n, _) in zip(states, refs, circs):
+            assert _err(s_.get_state(), ref) < 2e-5, (rep, n)
+    b.free()
+    q.run_batch(states, x0s, [g for _, g in circs], fuse_k=-1)
+    for s_, ref, (n, _) in zip(states, refs, circs):
+        assert _err(s_.get_state(), ref) < 2e-5, n
+        s_.free()
 
 
 def test_batch_config_512_sampled(q):
@@ -124,6 +151,7 @@ def test_batch_config_512_sampled(q):
     for st, (n, g) in zip(states, circs):
         assert abs(st.norm() - 1) < 1e-4
     picked = [i for i, (n, _) in enumerate(circs) if n <= 15][:6]
+    picked += [i for i, (n, _) in enumerate(circs) if n == 20][:2]  # the tensor-core lane
     for i in picked:
         n, g = circs[i]
         assert _err(states[i].get_state(), oracle.run(n, g, x0=x0s[i])) < 2e-5
