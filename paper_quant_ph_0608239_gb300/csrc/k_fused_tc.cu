@@ -268,10 +268,12 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
             const uint32_t ahi = smem_u32(s_ahi);
             const uint32_t bhi = smem_u32(s_bhi), blo = smem_u32(s_blo);
             const uint32_t idesc = umma_idesc_tf32(128, N);
-            // The tensor cores round each accumulation toward zero, relative
-            // to the running sum: the small cross products go in first, while
-            // the sum is small, and the head products last, so that only one
-            // accumulation per K step rounds at the output's scale.
+            // Each accumulation into the FP32 accumulator loses a little
+            // magnitude relative to the running sum (measured: a systematic
+            // norm loss per block, not a random one): the small cross
+            // products go in first, while the sum is small, and the head
+            // products last, so that only one accumulation per K step rounds
+            // at the output's scale.
 #pragma unroll
             for (int ks = 0; ks < KR / 8; ks++) {
                 const uint32_t o = (uint32_t)ks * 256u;  // 8 TF32 along K = two core matrices
