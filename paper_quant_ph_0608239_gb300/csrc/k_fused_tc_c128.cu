@@ -19,35 +19,39 @@
 // first block of a run reads IEEE doubles (IN_IEEE) and the last one writes
 // them (OUT_IEEE), converting with integer operations (df64.cuh).
 //
-// One CTA per SM, 640 threads (20 warps, five per scheduler, 96 registers
-// each): 16 compute warps -- the four warps of a tensor-memory lane quarter
-// share its 32 groups, each taking one quarter of a group's 32 amplitudes,
-// which is one K step (16 reals) of the product -- and one duty warp per
-// scheduler: the MMA warp, the fetch warp and two idle ones.  The duty warps
-// issue work whose issue stalls (the tensor pipe and the bulk-copy engine
-// take instructions only as fast as they execute them), so no compute warp
-// waits for it.  Per tile of 128 groups (4096 amplitudes, 64 KiB):
+// One CTA per SM, 608 threads (19 warps, 96 registers each): 16 compute
+// warps -- the four warps of a tensor-memory lane quarter share its 32
+// groups, each taking one quarter of a group's 32 amplitudes, which is one K
+// step (16 reals) of the product -- and three duty warps: the MMA warp, the
+// fetch warp and the store warp.  The duty warps issue work whose issue
+// stalls (the tensor pipe and the bulk-copy engine take instructions only as
+// fast as they execute them), so no compute warp waits for it.  Per tile of
+// 128 groups (4096 amplitudes, 64 KiB):
 //   1. the fetch warp copies the tile (bulk asynchronous copies, TMA engine)
-//      into one of two shared-memory buffers, as soon as the compute warps
-//      have read the tile two before out of it;
+//      into the input buffer as soon as the compute warps have read the tile
+//      before out of it;
 //   2. fetch: each compute thread reads its 8 amplitudes into registers and
 //      the four threads of a group agree on its largest exponent;
-//   3. digits: the thread writes the six slices of its amplitudes into the A
-//      slices in tensor memory (its lane, 8 columns per slice);
+//   3. split: the thread cuts its amplitudes into six bf16 digit slices,
+//      kept in registers until the A slices in tensor memory are free, then
+//      written there (its lane, 8 columns per slice);
 //   4. the MMA warp issues the 21 products x 4 K steps of 16 as 48
 //      instructions (slices of B side by side along N);
 //   5. combination: each thread reads the accumulators of its 16 output
-//      reals in two halves of 8, adds the levels in double-float and stores
-//      the amplitudes from registers to global memory.
+//      reals in two halves of 8, adds the levels in double-float and writes
+//      the amplitudes into the output buffer at their tile positions; the
+//      store warp copies the buffer's runs to global memory (bulk copies).
 // The compute warps run tile i + 1's digits and tile i's combination around
 // the MMAs: the MMA warp commits each K step of a tile on its own mbarrier, so
 // the warps of a K quarter write the next tile's digits into their A slices
 // as soon as the current tile's MMAs of that K step are done; once all are
 // done and tile i's accumulators are read into registers (the first half
 // combined meanwhile), tile i + 1's MMAs start, and the rest of tile i's
-// combination, its stores and tile i + 2's fetch run beside them.
+// combination, its stores and tile i + 2's fetch and split run beside them.
+// Shared-memory loads and stores of the amplitudes go through a per-lane
+// rotation of the column index (no bank conflicts within a wavefront).
 // Hand-offs go through mbarriers (tile fetched, buffer read, A slices ready,
-// K step done), every wait bounded.
+// K step done, outputs written, outputs copied out), every wait bounded.
 // Tensor memory: accumulators at columns 0..319 (level L at 64 L), the A
 // slices at 320 + 48 s + 8 i (K step s, slice i): all 512 columns.
 #include <cstring>
@@ -64,7 +68,7 @@ namespace qsim {
 namespace {
 
 constexpr int kThreads128 = 512;            // compute threads: 16 warps
-constexpr int kThreadsAll128 = 576;         // + the MMA-issue warp and the fetch-issue warp
+constexpr int kThreadsAll128 = 608;         // + the MMA-issue, fetch-issue and store-issue warps
 constexpr int kK = 5;                          // qubits of a block
 constexpr int kAmps = 1 << kK;                 // 32 amplitudes of a group
 constexpr int kReals = 2 * kAmps;              // 64: K and N of the product
@@ -141,12 +145,14 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                     uint32_t *err, uint64_t ntiles) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *s_b = smem_raw;                    // six B slices
-    unsigned char *s_buf0 = smem_raw + kBBytes;       // two input buffers
-    // bar_ld: tile arrived in buffer b; bar_free: the compute warps have read
-    // buffer b into registers; bar_ready: tile's A slices written and the last tile's
-    // accumulators read (MMAs may start); bar_mks[s]: the MMAs of K steps
-    // 0..s done (bar_mks[3]: all); bar_b: B loaded
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mks[4], bar_b;
+    unsigned char *s_in = smem_raw + kBBytes;         // the tile being fetched
+    unsigned char *s_out = s_in + kTileBytes;         // the outputs of the tile being stored
+    // bar_ld: a tile arrived in s_in; bar_free: the compute warps have read
+    // it into registers; bar_ready: tile's A slices written and the last
+    // tile's accumulators read (MMAs may start); bar_mks[s]: the MMAs of K
+    // steps 0..s done (bar_mks[3]: all); bar_out: a tile's outputs are in
+    // s_out; bar_outfree: their bulk stores have read s_out; bar_b: B loaded
+    __shared__ __align__(8) uint64_t bar_ld, bar_free, bar_ready, bar_mks[4], bar_out, bar_outfree, bar_b;
     __shared__ uint32_t tmem_base_s;
     __shared__ uint32_t s_max[2][4][128];  // per tile parity, K quarter, group: largest hi exponent field
     __shared__ int s_hb[kMaxH128];
@@ -158,10 +164,10 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
     if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < kMaxH128; k++) s_hb[k] = k < H ? g.hb[k] : 0;
-        for (int b = 0; b < 2; b++) {
-            mbar_init(&bar_ld[b], 1);
-            mbar_init(&bar_free[b], kThreads128 / 32);
-        }
+        mbar_init(&bar_ld, 1);
+        mbar_init(&bar_free, kThreads128 / 32);
+        mbar_init(&bar_out, kThreads128 / 32);
+        mbar_init(&bar_outfree, 1);
         mbar_init(&bar_ready, kThreads128 / 32);
         for (int ks = 0; ks < 4; ks++) mbar_init(&bar_mks[ks], 1);
         mbar_init(&bar_b, 1);
@@ -186,7 +192,6 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         for (int k = 0; k < H; k++) base = insert_zero(base, s_hb[k]);
         return base;
     };
-    auto buf = [&](int b) { return s_buf0 + (size_t)b * kTileBytes; };
     const uint64_t stride = gridDim.x;
     // this CTA's tiles: blockIdx.x + i * stride, i < count
     const uint32_t count = blockIdx.x < ntiles ? (uint32_t)((ntiles - 1 - blockIdx.x) / stride + 1) : 0u;
@@ -237,17 +242,16 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         if (issued) mbar_wait_bounded(&bar_mks[3], (issued - 1u) & 1u, kWaitBudget128);
         if (!ok) atomicExch(err, kErrTimeout);
     } else if (warp == kThreads128 / 32 + 1) {
-        // ---- fetch warp: tile k into buffer k & 1 once tile k - 2 left it
-        uint32_t issued0 = 0u, issued1 = 0u;
+        // ---- fetch warp: tile k into s_in once tile k - 1 was read out of it
+        uint32_t issued = 0u;
         auto issue_load = [&](uint32_t i) {
-            const int b = (int)(i & 1u);
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * stride);
-            if (lane == 0) mbar_arrive_expect_tx(&bar_ld[b], kTileBytes);
+            if (lane == 0) mbar_arrive_expect_tx(&bar_ld, kTileBytes);
             __syncwarp();
-            double2 *dst = reinterpret_cast<double2 *>(buf(b));
+            double2 *dst = reinterpret_cast<double2 *>(s_in);
             for (uint32_t j = lane; j < nruns; j += 32)
-                bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld[b]);
-            if (b) issued1++; else issued0++;
+                bulk_g2s(dst + ((size_t)j << L), a + (base | run_off(j)), run_bytes, &bar_ld);
+            issued++;
         };
         if (lane == 0) {
             mbar_arrive_expect_tx(&bar_b, kBBytes);
@@ -255,12 +259,30 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         }
         bool ok = true;
         for (uint32_t k = 0; k < count && ok; k++) {
-            if (k >= 2) ok = mbar_wait_bounded(&bar_free[k & 1u], ((k - 2) >> 1) & 1u, kWaitBudget128);
+            if (k >= 1) ok = mbar_wait_bounded(&bar_free, (k - 1u) & 1u, kWaitBudget128);
             if (ok) issue_load(k);
         }
         // every fetch has landed before the CTA may leave
-        if (issued0) mbar_wait_bounded(&bar_ld[0], (issued0 - 1u) & 1u, kWaitBudget128);
-        if (issued1) mbar_wait_bounded(&bar_ld[1], (issued1 - 1u) & 1u, kWaitBudget128);
+        if (issued) mbar_wait_bounded(&bar_ld, (issued - 1u) & 1u, kWaitBudget128);
+    } else if (warp == kThreads128 / 32 + 2) {
+        // ---- store warp: a tile's outputs from s_out to global memory (bulk
+        // copies, one per run) once the compute warps wrote them; s_out is
+        // free again when the copies have read it
+        bool ok = true;
+        for (uint32_t i = 0; i < count && ok; i++) {
+            ok = mbar_wait_bounded(&bar_out, i & 1u, kWaitBudget128);
+            if (!ok) break;
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * stride);
+            const double2 *src = reinterpret_cast<const double2 *>(s_out);
+            for (uint32_t j = lane; j < nruns; j += 32)
+                bulk_s2g(a + (base | run_off(j)), src + ((size_t)j << L), run_bytes);
+            bulk_commit();
+            bulk_wait_read_all();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_outfree);
+        }
+        bulk_wait_all();  // the stores are complete before the CTA leaves
+        if (!ok) atomicExch(err, kErrTimeout);
     } else if (warp < kThreads128 / 32) {
         // ---- compute warps: group m (tensor-memory lane), K quarter qq
         const int lq = warp & 3, qq = warp >> 2;
@@ -272,12 +294,45 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         uint32_t wc[kK];
 #pragma unroll
         for (int b = 0; b < kK; b++) wc[b] = 1u << fm.col[b];
-        // this thread's amplitudes: columns 8 qq + j, j < 8; their tile
-        // indices (shared memory) and offsets from the tile's base (global)
+        // this thread's amplitudes: columns 8 qq + j, j < 8, and their tile
+        // indices (the same in s_in and s_out)
         const uint32_t qbase = ibase | ((qq & 1) ? wc[3] : 0u) | ((qq & 2) ? wc[4] : 0u);
-        const uint32_t lowmask = (1u << L) - 1u;
-        auto goff = [&](uint32_t t) { return (uint64_t)(t & lowmask) | run_off(t >> L); };
-        const uint64_t gq = goff(qbase), gc0 = goff(wc[0]), gc1 = goff(wc[1]), gc2 = goff(wc[2]);
+        // Shared-memory banks: the 8 lanes of one 128-byte wavefront of a
+        // 16-byte access read or write 8 different 16-byte slots when tile
+        // bits 0..2 vary across them.  Those that are rows vary with lane bits
+        // 0..k-1 (rows are in ascending order); those that are columns 0..2 of
+        // the thread are made to vary with the next lane bits by an XOR rot
+        // on the column index of every load and store, undone in registers.
+        uint32_t rot = 0;
+        {
+            uint32_t colmask = 0;
+#pragma unroll
+            for (int c = 0; c < kK; c++) colmask |= 1u << fm.col[c];
+            int lb = 0;
+#pragma unroll
+            for (int b = 0; b < 3; b++) lb += ((colmask >> b) & 1u) ? 0 : 1;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                if (fm.col[c] <= 2) rot |= ((uint32_t)(lane >> lb++) & 1u) << c;
+        }
+        const bool rotated = __any_sync(0xffffffffu, rot != 0);  // the same in every warp
+        auto colbits = [&](int j) {
+            return ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
+        };
+        // x[j] := x[j ^ rot] (after loads at rotated columns; before stores)
+        auto unrot = [&](auto (&x)[8]) {
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                const bool sw = (rot >> b) & 1u;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (!(j & (1 << b))) {
+                        const auto p = x[j], q2 = x[j | (1 << b)];
+                        x[j] = sw ? q2 : p;
+                        x[j | (1 << b)] = sw ? p : q2;
+                    }
+            }
+        };
         auto coff = [&](int j) {
             return qbase | ((j & 1) ? wc[0] : 0u) | ((j & 2) ? wc[1] : 0u) | ((j & 4) ? wc[2] : 0u);
         };
@@ -294,13 +349,14 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         // K quarter qq), two amplitudes at a time.
         uint4 v[8];
         auto fetch = [&](uint32_t i) -> bool {
-            const int b = (int)(i & 1u);
-            if (compute_any(!mbar_wait_bounded(&bar_ld[b], (i >> 1) & 1u, kWaitBudget128))) return false;
-            const uint32_t sbuf = smem_u32(buf(b));
+            const int b = (int)(i & 1u);  // s_max slot
+            if (compute_any(!mbar_wait_bounded(&bar_ld, i & 1u, kWaitBudget128))) return false;
+            const uint32_t sbuf = smem_u32(s_in);
             uint32_t mx = 0;
+            const uint32_t cb = coff(0) | colbits((int)rot);  // coff(j ^ rot) = cb ^ colbits(j)
 #pragma unroll
             for (int j = 0; j < 8; j++) {
-                v[j] = lds_u4(sbuf + 16u * coff(j));
+                v[j] = lds_u4(sbuf + 16u * (cb ^ colbits(j)));
                 if (IN_IEEE) {  // a double2 -> (re.h, re.l, im.h, im.l)
                     const df re = df_from_double(__hiloint2double((int)v[j].y, (int)v[j].x));
                     const df im = df_from_double(__hiloint2double((int)v[j].w, (int)v[j].z));
@@ -309,10 +365,11 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                 }
                 mx = max(mx, max(v[j].x & 0x7f800000u, v[j].z & 0x7f800000u));
             }
+            if (rotated) unrot(v);
             s_max[b][qq][m] = mx;
             quarter_sync(1u + (uint32_t)lq);
             // this warp's amplitudes are in registers: its share of the buffer is free
-            if (lane == 0) mbar_arrive(&bar_free[b]);
+            if (lane == 0) mbar_arrive(&bar_free);
             Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
             return true;
         };
@@ -369,7 +426,10 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
         // next), combined and stored; false if a wait gave up here or in a
         // warp (bad).
         auto finish = [&](uint32_t i, bool next, bool bad) -> bool {
-            if (compute_any(bad || !mbar_wait_bounded(&bar_mks[3], i & 1u, kWaitBudget128))) return false;
+            // s_out is free once the last tile's stores have read it
+            const bool out_free = i == 0 || mbar_wait_bounded(&bar_outfree, (i - 1u) & 1u, kWaitBudget128);
+            if (compute_any(bad || !out_free || !mbar_wait_bounded(&bar_mks[3], i & 1u, kWaitBudget128)))
+                return false;
             tc_fence_after();
             // Tile i's accumulators, 16 output reals (8 amplitudes) in two
             // halves: levels 3 and 4-5 folded into one on arrival (rounding
@@ -377,7 +437,7 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             // half is combined before the second is read; once both are in
             // registers, tile i + 1's MMAs may start.
             const float su = dg_scale_up(Ecur);
-            double2 *gt = a + tile_base(blockIdx.x + (uint64_t)i * stride);
+            const uint32_t so = smem_u32(s_out);
             uint32_t acc[kDigitLevels - 1][8];
             auto drain = [&](int hf) {
                 uint32_t a4[8];
@@ -410,20 +470,16 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
                     o[c + 1] = df{h.y, l.y};
                 }
             };
-            // output amplitudes 8 qq + 4 hf + jj, from registers to global memory
-            auto store = [&](int hf, const df (&o)[8]) {
-#pragma unroll
-                for (int jj = 0; jj < 4; jj++) {
-                    const int j = 4 * hf + jj;
-                    const df re = o[2 * jj], im = o[2 * jj + 1];
-                    const uint64_t go =
-                        gq | ((j & 1) ? gc0 : 0ull) | ((j & 2) ? gc1 : 0ull) | ((j & 4) ? gc2 : 0ull);
-                    if (OUT_IEEE) {
-                        gt[go] = make_double2(df_to_double(re), df_to_double(im));
-                    } else {
-                        *reinterpret_cast<float4 *>(gt + go) = make_float4(re.h, re.l, im.h, im.l);
-                    }
+            // the 8 output amplitudes (re.h, re.l, im.h, im.l, or the IEEE
+            // doubles in the last block) into s_out at their tile indices,
+            // at rotated columns (the store warp copies whole runs out)
+            auto amp4 = [&](const df &re, const df &im) {
+                if (OUT_IEEE) {
+                    const double x = df_to_double(re), y = df_to_double(im);
+                    return make_float4(__uint_as_float(__double2loint(x)), __uint_as_float(__double2hiint(x)),
+                                       __uint_as_float(__double2loint(y)), __uint_as_float(__double2hiint(y)));
                 }
+                return make_float4(re.h, re.l, im.h, im.l);
             };
             df o0[8], o1[8];
             drain(0);
@@ -431,9 +487,22 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             drain(1);
             tmem_st_wait();
             if (next) arrive_ready();  // tile i + 1's digits written, tile i's accumulators read
-            store(0, o0);
             combine(o1);
-            store(1, o1);
+            {
+                float4 w[8];
+#pragma unroll
+                for (int jj = 0; jj < 4; jj++) {
+                    w[jj] = amp4(o0[2 * jj], o0[2 * jj + 1]);
+                    w[4 + jj] = amp4(o1[2 * jj], o1[2 * jj + 1]);
+                }
+                if (rotated) unrot(w);
+                const uint32_t cb = coff(0) | colbits((int)rot);
+#pragma unroll
+                for (int j = 0; j < 8; j++) sts128(so + 16u * (cb ^ colbits(j)), w[j]);
+            }
+            fence_proxy_async_smem();  // the outputs are visible to the bulk stores
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_out);
             return true;
         };
         // steady state, the MMAs of tile i in flight and tile i + 1 split in
