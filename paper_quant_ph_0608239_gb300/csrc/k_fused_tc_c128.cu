@@ -45,9 +45,9 @@
 // the MMAs: the MMA warp commits each K step of a tile on its own mbarrier, so
 // the warps of a K quarter write the next tile's digits into their A slices
 // as soon as the current tile's MMAs of that K step are done; once all are
-// done and tile i's accumulators are read into registers (the first half
-// combined meanwhile), tile i + 1's MMAs start, and the rest of tile i's
-// combination, its stores and tile i + 2's fetch and split run beside them.
+// done and tile i's accumulators are read into registers, tile i + 1's
+// MMAs start, and tile i's combination, its stores and tile i + 2's fetch and
+// split run beside them.
 // Shared-memory loads and stores of the amplitudes go through a per-lane
 // rotation of the column index (no bank conflicts within a wavefront).
 // Hand-offs go through mbarriers (tile fetched, buffer read, A slices ready,
@@ -433,13 +433,13 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             tc_fence_after();
             // Tile i's accumulators, 16 output reals (8 amplitudes) in two
             // halves: levels 3 and 4-5 folded into one on arrival (rounding
-            // below 2^-50 of the result), then levels 0, 1, 2.  The first
-            // half is combined before the second is read; once both are in
-            // registers, tile i + 1's MMAs may start.
+            // below 2^-50 of the result), then levels 0, 1, 2.  Once both
+            // halves are in registers, tile i + 1's MMAs may start.
             const float su = dg_scale_up(Ecur);
             const uint32_t so = smem_u32(s_out);
-            uint32_t acc[kDigitLevels - 1][8];
+            uint32_t acc2[2][kDigitLevels - 1][8];
             auto drain = [&](int hf) {
+                auto &acc = acc2[hf];
                 uint32_t a4[8];
                 const uint32_t c0 = tmem + lane_off + (uint32_t)(16 * qq + 8 * hf);
                 tmem_ld8(c0 + kReals * 3, acc[3]);
@@ -458,7 +458,8 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             };
             // the 8 output reals of the half in acc as double-floats, the re
             // and im parts of an amplitude together (packed FP32x2)
-            auto combine = [&](df (&o)[8]) {
+            auto combine = [&](int hf, df (&o)[8]) {
+                auto &acc = acc2[hf];
                 auto pr = [&](int L, int c) {
                     return fpair{__uint_as_float(acc[L][c]), __uint_as_float(acc[L][c + 1])};
                 };
@@ -483,11 +484,11 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             };
             df o0[8], o1[8];
             drain(0);
-            combine(o0);
             drain(1);
             tmem_st_wait();
             if (next) arrive_ready();  // tile i + 1's digits written, tile i's accumulators read
-            combine(o1);
+            combine(0, o0);
+            combine(1, o1);
             {
                 float4 w[8];
 #pragma unroll
