@@ -114,8 +114,9 @@ def test_batch_wait_budget_expiry_is_reported(q):
 def test_batch_tensor_core_lane(q):
     """Circuits of 20 qubits or more run as 6-qubit tensor-core blocks after
     the persistent launch (the others in it), in one captured graph: every
-    state against the oracle, twice in a row, and the same circuits kept in
-    the persistent launch (fuse_k = -1) agree."""
+    state against the oracle, twice in a row; the same with 5-qubit blocks
+    (fuse_k = 5) and with every circuit kept in the persistent launch
+    (fuse_k = -1)."""
     circs = (inputs.batch_circuits(count=3, seed0=70, nmin=12, nmax=16, dmin=6, dmax=12) +
              inputs.batch_circuits(count=3, seed0=80, nmin=20, nmax=21, dmin=8, dmax=14))
     states = [q.State(n, "c64") for n, _ in circs]
@@ -131,6 +132,9 @@ def test_batch_tensor_core_lane(q):
         for s_, ref, (n, _) in zip(states, refs, circs):
             assert _err(s_.get_state(), ref) < 2e-5, (rep, n)
     b.free()
+    q.run_batch(states, x0s, [g for _, g in circs], fuse_k=5)  # 5-qubit blocks (3xTF32) on the lane
+    for s_, ref, (n, _) in zip(states, refs, circs):
+        assert _err(s_.get_state(), ref) < 2e-5, n
     q.run_batch(states, x0s, [g for _, g in circs], fuse_k=-1)
     for s_, ref, (n, _) in zip(states, refs, circs):
         assert _err(s_.get_state(), ref) < 2e-5, n
