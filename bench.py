@@ -747,7 +747,12 @@ def run_batch_workload(args, w, ws, rank, local):
                 "frac": tfl / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "nominal FP32: 152 SM x 128 x 2 x 2.07 GHz",
                 "alg_flops_per_launch": bst["alg_flops"], "launches": args.steps, "avg_launch_ms": per_run * 1e3}
-    roof, other = (alu_roof, hbm_roof) if alu_roof["frac"] > hbm_roof["frac"] else (hbm_roof, alu_roof)
+    if bst["fused"]:
+        # the tensor-core lane's dense products are counted in alg_flops but run
+        # on the tensor cores, not the FP32 pipes: no FP32 roofline then
+        roof, other = hbm_roof, None
+    else:
+        roof, other = (alu_roof, hbm_roof) if alu_roof["frac"] > hbm_roof["frac"] else (hbm_roof, alu_roof)
     out = {
         "metric": METRIC, "value": ng * args.steps / el, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
