@@ -110,11 +110,10 @@ def dtype_label(dt, kernel=None):
 
 
 # The batch's algorithmic bytes count every pass and block as a read and a
-# write of its state; states of up to 2^23 complex64 amplitudes (64 MiB) stay
-# in the 129 MB L2 from one pass or block to the next, so the batch's figure
-# against the HBM copy rate can exceed 1.
+# write of its state; states of up to 2^23 complex64 amplitudes (64 MiB) can
+# stay in the 129 MB L2 from one pass or block to the next.
 BATCH_L2_NOTE = ("algorithmic bytes = every pass or block reads and writes its state; states of <= 2^23 "
-                 "amplitudes (64 MiB) stay in the 129 MB L2 between passes, so achieved/peak may exceed 1")
+                 "amplitudes (64 MiB) can stay in the 129 MB L2 between passes")
 
 
 def path_label(dt, pst, pergate=False):
