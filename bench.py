@@ -658,11 +658,13 @@ def config_lines(q, main, args):
     st.free()
     ad["output_index_exact"] = sum(1 << i for i in range(30) if qp[i] > 0.5) == inputs.adder_expected_index([a, b], 15)
     res["adder2x15_c64"] = ad
-    # 34 qubits, depth 20, complex64 (128 GiB): 5-qubit tensor-core blocks
-    # (the autotuner's pick there; its other candidates take 2-4x longer)
+    # 34 qubits, depth 20, complex64 (128 GiB): 5- and 6-qubit tensor-core
+    # blocks (the tile passes take 2-4x longer there)
     g = inputs.random_circuit(34, 20, 4)
     res["random34_c64"] = {"tensor_cores_k5": _timed_circuit(q, 34, "c64", g, inputs.random_basis(34, 4), 3,
-                                                             fuse_k=5)}
+                                                             fuse_k=5),
+                           "tensor_cores_k6": _timed_circuit(q, 34, "c64", g, inputs.random_basis(34, 4), 3,
+                                                             fuse_k=6)}
     # batch of 512 circuits: one graph replay per run
     import torch
     circs = inputs.batch_circuits()

@@ -160,5 +160,7 @@ def test_config_lines_bookkeeping(monkeypatch):
     assert ad["output_index_exact"] is True
     assert (30, "c64", _Dev.MODE_AUTO, 0, 0) in _Dev.planned
     assert res["batch512_c64"]["cuda_graph"] is True
-    assert res["batch512_c64"]["eff_hbm_frac"] == pytest.approx(5e9 / 0.040 / 1e9 / 1000.0)
+    bms = res["batch512_c64"]["ms_per_run"]
+    assert res["batch512_c64"]["eff_hbm_frac"] == pytest.approx(5e9 / (bms / 1e3) / 1e9 / 1000.0)
+    assert set(res["random34_c64"]) == {"tensor_cores_k5", "tensor_cores_k6"}
     assert "random34_c64" in res and "qft10_c128" in res

@@ -147,7 +147,11 @@ def test_c4_slice_every_autotune_candidate(q):
 
 
 # ----------------------------------- 34 qubits on the tensor-core blocks
-def test_34q_qft_tensor_cores_sampled_amplitudes(q):
+FAMILY = {5: "fused_tensor_core", 6: "fused_tc_bf16x3"}
+
+
+@pytest.mark.parametrize("k", [5, 6])
+def test_34q_qft_tensor_cores_sampled_amplitudes(q, k):
     # QFT|x> has a closed form at every index; the fused blocks of the QFT
     # network are not symmetric, so a transposed block would show here
     import torch
@@ -156,16 +160,16 @@ def test_34q_qft_tensor_cores_sampled_amplitudes(q):
     st = q.State(n, "c64")
     st.set_basis(x)
     st.profile(True)
-    st.run(gates, fuse_k=5)
+    st.run(gates, fuse_k=k)
     prof = st.profile_read()
-    assert "fused_tensor_core" in prof, prof
+    assert FAMILY[k] in prof, prof
     torch.cuda.synchronize()
     rng = np.random.default_rng(3)
     idx = np.concatenate([rng.integers(0, 1 << n, 8192), [0, 1, (1 << n) - 1, 1 << 32, (1 << 32) - 1]])
     got = st.tensor[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
     expect = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
     rel = float(np.max(np.abs(got - expect))) / (2.0 ** (-n / 2))
-    print("34-qubit QFT, 5-qubit tensor-core blocks: relative error %.3g" % rel)
+    print("34-qubit QFT, %d-qubit tensor-core blocks: relative error %.3g" % (k, rel))
     assert rel < 1e-4, rel
     assert abs(st.norm() - 1) < 1e-4
     st.free()
@@ -185,7 +189,8 @@ def _inverse(gates):
     return inv
 
 
-def test_34q_random_circuit_tensor_cores_then_inverse(q):
+@pytest.mark.parametrize("k", [5, 6])
+def test_34q_random_circuit_tensor_cores_then_inverse(q, k):
     import torch
     n = 34
     gates = inputs.random_circuit(n, 20, seed=4)
@@ -193,11 +198,11 @@ def test_34q_random_circuit_tensor_cores_then_inverse(q):
     st = q.State(n, "c64")
     st.set_basis(x0)
     st.profile(True)
-    st.run(gates, fuse_k=5)
+    st.run(gates, fuse_k=k)
     assert abs(st.norm() - 1) < 1e-4
-    st.run(_inverse(gates), fuse_k=5)
+    st.run(_inverse(gates), fuse_k=k)
     prof = st.profile_read()
-    assert "fused_tensor_core" in prof and "tile_pass" not in prof, prof
+    assert FAMILY[k] in prof and "tile_pass" not in prof, prof
     t = st.tensor
     torch.cuda.synchronize()
     a0 = complex(t[x0].item())
