@@ -85,10 +85,11 @@ struct qsim_state {
 
 // Kernel families reported by qsim_profile_read.
 enum Fam { F_INIT, F_PAIR, F_DIAG, F_DENSE, F_TILE, F_NORM, F_BITS, F_PROBS, F_GATHER, F_SAMPLE, F_FUSED_TC,
-           F_BATCH, F_FUSED_TC128, F_FUSED_TC6, F_PERM, F_COUNT };
+           F_BATCH, F_FUSED_TC128, F_FUSED_TC6, F_PERM, F_PHASE, F_COUNT };
 static const char *kFamName[F_COUNT] = {"init_basis", "pair_sweep", "diag_sweep", "dense_cuda_core", "tile_pass",
                                         "norm", "bit_probs", "probs", "gather", "sample", "fused_tensor_core",
-                                        "batch", "fused_tc_digits", "fused_tc_bf16x3", "interchange"};
+                                        "batch", "fused_tc_digits", "fused_tc_bf16x3", "interchange",
+                                        "phase_pass"};
 
 static cudaEvent_t take_event(qsim_state *h) {
     if (!h->pool.empty()) {
@@ -502,6 +503,12 @@ struct qsim_plan_s {
     std::vector<unsigned char> cmats;
     size_t cmat_stride = 0;
     void *d_cmats = nullptr;
+    // runs of commuting phase shifts among the dense blocks (complex64
+    // tensor-core plans): their tables, concatenated
+    std::vector<PhasePass> phases;
+    std::vector<uint32_t> phase_words;
+    std::vector<size_t> phase_off;  // word offset of each pass's tables
+    uint32_t *d_phase = nullptr;
     qsim_plan_stats stats{};
     // QSIM_MODE_AUTO: one candidate plan per tile size / fusion width; the
     // first runs time each candidate, later runs use the fastest
@@ -510,6 +517,19 @@ struct qsim_plan_s {
     int next = 0;
     int chosen = -1;
 };
+
+// Runs of at least this many commuting phase shifts over more than k qubits
+// may become one phase pass (planner.hpp, plan_fused_phases).
+constexpr int kPhaseRunMin = 24;
+
+static void gather_phase_tables(qsim_plan_s &P) {
+    P.phase_words.clear();
+    P.phase_off.clear();
+    for (const PhasePass &pp : P.phases) {
+        P.phase_off.push_back(P.phase_words.size());
+        P.phase_words.insert(P.phase_words.end(), pp.words.begin(), pp.words.end());
+    }
+}
 
 static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
                               qsim_plan_s &P) {
@@ -568,12 +588,18 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         P.stats.alg_flops = 0.0;
     }
     if (o.fuse_k == 6 && h->dt == QSIM_C64 && fused_tc6_supported(h->n)) {
-        // complex64 6-qubit blocks on the tensor cores (bf16 hi/mid/lo slices)
-        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+        // complex64 6-qubit blocks on the tensor cores (bf16 hi/mid/lo slices),
+        // long runs of phase shifts as phase passes
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, P.blocks, P.phases))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
+        gather_phase_tables(P);
         const size_t per = fused_tc6_b_bytes() / sizeof(float);
         P.bmats.resize(per * P.blocks.size());
         for (size_t b = 0; b < P.blocks.size(); b++) {
+            if (P.blocks[b].phase >= 0) {
+                P.stats.alg_flops += P.blocks[b].flops;
+                continue;
+            }
             TileGeom g;
             FusedMap fm;
             if (!fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm))
@@ -615,11 +641,18 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         return QSIM_OK;
     }
     if (o.fuse_k > 0) {
-        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+        // complex64 4- and 5-qubit blocks on the tensor cores (3xTF32), long
+        // runs of phase shifts as phase passes
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, P.blocks, P.phases))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
+        gather_phase_tables(P);
         const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
         P.bmats.resize(per * P.blocks.size());
         for (size_t b = 0; b < P.blocks.size(); b++) {
+            if (P.blocks[b].phase >= 0) {
+                P.stats.alg_flops += P.blocks[b].flops;
+                continue;
+            }
             TileGeom g;
             FusedMap fm;
             if (!fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm))
@@ -653,7 +686,25 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     return QSIM_OK;
 }
 
-static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *d_bmats, const void *d_cmats) {
+// a phase pass among the blocks (complex64 tensor-core plans)
+static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t *d_phase, int idx) {
+    const PhasePass &pp = P.phases[(size_t)idx];
+    PhaseMeta m{};
+    m.ntab = (int32_t)pp.ta.size();
+    for (size_t t = 0; t < pp.ta.size() && t < (size_t)kMaxPhaseTables; t++) {
+        m.ta[t] = pp.ta[t];
+        m.tb[t] = pp.tb[t];
+    }
+    const uint32_t *tabs = d_phase + P.phase_off[(size_t)idx];
+    CK(launch(h, F_PHASE, 2.0 * (double)state_bytes(h), 1,
+              [&] { return launch_phase_pass(h->amp, h->n, tabs, m, h->sm_count, h->stream); },
+              8.0 * std::ldexp(1.0, h->n)),
+       "phase pass");
+    return QSIM_OK;
+}
+
+static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *d_bmats, const void *d_cmats,
+                              const uint32_t *d_phase) {
     if (P.blocks.empty()) return QSIM_OK;
     const int k = P.blocks[0].k;
     if (P.cuda_core) {
@@ -669,6 +720,11 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
     if (P.tc6) {
         const size_t per = fused_tc6_b_bytes() / sizeof(float);
         for (size_t b = 0; b < P.blocks.size(); b++) {
+            if (P.blocks[b].phase >= 0) {
+                const qsim_status st = run_phase(h, P, d_phase, P.blocks[b].phase);
+                if (st != QSIM_OK) return st;
+                continue;
+            }
             TileGeom g;
             FusedMap fm;
             fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
@@ -700,6 +756,11 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
     }
     const size_t per = 2 * (size_t)(2 << k) * (size_t)(2 << k);
     for (size_t b = 0; b < P.blocks.size(); b++) {
+        if (P.blocks[b].phase >= 0) {
+            const qsim_status st = run_phase(h, P, d_phase, P.blocks[b].phase);
+            if (st != QSIM_OK) return st;
+            continue;
+        }
         TileGeom g;
         FusedMap fm;
         fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
@@ -714,7 +775,10 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
 static qsim_status run_built(qsim_state *h, const qsim_plan_s &P, const TileOp *d_ops, const TilePhase *d_phases) {
     if (!P.blocks.empty())
         return run_blocks(h, P, P.d_bmats ? P.d_bmats : static_cast<const float *>(h->d_dense),
-                          P.d_cmats ? P.d_cmats : h->d_dense);
+                          P.d_cmats ? P.d_cmats : h->d_dense,
+                          P.d_phase ? P.d_phase
+                                    : reinterpret_cast<const uint32_t *>(static_cast<const float *>(h->d_dense) +
+                                                                         P.bmats.size()));
     if (P.mode == QSIM_MODE_PERGATE) {
         for (const PGate &g : P.sweeps) {
             qsim_status st = sweep_gate(h, g);
@@ -731,13 +795,19 @@ qsim_status qsim_run_circuit(qsim_handle h, const qsim_gate *gates, size_t ng, c
     qsim_status st = build_plan(h, gates, ng, opts, P);
     if (st != QSIM_OK) return st;
     if (!P.blocks.empty()) {
+        // block matrices, then the phase passes' tables (right after them)
         const size_t bytes = P.cuda_core ? P.cmats.size() : P.bmats.size() * sizeof(float);
+        const size_t pbytes = P.phase_words.size() * sizeof(uint32_t);
         const void *src = P.cuda_core ? static_cast<const void *>(P.cmats.data()) : static_cast<const void *>(P.bmats.data());
-        st = ensure_dense(h, bytes);
+        st = ensure_dense(h, bytes + pbytes);
         if (st != QSIM_OK) return st;
         CK(cudaMemcpyAsync(h->d_dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "upload blocks");
+        if (pbytes)
+            CK(cudaMemcpyAsync(static_cast<unsigned char *>(h->d_dense) + bytes, P.phase_words.data(), pbytes,
+                               cudaMemcpyHostToDevice, h->stream),
+               "upload phase tables");
         CK(cudaStreamSynchronize(h->stream), "sync");  // the host copy dies with P
-        h->h2d += bytes;
+        h->h2d += bytes + pbytes;
         return run_built(h, P, nullptr, nullptr);
     }
     if (P.mode == QSIM_MODE_FUSED && !P.plan.ops.empty()) {
@@ -753,6 +823,7 @@ static void plan_release(qsim_plan_s *P) {
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     if (P->d_bmats) cudaFree(P->d_bmats);
     if (P->d_cmats) cudaFree(P->d_cmats);
+    if (P->d_phase) cudaFree(P->d_phase);
     if (P->d_ops) cudaFree(P->d_ops);
     if (P->d_phases) cudaFree(P->d_phases);
     delete P;
@@ -795,6 +866,14 @@ static qsim_status upload_plan(qsim_state *h, qsim_plan_s *P, qsim_plan_s *&out)
         if (e == cudaSuccess) e = cudaMemcpy(P->d_cmats, P->cmats.data(), P->cmats.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_fail(e, "upload fused blocks");
         else h->h2d += P->cmats.size();
+    }
+    if (st == QSIM_OK && !P->phase_words.empty()) {
+        cudaError_t e = cudaMalloc(&P->d_phase, P->phase_words.size() * sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_phase, P->phase_words.data(), P->phase_words.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload phase tables");
+        else h->h2d += P->phase_words.size() * sizeof(uint32_t);
     }
     if (st == QSIM_OK && !P->bmats.empty()) {
         cudaError_t e = cudaMalloc(&P->d_bmats, P->bmats.size() * sizeof(float));

@@ -1,0 +1,115 @@
+// k_phase.cu -- a run of commuting phase shifts (Eqs. NUM5 and COMM5: the
+// controlled phases of the QFT adders of Sec. V.A) as one pass over a
+// complex64 state.
+//
+// The phase of amplitude x is a sum of table entries, one table per chunk
+// pair (a, b) of the index bits (planner.hpp, PhasePass), in fixed-point
+// turns summed mod 2^32.  A warp takes rows of 1024 amplitudes: chunk 0 (bits
+// 0..4) is the lane, chunk 1 (bits 5..9) the step j of its loop, the higher
+// chunks are fixed for the row.  So the tables of two high chunks are read
+// once per row, those of chunk 0 with a high chunk once per row and lane, and
+// per amplitude only the tables of chunk 1 (the same word for the whole warp)
+// and the table of chunks 0 and 1 (consecutive words across the warp): no
+// bank conflicts.  The phase becomes e^(i 2 pi turns) through sincospif and
+// multiplies the amplitude in place: one read and one write of the state.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kPhThreads = 256;
+constexpr int kPhMaxUni = 8;  // tables of chunk 1 with chunk 1..7
+
+__global__ void __launch_bounds__(kPhThreads)
+    k_phase(float2 *__restrict__ a, uint64_t nrows, const uint32_t *__restrict__ tab, PhaseMeta m) {
+    extern __shared__ uint32_t s_tab[];  // m.ntab tables of kPhaseTableWords
+    __shared__ int8_t s_ta[kMaxPhaseTables], s_tb[kMaxPhaseTables];
+    const uint32_t nw = (uint32_t)m.ntab * kPhaseTableWords;
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) s_tab[w] = tab[w];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < kMaxPhaseTables; t++) {
+            s_ta[t] = m.ta[t];
+            s_tb[t] = m.tb[t];
+        }
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (kPhThreads / 32);
+    for (uint64_t row = (uint64_t)blockIdx.x * (kPhThreads / 32) + (threadIdx.x >> 5); row < nrows; row += warps) {
+        const uint64_t hi = row << (2 * kPhaseChunk);
+        auto chunk = [&](int c) { return (uint32_t)(hi >> (kPhaseChunk * c)) & 31u; };
+        // per row and lane: the tables without chunk 1; per step j: the
+        // offsets (row part) of the tables with chunk 1
+        uint32_t base = 0, nuni = 0, lan = 0xffffffffu;
+        uint32_t uoff[kPhMaxUni];
+#pragma unroll
+        for (int u = 0; u < kPhMaxUni; u++) uoff[u] = 0u;
+        for (int t = 0; t < m.ntab; t++) {
+            const int ca = s_ta[t], cb = s_tb[t];
+            const uint32_t tb0 = (uint32_t)t * kPhaseTableWords;
+            if (ca == 1 || (ca == 0 && cb == 1)) {
+                if (ca == 0) {
+                    lan = tb0;  // table of chunks 0 and 1: index lane + 32 j
+                } else {
+                    // chunk 1 with chunk cb >= 1: index j + 32 x_cb (j alone for cb = 1)
+                    const uint32_t o = tb0 + (cb == 1 ? 0u : 32u * chunk(cb));
+#pragma unroll
+                    for (int u = 0; u < kPhMaxUni; u++)
+                        if ((uint32_t)u == nuni) uoff[u] = o;
+                    nuni++;
+                }
+            } else if (ca == 0) {
+                base += s_tab[tb0 + lane + (cb == 0 ? 0u : 32u * chunk(cb))];
+            } else {
+                base += s_tab[tb0 + chunk(ca) + (ca == cb ? 0u : 32u * chunk(cb))];
+            }
+        }
+        float2 *ar = a + hi + lane;
+#pragma unroll 4
+        for (uint32_t j = 0; j < 32u; j++) {
+            uint32_t ph = base;
+#pragma unroll
+            for (int u = 0; u < kPhMaxUni; u++)
+                if ((uint32_t)u < nuni) ph += s_tab[uoff[u] + j];
+            if (lan != 0xffffffffu) ph += s_tab[lan + lane + 32u * j];
+            // 2 pi turns = pi (turns as a signed 32-bit fraction of 2^31)
+            float s, c;
+            sincospif((float)(int32_t)ph * 4.656612873077393e-10f, &s, &c);
+            const float2 v = ar[32u * j];
+            ar[32u * j] = make_float2(c * v.x - s * v.y, c * v.y + s * v.x);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_phase_pass(void *amp, int n, const uint32_t *tables, const PhaseMeta &m, int sm_count,
+                              cudaStream_t s) {
+    if (n < 2 * kPhaseChunk || m.ntab < 1 || m.ntab > kMaxPhaseTables) return cudaErrorInvalidValue;
+    int nuni = 0;
+    for (int t = 0; t < m.ntab; t++) {
+        if (m.ta[t] > m.tb[t] || (int)m.tb[t] * kPhaseChunk >= n) return cudaErrorInvalidValue;
+        if (m.ta[t] == 1) nuni++;
+    }
+    if (nuni > kPhMaxUni) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)m.ntab * kPhaseTableWords * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase, kPhThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t nrows = 1ull << (n - 2 * kPhaseChunk);
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    const uint64_t need = (nrows + kPhThreads / 32 - 1) / (kPhThreads / 32);
+    if (grid > need) grid = need;
+    k_phase<<<(unsigned)grid, kPhThreads, smem, s>>>(static_cast<float2 *>(amp), nrows, tables, m);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

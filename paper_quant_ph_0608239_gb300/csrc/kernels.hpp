@@ -222,6 +222,23 @@ int permute_tile_bits(int elem_bytes);
 cudaError_t launch_permute(void *amp, int elem_bytes, const TileGeom &g, const PermPairs &pp, uint32_t *err,
                            int sm_count, cudaStream_t s);
 
+// ------------------------------------------------------------ phase passes
+// A run of commuting phase shifts applied in one pass (k_phase.cu, complex64;
+// tables built by the planner, planner.hpp PhasePass): ntab tables of
+// kPhaseTableWords fixed-point turns, table t for the chunk pair (ta[t],
+// tb[t]), ta <= tb, chunk c = index bits kPhaseChunk c .. kPhaseChunk c + 4.
+constexpr int kPhaseChunk = 5;
+constexpr int kPhaseTableWords = 1 << (2 * kPhaseChunk);
+constexpr int kMaxPhaseTables = 36;  // chunk pairs of 8 chunks (n <= 40)
+struct PhaseMeta {
+    int32_t ntab;
+    int8_t ta[kMaxPhaseTables];
+    int8_t tb[kMaxPhaseTables];
+};
+// n >= 10; tables: device copy of ntab * kPhaseTableWords words.
+cudaError_t launch_phase_pass(void *amp, int n, const uint32_t *tables, const PhaseMeta &m, int sm_count,
+                              cudaStream_t s);
+
 // ------------------------------------------------------------ batches
 struct BatchCircuit {
     void *amp;            // complex64 state of the circuit

@@ -879,4 +879,122 @@ bool fused_geometry(int n, int k, const int *pos, TileGeom &g, FusedMap &fm) {
     return r == T - k;
 }
 
+bool phase_term(const PGate &g, uint32_t &turns, uint64_t &bits) {
+    if (g.kind == QSIM_GATE_SWAP || popc(g.cmask) > 1) return false;
+    const Mat2 &M = g.U;
+    if (M.u[2] != 0.0 || M.u[3] != 0.0 || M.u[4] != 0.0 || M.u[5] != 0.0) return false;
+    if (std::fabs(M.u[0] - 1.0) > 1e-15 || std::fabs(M.u[1]) > 1e-15) return false;
+    if (std::fabs(std::hypot(M.u[6], M.u[7]) - 1.0) > 1e-14) return false;
+    double t = std::atan2(M.u[7], M.u[6]) / (2.0 * M_PI);  // turns in (-1/2, 1/2]
+    if (t < 0.0) t += 1.0;
+    turns = (uint32_t)(uint64_t)std::llround(std::ldexp(t, 32));  // mod 2^32
+    bits = g.cmask | (1ull << g.t0);
+    return true;
+}
+
+namespace {
+
+// The tables of one run of phase shifts.
+void build_phase_pass(const std::vector<PGate> &run, PhasePass &pp) {
+    std::vector<int> slot(64 * 64, -1);
+    for (const PGate &g : run) {
+        uint32_t turns;
+        uint64_t bits;
+        phase_term(g, turns, bits);
+        int b[2], nb = 0;
+        for (uint64_t m = bits; m; m &= m - 1) b[nb++] = __builtin_ctzll(m);
+        const int ca = b[0] / kPhaseChunk, cb = (nb == 2 ? b[1] : b[0]) / kPhaseChunk;  // ca <= cb
+        int &t = slot[ca * 64 + cb];
+        if (t < 0) {
+            t = (int)pp.ta.size();
+            pp.ta.push_back((int8_t)ca);
+            pp.tb.push_back((int8_t)cb);
+            pp.words.resize(pp.words.size() + kPhaseTableWords, 0u);
+        }
+        uint32_t *w = pp.words.data() + (size_t)t * kPhaseTableWords;
+        // local bit masks within the chunks; entry index xa + 32 xb (xa when ca = cb)
+        uint32_t ma = 0, mb = 0;
+        for (int j = 0; j < nb; j++) {
+            if (b[j] / kPhaseChunk == ca) ma |= 1u << (b[j] % kPhaseChunk);
+            else mb |= 1u << (b[j] % kPhaseChunk);
+        }
+        const int span = ca == cb ? (1 << kPhaseChunk) : kPhaseTableWords;
+        for (int e = 0; e < span; e++) {
+            const uint32_t xa = (uint32_t)e & 31u, xb = (uint32_t)e >> kPhaseChunk;
+            if ((xa & ma) == ma && (xb & mb) == mb) w[e] += turns;
+        }
+        pp.gates++;
+    }
+}
+
+}  // namespace
+
+bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, std::vector<FusedBlock> &out,
+                       std::vector<PhasePass> &phases) {
+    std::vector<FusedBlock> plain;
+    if (!plan_fused(gates, n, k, plain)) return false;
+    // Runs: phase shifts are held back while the gates after them commute
+    // with them (none targets one of their bits); a gate that does not
+    // commute releases the whole held set before it -- as one run if it is
+    // long, else as ordinary gates.
+    std::vector<std::vector<PGate>> segs(1), runs;
+    std::vector<PGate> held;
+    uint64_t held_bits = 0;
+    auto release = [&]() {
+        if ((int)held.size() >= min_gates && popc(held_bits) > k) {
+            runs.push_back(held);
+            segs.emplace_back();
+        } else {
+            segs.back().insert(segs.back().end(), held.begin(), held.end());
+        }
+        held.clear();
+        held_bits = 0;
+    };
+    for (const PGate &g : gates) {
+        uint32_t turns;
+        uint64_t bits;
+        if (phase_term(g, turns, bits) && (int)runs.size() < 64) {
+            held.push_back(g);
+            held_bits |= bits;
+            continue;
+        }
+        uint64_t moved = 1ull << g.t0;  // the bits g changes (a diagonal g changes none)
+        if (g.kind == QSIM_GATE_SWAP) moved |= 1ull << g.t1;
+        else if (g.U.u[2] == 0.0 && g.U.u[3] == 0.0 && g.U.u[4] == 0.0 && g.U.u[5] == 0.0) moved = 0;
+        if (moved & held_bits) release();
+        segs.back().push_back(g);
+    }
+    release();
+    if (runs.empty() || (size_t)(n + kPhaseChunk - 1) / kPhaseChunk > 8) {
+        out = std::move(plain);
+        return true;
+    }
+    std::vector<FusedBlock> with;
+    std::vector<PhasePass> pps;
+    for (size_t s = 0; s < segs.size(); s++) {
+        std::vector<FusedBlock> part;
+        if (!plan_fused(segs[s], n, k, part)) return false;
+        for (FusedBlock &b : part) with.push_back(std::move(b));
+        if (s < runs.size()) {
+            PhasePass pp;
+            build_phase_pass(runs[s], pp);
+            FusedBlock mark;
+            mark.k = k;
+            for (int j = 0; j < 8; j++) mark.pos[j] = j < k ? j : 0;
+            mark.flops = 8.0 * std::ldexp(1.0, n);  // one complex product per amplitude
+            mark.phase = (int)pps.size();
+            with.push_back(std::move(mark));
+            pps.push_back(std::move(pp));
+        }
+    }
+    if (with.size() < plain.size()) {
+        out = std::move(with);
+        phases = std::move(pps);
+    } else {
+        out = std::move(plain);
+        phases.clear();
+    }
+    return true;
+}
+
 }  // namespace qsim

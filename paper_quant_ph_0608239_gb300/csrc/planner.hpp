@@ -117,8 +117,34 @@ struct FusedBlock {
     int pos[8];               // physical bits, bit j of U's index = pos[j]
     std::vector<double> U;    // 2^k x 2^k complex, row-major (re, im)
     double flops;             // algorithmic flops: 8 * 2^k per amplitude
+    int phase = -1;           // >= 0: not a dense block but phase pass number `phase` (PhasePass)
 };
 bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out);
+
+// Phase passes.  Phase shifts with up to one control, diag(1, e^(i phi)) on
+// a target with its control (Eqs. NUM5 and COMM5), commute with each other and
+// with every gate whose target is none of their bits.  A long run of them
+// (the controlled phases of the QFT adders between two registers, Sec. V.A)
+// spreads over many dense blocks but is one diagonal operator: the phase of
+// amplitude x is the sum over the gates whose bits are all 1 in x.  The index
+// bits are cut into chunks of kPhaseChunk bits (kernels.hpp); a gate's bits lie in one or
+// two chunks, so the sum is a sum of table entries, one table per chunk pair
+// (a, b) with a <= b, indexed by x_a + 32 x_b (x_a alone when a = b).  The
+// entries are fixed-point turns (phi / 2 pi times 2^32, summed mod 2^32).
+struct PhasePass {
+    std::vector<int8_t> ta, tb;    // chunk pair of table t, ta <= tb
+    std::vector<uint32_t> words;   // kPhaseTableWords per table
+    int gates = 0;
+};
+// The phase-shift gate's term (turns as fixed point, bit set); false if the
+// gate is not diag(1, e^(i phi)) with at most one control.
+bool phase_term(const PGate &g, uint32_t &turns, uint64_t &bits);
+// plan_fused, with every long run of commuting phase shifts (at least
+// min_gates of them over more than k qubits) taken out as a phase pass where
+// that gives fewer passes in all; blocks with phase >= 0 stand for
+// phases[phase].
+bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, std::vector<FusedBlock> &out,
+                       std::vector<PhasePass> &phases);
 
 // Tile geometry of a fused block on the tensor cores: T = k + 7 bits holding
 // the block's qubits; false if n is too small.

@@ -705,6 +705,57 @@ def test_fused_blocks_adder_exact(q):
     st.free()
 
 
+@pytest.mark.parametrize("k,m", [(4, 7), (5, 7), (6, 10)])
+def test_phase_pass_adder(q, k, m):
+    """The controlled phases between the adder's registers (Sec. V.A) as one
+    phase pass among the tensor-core blocks: the state against the oracle,
+    the sum bit-exact, and the pass in the launch profile."""
+    values = (37, 98)
+    n = 2 * m
+    gates = inputs.adder_circuit(values, m)
+    st = q.State(n, "c64")
+    st.set_basis(0)
+    st.profile(True)
+    st.run(gates, fuse_k=k)
+    prof = st.profile_read()
+    assert "phase_pass" in prof, prof
+    got = st.get_state()
+    ref = oracle.run(n, gates, x0=0)
+    assert err(got, ref) < TOL["c64"], err(got, ref)
+    assert int(np.argmax(np.abs(got))) == inputs.adder_expected_index(values, m)
+    plan = st.plan(gates, fuse_k=k)
+    st.set_basis(0)
+    plan.run()
+    assert err(st.get_state(), ref) < TOL["c64"]  # plans upload the tables themselves
+    plan.free()
+    st.free()
+
+
+@pytest.mark.parametrize("n", [12, 13, 22])
+def test_phase_pass_random_phases(q, n):
+    """A long run of controlled phases on random qubit pairs (every chunk
+    pair of the tables), Hadamards around it, on 4-, 5- and 6-qubit block
+    plans, against the oracle."""
+    rng = np.random.default_rng(n)
+    gates = [g1("H", t) for t in range(n)]
+    for _ in range(60):
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        gates.append(g1("R", a, (b,), (float(rng.uniform(0, 2 * np.pi)),)))
+    gates += [g1("R", int(t), (), (float(rng.uniform(0, 2 * np.pi)),)) for t in rng.choice(n, 6, replace=False)]
+    gates += [g1("H", t) for t in range(n)]
+    ref = oracle.run(n, gates, x0=0)
+    for k in (4, 5, 6):
+        if (k == 6 and n < 13) or (k < 6 and n < 12):
+            continue
+        st = q.State(n, "c64")
+        st.set_basis(0)
+        st.profile(True)
+        st.run(gates, fuse_k=k)
+        assert "phase_pass" in st.profile_read()
+        assert err(st.get_state(), ref) < TOL["c64"], (n, k)
+        st.free()
+
+
 # ------------------------------------------------------------- reductions
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [3, 9, 10, 16, 21])
