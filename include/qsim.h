@@ -122,6 +122,11 @@ typedef struct {
                            k = 5 on the tensor cores (exact bf16 digit slices), other
                            widths on the CUDA cores (FP64 for complex128).  A block may take a
                            gate past earlier gates on other qubits (they commute).
+                           On the complex64 tensor-core plans, a long run of commuting
+                           phase shifts (diag(1, e^{i phi}), at most one control: the
+                           controlled phases between the registers of a QFT adder)
+                           becomes one phase pass instead of spreading over blocks,
+                           where that gives fewer passes.
                            QSIM_EINVAL if a gate acts on more than fuse_k qubits
                            (controls included).  0 or -1: tile passes */
     int32_t max_swap;   /* most bit pairs exchanged per interchange pass; 0 = default */
