@@ -503,8 +503,8 @@ struct qsim_plan_s {
     std::vector<unsigned char> cmats;
     size_t cmat_stride = 0;
     void *d_cmats = nullptr;
-    // runs of commuting phase shifts among the dense blocks (complex64
-    // tensor-core plans): their tables, concatenated
+    // runs of commuting phase shifts among the dense blocks (tensor-core
+    // plans): their tables, concatenated
     std::vector<PhasePass> phases;
     std::vector<uint32_t> phase_words;
     std::vector<size_t> phase_off;  // word offset of each pass's tables
@@ -521,13 +521,25 @@ struct qsim_plan_s {
 // Runs of at least this many commuting phase shifts over more than k qubits
 // may become one phase pass (planner.hpp, plan_fused_phases).
 constexpr int kPhaseRunMin = 24;
+// complex128 phase passes hold 64-bit tables in shared memory: at most 24
+constexpr int kMaxPhaseTables128 = 24;
 
-static void gather_phase_tables(qsim_plan_s &P) {
+// The phase passes' tables for the device: complex64 passes take the top 32
+// bits of each 64-bit entry (rounded), complex128 ones the whole entry (two
+// 32-bit words, low first).
+static void gather_phase_tables(qsim_plan_s &P, bool wide) {
     P.phase_words.clear();
     P.phase_off.clear();
     for (const PhasePass &pp : P.phases) {
         P.phase_off.push_back(P.phase_words.size());
-        P.phase_words.insert(P.phase_words.end(), pp.words.begin(), pp.words.end());
+        for (uint64_t w : pp.words) {
+            if (wide) {
+                P.phase_words.push_back((uint32_t)w);
+                P.phase_words.push_back((uint32_t)(w >> 32));
+            } else {
+                P.phase_words.push_back((uint32_t)((w + (1ull << 31)) >> 32));
+            }
+        }
     }
 }
 
@@ -562,14 +574,20 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         return QSIM_OK;
     }
     if (o.fuse_k > 0 && h->dt == QSIM_C128 && fused_tc128_supported(o.fuse_k, h->n)) {
-        // complex128 blocks on the tensor cores (bf16 digit slices); a block
-        // the scheme cannot take exactly sends the whole plan to the CUDA cores
-        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+        // complex128 blocks on the tensor cores (bf16 digit slices) and phase
+        // passes; a block the scheme cannot take exactly sends the whole plan
+        // to the CUDA cores
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables128, P.blocks, P.phases))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
+        gather_phase_tables(P, true);
         const size_t per = fused_tc128_b_bytes() / sizeof(float);
         P.bmats.resize(per * P.blocks.size());
         bool ok = true;
         for (size_t b = 0; b < P.blocks.size() && ok; b++) {
+            if (P.blocks[b].phase >= 0) {
+                P.stats.alg_flops += P.blocks[b].flops;
+                continue;
+            }
             TileGeom g;
             FusedMap fm;
             ok = fused_geometry(h->n, o.fuse_k, P.blocks[b].pos, g, fm) &&
@@ -585,14 +603,17 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         }
         P.blocks.clear();
         P.bmats.clear();
+        P.phases.clear();
+        P.phase_words.clear();
+        P.phase_off.clear();
         P.stats.alg_flops = 0.0;
     }
     if (o.fuse_k == 6 && h->dt == QSIM_C64 && fused_tc6_supported(h->n)) {
         // complex64 6-qubit blocks on the tensor cores (bf16 hi/mid/lo slices),
         // long runs of phase shifts as phase passes
-        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, P.blocks, P.phases))
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
-        gather_phase_tables(P);
+        gather_phase_tables(P, false);
         const size_t per = fused_tc6_b_bytes() / sizeof(float);
         P.bmats.resize(per * P.blocks.size());
         for (size_t b = 0; b < P.blocks.size(); b++) {
@@ -643,9 +664,9 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     if (o.fuse_k > 0) {
         // complex64 4- and 5-qubit blocks on the tensor cores (3xTF32), long
         // runs of phase shifts as phase passes
-        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, P.blocks, P.phases))
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
-        gather_phase_tables(P);
+        gather_phase_tables(P, false);
         const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
         P.bmats.resize(per * P.blocks.size());
         for (size_t b = 0; b < P.blocks.size(); b++) {
@@ -686,7 +707,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     return QSIM_OK;
 }
 
-// a phase pass among the blocks (complex64 tensor-core plans)
+// a phase pass among the blocks (tensor-core plans, either precision)
 static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t *d_phase, int idx) {
     const PhasePass &pp = P.phases[(size_t)idx];
     PhaseMeta m{};
@@ -697,7 +718,11 @@ static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t
     }
     const uint32_t *tabs = d_phase + P.phase_off[(size_t)idx];
     CK(launch(h, F_PHASE, 2.0 * (double)state_bytes(h), 1,
-              [&] { return launch_phase_pass(h->amp, h->n, tabs, m, h->sm_count, h->stream); },
+              [&] {
+                  return h->dt == QSIM_C64 ? launch_phase_pass(h->amp, h->n, tabs, m, h->sm_count, h->stream)
+                                           : launch_phase_pass128(h->amp, h->n, reinterpret_cast<const uint64_t *>(tabs),
+                                                                  m, h->sm_count, h->stream);
+              },
               8.0 * std::ldexp(1.0, h->n)),
        "phase pass");
     return QSIM_OK;
@@ -739,12 +764,19 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
     if (P.tc128) {
         const size_t per = fused_tc128_b_bytes() / sizeof(float);
         for (size_t b = 0; b < P.blocks.size(); b++) {
+            if (P.blocks[b].phase >= 0) {
+                const qsim_status st = run_phase(h, P, d_phase, P.blocks[b].phase);
+                if (st != QSIM_OK) return st;
+                continue;
+            }
             TileGeom g;
             FusedMap fm;
             fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
             const uint16_t *bm = reinterpret_cast<const uint16_t *>(d_bmats + per * b);
-            // double-float form between the first and the last block
-            const bool first = b == 0, last = b + 1 == P.blocks.size();
+            // double-float form between the first and the last block of a
+            // stretch of blocks (phase passes read and write IEEE doubles)
+            const bool first = b == 0 || P.blocks[b - 1].phase >= 0;
+            const bool last = b + 1 == P.blocks.size() || P.blocks[b + 1].phase >= 0;
             CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
                       [&] {
                           return launch_fused_tc128(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream, first, last);

@@ -1,20 +1,22 @@
 // k_phase.cu -- a run of commuting phase shifts (Eqs. NUM5 and COMM5: the
-// controlled phases of the QFT adders of Sec. V.A) as one pass over a
-// complex64 state.
+// controlled phases of the QFT adders of Sec. V.A) as one pass over the
+// state, complex64 (k_phase) and complex128 (k_phase128).
 //
 // The phase of amplitude x is a sum of table entries, one table per chunk
 // pair (a, b) of the index bits (planner.hpp, PhasePass), in fixed-point
-// turns summed mod 2^32.  A warp takes rows of 1024 amplitudes: chunk 0 (bits
-// 0..4) is the lane, chunk 1 (bits 5..9) the step j of its loop, the higher
-// chunks are fixed for the row.  So the tables of two high chunks are read
+// turns summed mod 2^32 (complex64) or 2^64 (complex128).  A warp takes rows
+// of 1024 amplitudes: chunk 0 (bits 0..4) is the lane, chunk 1 (bits 5..9)
+// the step j of its loop, the higher chunks are fixed for the row.  So the tables of two high chunks are read
 // once per row, those of chunk 0 with a high chunk once per row and lane, and
 // per amplitude only the tables of chunk 1 (the same word for the whole warp)
 // and the table of chunks 0 and 1 (consecutive words across the warp): no
-// bank conflicts.  The phase becomes e^(i 2 pi turns) through sincospif and
-// multiplies the amplitude in place: one read and one write of the state.
+// bank conflicts.  The phase becomes e^(i 2 pi turns) (complex64 through
+// sincospif) and multiplies the amplitude in place: one read and one write of
+// the state.
 #include <cmath>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.hpp"
 
 namespace qsim {
@@ -86,7 +88,124 @@ __global__ void __launch_bounds__(kPhThreads)
     }
 }
 
+// complex128: 64-bit turns; the factor e^(2 pi i t) from a table of the
+// 1024 multiples of 2 pi / 1024 (double-float, computed at the start from
+// FP64 sincospi) times e^(i delta) for the remaining delta < 2 pi / 1024 as a
+// short Taylor series in double-float (terms past delta^7 below 1e-22); the
+// amplitude, an IEEE double pair, is multiplied in double-float.
+constexpr int kPhE = 1024;
+
+__global__ void __launch_bounds__(kPhThreads)
+    k_phase128(double2 *__restrict__ a, uint64_t nrows, const uint64_t *__restrict__ tab, PhaseMeta m) {
+    extern __shared__ __align__(16) unsigned char smem128[];
+    uint64_t *s_tab = reinterpret_cast<uint64_t *>(smem128);
+    float4 *s_e = reinterpret_cast<float4 *>(smem128 + (size_t)m.ntab * kPhaseTableWords * sizeof(uint64_t));
+    __shared__ int8_t s_ta[kMaxPhaseTables], s_tb[kMaxPhaseTables];
+    const uint32_t nw = (uint32_t)m.ntab * kPhaseTableWords;
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) s_tab[w] = tab[w];
+    for (int e = threadIdx.x; e < kPhE; e += blockDim.x) {
+        double sn, cs;
+        sincospi((double)e / (kPhE / 2), &sn, &cs);
+        const df c = df_from_double_rn(cs), sv = df_from_double_rn(sn);
+        s_e[e] = make_float4(c.h, c.l, sv.h, sv.l);
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < kMaxPhaseTables; t++) {
+            s_ta[t] = m.ta[t];
+            s_tb[t] = m.tb[t];
+        }
+    }
+    __syncthreads();
+    // 2 pi / 2^64 and 1/6 as double-floats
+    const double twopi = 6.283185307179586476925286766559;
+    const float kph = (float)twopi;
+    const df K = df{ldexpf(kph, -64), ldexpf((float)(twopi - (double)kph), -64)};
+    const float s6h = 1.0f / 6.0f;
+    const df SIXTH = df{s6h, (float)(1.0 / 6.0 - (double)s6h)};
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (kPhThreads / 32);
+    for (uint64_t row = (uint64_t)blockIdx.x * (kPhThreads / 32) + (threadIdx.x >> 5); row < nrows; row += warps) {
+        const uint64_t hi = row << (2 * kPhaseChunk);
+        auto chunk = [&](int c) { return (uint32_t)(hi >> (kPhaseChunk * c)) & 31u; };
+        uint64_t base = 0;
+        uint32_t nuni = 0, lan = 0xffffffffu;
+        uint32_t uoff[kPhMaxUni];
+#pragma unroll
+        for (int u = 0; u < kPhMaxUni; u++) uoff[u] = 0u;
+        for (int t = 0; t < m.ntab; t++) {
+            const int ca = s_ta[t], cb = s_tb[t];
+            const uint32_t tb0 = (uint32_t)t * kPhaseTableWords;
+            if (ca == 1 || (ca == 0 && cb == 1)) {
+                if (ca == 0) {
+                    lan = tb0;
+                } else {
+                    const uint32_t o = tb0 + (cb == 1 ? 0u : 32u * chunk(cb));
+#pragma unroll
+                    for (int u = 0; u < kPhMaxUni; u++)
+                        if ((uint32_t)u == nuni) uoff[u] = o;
+                    nuni++;
+                }
+            } else if (ca == 0) {
+                base += s_tab[tb0 + lane + (cb == 0 ? 0u : 32u * chunk(cb))];
+            } else {
+                base += s_tab[tb0 + chunk(ca) + (ca == cb ? 0u : 32u * chunk(cb))];
+            }
+        }
+        double2 *ar = a + hi + lane;
+#pragma unroll 2
+        for (uint32_t j = 0; j < 32u; j++) {
+            uint64_t ph = base;
+#pragma unroll
+            for (int u = 0; u < kPhMaxUni; u++)
+                if ((uint32_t)u < nuni) ph += s_tab[uoff[u] + j];
+            if (lan != 0xffffffffu) ph += s_tab[lan + lane + 32u * j];
+            // t = ph / 2^64 = k / 1024 + r / 2^64, r < 2^54
+            const uint32_t k = (uint32_t)(ph >> 54);
+            const uint64_t r = ph & ((1ull << 54) - 1ull);
+            const df rr = quick_two_sum(ldexpf((float)(uint32_t)(r >> 30), 30), (float)(uint32_t)(r & 0x3fffffffu));
+            const df d = df_mul(rr, K);                   // delta
+            const df d2 = df_mul(d, d);
+            const float f2 = d2.h;
+            df cv = df_add(df{1.0f, 0.0f}, df{-0.5f * d2.h, -0.5f * d2.l});
+            cv = df_add(cv, df{f2 * f2 * (1.0f / 24.0f) - f2 * f2 * f2 * (1.0f / 720.0f), 0.0f});
+            const df d3 = df_mul(d2, d);
+            df sv = df_add(d, df_neg(df_mul(d3, SIXTH)));
+            sv = df_add(sv, df{d3.h * f2 * (1.0f / 120.0f) - d3.h * f2 * f2 * (1.0f / 5040.0f), 0.0f});
+            const float4 e4 = s_e[k];
+            const dcx f = dcx_mul(dcx{df{e4.x, e4.y}, df{e4.z, e4.w}}, dcx{cv, sv});
+            const double2 v = ar[32u * j];
+            const dcx w = dcx_mul(f, dcx{df_from_double(v.x), df_from_double(v.y)});
+            ar[32u * j] = make_double2(df_to_double(w.re), df_to_double(w.im));
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_phase_pass128(void *amp, int n, const uint64_t *tables, const PhaseMeta &m, int sm_count,
+                                 cudaStream_t s) {
+    if (n < 2 * kPhaseChunk || m.ntab < 1 || m.ntab > 24) return cudaErrorInvalidValue;
+    int nuni = 0;
+    for (int t = 0; t < m.ntab; t++) {
+        if (m.ta[t] > m.tb[t] || (int)m.tb[t] * kPhaseChunk >= n) return cudaErrorInvalidValue;
+        if (m.ta[t] == 1) nuni++;
+    }
+    if (nuni > kPhMaxUni) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)m.ntab * kPhaseTableWords * sizeof(uint64_t) + kPhE * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_phase128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase128, kPhThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t nrows = 1ull << (n - 2 * kPhaseChunk);
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    const uint64_t need = (nrows + kPhThreads / 32 - 1) / (kPhThreads / 32);
+    if (grid > need) grid = need;
+    k_phase128<<<(unsigned)grid, kPhThreads, smem, s>>>(static_cast<double2 *>(amp), nrows, tables, m);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_phase_pass(void *amp, int n, const uint32_t *tables, const PhaseMeta &m, int sm_count,
                               cudaStream_t s) {

@@ -238,6 +238,10 @@ struct PhaseMeta {
 // n >= 10; tables: device copy of ntab * kPhaseTableWords words.
 cudaError_t launch_phase_pass(void *amp, int n, const uint32_t *tables, const PhaseMeta &m, int sm_count,
                               cudaStream_t s);
+// complex128 (IEEE doubles in and out, double-float arithmetic): 64-bit
+// turns, ntab <= 24.
+cudaError_t launch_phase_pass128(void *amp, int n, const uint64_t *tables, const PhaseMeta &m, int sm_count,
+                                 cudaStream_t s);
 
 // ------------------------------------------------------------ batches
 struct BatchCircuit {

@@ -879,15 +879,15 @@ bool fused_geometry(int n, int k, const int *pos, TileGeom &g, FusedMap &fm) {
     return r == T - k;
 }
 
-bool phase_term(const PGate &g, uint32_t &turns, uint64_t &bits) {
+bool phase_term(const PGate &g, uint64_t &turns, uint64_t &bits) {
     if (g.kind == QSIM_GATE_SWAP || popc(g.cmask) > 1) return false;
     const Mat2 &M = g.U;
     if (M.u[2] != 0.0 || M.u[3] != 0.0 || M.u[4] != 0.0 || M.u[5] != 0.0) return false;
     if (std::fabs(M.u[0] - 1.0) > 1e-15 || std::fabs(M.u[1]) > 1e-15) return false;
     if (std::fabs(std::hypot(M.u[6], M.u[7]) - 1.0) > 1e-14) return false;
-    double t = std::atan2(M.u[7], M.u[6]) / (2.0 * M_PI);  // turns in (-1/2, 1/2]
-    if (t < 0.0) t += 1.0;
-    turns = (uint32_t)(uint64_t)std::llround(std::ldexp(t, 32));  // mod 2^32
+    // turns in (-1/2, 1/2] as a signed 64-bit fraction of 2^63, kept mod 2^64
+    const double v = std::ldexp(std::atan2(M.u[7], M.u[6]) / M_PI, 63);
+    turns = v >= 9223372036854775808.0 ? (1ull << 63) : (uint64_t)(int64_t)std::llround(v);  // pi == -pi
     bits = g.cmask | (1ull << g.t0);
     return true;
 }
@@ -898,8 +898,7 @@ namespace {
 void build_phase_pass(const std::vector<PGate> &run, PhasePass &pp) {
     std::vector<int> slot(64 * 64, -1);
     for (const PGate &g : run) {
-        uint32_t turns;
-        uint64_t bits;
+        uint64_t turns, bits;
         phase_term(g, turns, bits);
         int b[2], nb = 0;
         for (uint64_t m = bits; m; m &= m - 1) b[nb++] = __builtin_ctzll(m);
@@ -909,9 +908,9 @@ void build_phase_pass(const std::vector<PGate> &run, PhasePass &pp) {
             t = (int)pp.ta.size();
             pp.ta.push_back((int8_t)ca);
             pp.tb.push_back((int8_t)cb);
-            pp.words.resize(pp.words.size() + kPhaseTableWords, 0u);
+            pp.words.resize(pp.words.size() + kPhaseTableWords, 0ull);
         }
-        uint32_t *w = pp.words.data() + (size_t)t * kPhaseTableWords;
+        uint64_t *w = pp.words.data() + (size_t)t * kPhaseTableWords;
         // local bit masks within the chunks; entry index xa + 32 xb (xa when ca = cb)
         uint32_t ma = 0, mb = 0;
         for (int j = 0; j < nb; j++) {
@@ -929,8 +928,25 @@ void build_phase_pass(const std::vector<PGate> &run, PhasePass &pp) {
 
 }  // namespace
 
-bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, std::vector<FusedBlock> &out,
-                       std::vector<PhasePass> &phases) {
+// chunk pairs of a set of phase terms
+static int phase_tables(const std::vector<PGate> &run) {
+    std::vector<char> seen(64 * 64, 0);
+    int c = 0;
+    for (const PGate &g : run) {
+        uint64_t turns, bits;
+        phase_term(g, turns, bits);
+        const int lo = __builtin_ctzll(bits), hi = 63 - __builtin_clzll(bits);
+        char &s = seen[(lo / kPhaseChunk) * 64 + hi / kPhaseChunk];
+        if (!s) {
+            s = 1;
+            c++;
+        }
+    }
+    return c;
+}
+
+bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, int max_tables,
+                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases) {
     std::vector<FusedBlock> plain;
     if (!plan_fused(gates, n, k, plain)) return false;
     // Runs: phase shifts are held back while the gates after them commute
@@ -941,7 +957,7 @@ bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_ga
     std::vector<PGate> held;
     uint64_t held_bits = 0;
     auto release = [&]() {
-        if ((int)held.size() >= min_gates && popc(held_bits) > k) {
+        if ((int)held.size() >= min_gates && popc(held_bits) > k && phase_tables(held) <= max_tables) {
             runs.push_back(held);
             segs.emplace_back();
         } else {
@@ -951,8 +967,7 @@ bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_ga
         held_bits = 0;
     };
     for (const PGate &g : gates) {
-        uint32_t turns;
-        uint64_t bits;
+        uint64_t turns, bits;
         if (phase_term(g, turns, bits) && (int)runs.size() < 64) {
             held.push_back(g);
             held_bits |= bits;

@@ -130,21 +130,22 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
 // bits are cut into chunks of kPhaseChunk bits (kernels.hpp); a gate's bits lie in one or
 // two chunks, so the sum is a sum of table entries, one table per chunk pair
 // (a, b) with a <= b, indexed by x_a + 32 x_b (x_a alone when a = b).  The
-// entries are fixed-point turns (phi / 2 pi times 2^32, summed mod 2^32).
+// entries are fixed-point turns (phi / 2 pi times 2^64, summed mod 2^64;
+// complex64 passes use their top 32 bits).
 struct PhasePass {
     std::vector<int8_t> ta, tb;    // chunk pair of table t, ta <= tb
-    std::vector<uint32_t> words;   // kPhaseTableWords per table
+    std::vector<uint64_t> words;   // kPhaseTableWords per table
     int gates = 0;
 };
 // The phase-shift gate's term (turns as fixed point, bit set); false if the
 // gate is not diag(1, e^(i phi)) with at most one control.
-bool phase_term(const PGate &g, uint32_t &turns, uint64_t &bits);
+bool phase_term(const PGate &g, uint64_t &turns, uint64_t &bits);
 // plan_fused, with every long run of commuting phase shifts (at least
-// min_gates of them over more than k qubits) taken out as a phase pass where
-// that gives fewer passes in all; blocks with phase >= 0 stand for
-// phases[phase].
-bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, std::vector<FusedBlock> &out,
-                       std::vector<PhasePass> &phases);
+// min_gates of them over more than k qubits, on at most max_tables chunk
+// pairs) taken out as a phase pass where that gives fewer passes in all;
+// blocks with phase >= 0 stand for phases[phase].
+bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, int max_tables,
+                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases);
 
 // Tile geometry of a fused block on the tensor cores: T = k + 7 bits holding
 // the block's qubits; false if n is too small.

@@ -731,11 +731,33 @@ def test_phase_pass_adder(q, k, m):
     st.free()
 
 
+@pytest.mark.parametrize("m", [7, 11])
+def test_phase_pass_adder_c128(q, m):
+    """complex128 phase pass (64-bit turns) between the 5-qubit tensor-core
+    blocks of the adder (Sec. V.A): the blocks around it hand IEEE doubles
+    to it and take them back; within the complex128 tolerance, the sum
+    bit-exact."""
+    values = (37, 98)
+    n = 2 * m
+    gates = inputs.adder_circuit(values, m)
+    st = q.State(n, "c128")
+    st.set_basis(0)
+    st.profile(True)
+    st.run(gates, fuse_k=5)
+    prof = st.profile_read()
+    assert "phase_pass" in prof, prof
+    got = st.get_state()
+    ref = oracle.run(n, gates, x0=0)
+    assert err(got, ref) < TOL["c128"], err(got, ref)
+    assert int(np.argmax(np.abs(got))) == inputs.adder_expected_index(values, m)
+    st.free()
+
+
 @pytest.mark.parametrize("n", [12, 13, 22])
 def test_phase_pass_random_phases(q, n):
     """A long run of controlled phases on random qubit pairs (every chunk
     pair of the tables), Hadamards around it, on 4-, 5- and 6-qubit block
-    plans, against the oracle."""
+    plans (complex64) and 5-qubit ones (complex128), against the oracle."""
     rng = np.random.default_rng(n)
     gates = [g1("H", t) for t in range(n)]
     for _ in range(60):
@@ -744,15 +766,15 @@ def test_phase_pass_random_phases(q, n):
     gates += [g1("R", int(t), (), (float(rng.uniform(0, 2 * np.pi)),)) for t in rng.choice(n, 6, replace=False)]
     gates += [g1("H", t) for t in range(n)]
     ref = oracle.run(n, gates, x0=0)
-    for k in (4, 5, 6):
+    for dt, k in (("c64", 4), ("c64", 5), ("c64", 6), ("c128", 5)):
         if (k == 6 and n < 13) or (k < 6 and n < 12):
             continue
-        st = q.State(n, "c64")
+        st = q.State(n, dt)
         st.set_basis(0)
         st.profile(True)
         st.run(gates, fuse_k=k)
         assert "phase_pass" in st.profile_read()
-        assert err(st.get_state(), ref) < TOL["c64"], (n, k)
+        assert err(st.get_state(), ref) < TOL[dt], (n, dt, k, err(st.get_state(), ref))
         st.free()
 
 

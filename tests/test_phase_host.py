@@ -6,7 +6,8 @@ as their FP64 matrices, phase passes as sums of the planner's tables (fixed-
 point turns mod 2^32, the evaluation of k_phase.cu).  Against the oracle:
 
   * the QFT register adder of Sec. V.A (the controlled phases between the two
-    registers become one phase pass, and the plan has fewer passes in all);
+    registers become one phase pass, and the plan has fewer passes in all),
+    with the complex64 (32-bit turns) and complex128 (64-bit turns) tables;
   * the adder's phase shifts interleaved with Hadamards on other qubits and
     controlled NOTs whose controls share their bits (they commute);
   * circuits without long runs keep the plain block plan.
@@ -46,9 +47,9 @@ def emu():
     shutil.rmtree(d, ignore_errors=True)
 
 
-def run_emu(exe, n, k, gates, psi, minrun=24):
+def run_emu(exe, n, k, gates, psi, minrun=24, wide=False):
     arr = gate_array(gates)
-    blob = struct.pack("<iiiQ", n, k, minrun, len(gates)) + bytes(memoryview(arr).cast("B"))[:len(gates) * ctypes.sizeof(arr._type_)]
+    blob = struct.pack("<iiiiQ", n, k, minrun, int(wide), len(gates)) + bytes(memoryview(arr).cast("B"))[:len(gates) * ctypes.sizeof(arr._type_)]
     blob += np.ascontiguousarray(psi, dtype=np.complex128).tobytes()
     r = subprocess.run([exe], input=blob, capture_output=True)
     assert r.returncode == 0, (r.returncode, r.stderr.decode())
@@ -57,17 +58,19 @@ def run_emu(exe, n, k, gates, psi, minrun=24):
                          struct.unpack("<4i", r.stdout[16 << n:])))
 
 
-@pytest.mark.parametrize("k,m", [(5, 7), (6, 10)])
-def test_adder_phase_pass(emu, k, m):
+@pytest.mark.parametrize("k,m,wide", [(5, 7, False), (6, 10, False), (5, 7, True), (5, 10, True)])
+def test_adder_phase_pass(emu, k, m, wide):
     vals = (37, 98)
     gates = inputs.adder_circuit(vals, m)
     n = 2 * m
     psi = oracle.basis(n, 0)
-    got, st = run_emu(emu, n, k, gates, psi)
+    got, st = run_emu(emu, n, k, gates, psi, wide=wide)
     ref = oracle.run(n, gates, x0=0)
     assert st["phase_passes"] >= 1 and st["phase_gates"] >= m * (m + 1) // 2, st
     assert st["blocks"] < st["plain_blocks"], st
-    assert np.max(np.abs(got - ref)) < 1e-8
+    # 64-bit turns (complex128): within the complex128 tolerance; 32-bit
+    # turns: within 2^-32 turns per table entry
+    assert np.max(np.abs(got - ref)) < (1e-13 if wide else 1e-8)
     assert int(np.argmax(np.abs(got))) == inputs.adder_expected_index(vals, m)
 
 
