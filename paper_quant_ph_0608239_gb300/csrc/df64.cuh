@@ -217,6 +217,66 @@ DF_HD dcx dcx_rmul2(const df &u, const dcx &a, const df &v, const dcx &b) {
     return dcx{df_dot<2>(xr, yr), df_dot<2>(xr, yi)};
 }
 
+// ---- squared magnitudes (probabilities) ----------------------------------
+DF_HD float df_fmaxf(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return fmaxf(a, b);
+#else
+    return std::fmax(a, b);
+#endif
+}
+DF_HD float df_fminf(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return fminf(a, b);
+#else
+    return std::fmin(a, b);
+#endif
+}
+// a + b for a, b >= 0: the heads' exact sum by Fast2Sum with the operands
+// ordered by size, the tails added in float, then renormalised.
+DF_HD df df_add_pos(df a, df b) {
+    const float s = a.h + b.h;
+    const float big = df_fmaxf(a.h, b.h), sm = df_fminf(a.h, b.h);
+    const float t = (sm - (s - big)) + (a.l + b.l);
+    const float h = s + t;
+    return df{h, t - (h - s)};
+}
+// True when |d| >= 2 (biased exponent >= 1024): df_sqmag's fast split does
+// not cover such values.
+DF_HD bool df_mag_ge2(double d) { return ((uint32_t)(df_bits64(d) >> 32) & 0x40000000u) != 0u; }
+// |d| = h + r for |d| < 2: h = the top 24 significand bits (truncated), r2 =
+// 2 r with r from the remaining 29 bits rounded to a float; |d| < 2^-126 (and
+// zero) gives (0, 0).  Integer operations and one int-to-float conversion.
+DF_HD void df_split_mag(double d, float &h, float &r2) {
+    const uint64_t b = df_bits64(d);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    // bits 31..23: the low 9 bits of the biased exponent e, which are e - 512
+    // for 512 <= e < 1024; below them the top 23 significand bits
+    const uint32_t x = (hi << 3) | (lo >> 29);
+    const uint32_t hb = x - 0xC0000000u;  // (e - 896) << 23 | significand
+    const bool tiny = (hi & 0x7ff00000u) < (897u << 20);
+    const float hexp = df_ffrom(hb & 0x7f800000u);  // 2^(e - 1023)
+    h = tiny ? 0.0f : df_ffrom(hb);
+    r2 = tiny ? 0.0f : (float)(lo & 0x1fffffffu) * hexp * 0x1p-51f;
+}
+// re^2 + im^2 as a double-float for |re|, |im| < 2 (df_mag_ge2 false):
+// (h + r)^2 = h^2 + r2 (h + r2 / 4) per component, the two h^2 as exact
+// products, their sum by ordered Fast2Sum, every smaller term in float.
+// Relative error below 2^-44.
+DF_HD df df_sqmag(double re, double im) {
+    float hr, rr2, hi, ri2;
+    df_split_mag(re, hr, rr2);
+    df_split_mag(im, hi, ri2);
+    const float p1 = hr * hr, e1 = df_fma(hr, hr, -p1);
+    const float p2 = hi * hi, e2 = df_fma(hi, hi, -p2);
+    const float s = p1 + p2;
+    const float big = df_fmaxf(p1, p2), sm = df_fminf(p1, p2);
+    float c = (e1 + e2) + (sm - (s - big));
+    c = df_fma(rr2, df_fma(0.25f, rr2, hr), c);
+    c = df_fma(ri2, df_fma(0.25f, ri2, hi), c);
+    const float h = s + c;
+    return df{h, c - (h - s)};
+}
 DF_HD df df_from_double_rn(double d) {
     // for constants built on the host: hi = nearest float, lo = nearest float of the rest
     const float h = (float)d;

@@ -6,12 +6,14 @@
 // amplitudes are summed in FP32 before they enter an FP64 accumulator (the
 // FP32 partial sums of non-negative terms carry at most 16 ulp of relative
 // error, far below the precision of the amplitudes themselves); complex128
-// states are summed in FP64 throughout.
+// states are summed in FP64, except the per-bit marginals for n >= 13, whose
+// inner sums run in double-float (k_bits_partial_df).
 //
 // The partial sums of each block go to a caller-provided scratch buffer in
 // global memory and a second kernel adds them up.
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.hpp"
 
 namespace qsim {
@@ -123,6 +125,99 @@ __global__ void __launch_bounds__(kRedThreads) k_bits_partial(const amp_t<R> *__
             const double r = block_sum(acc[b], sh);
             if (threadIdx.x == 0) partial[(size_t)blockIdx.x * n + b] = r;
         }
+    }
+}
+
+// Per-bit marginals of a complex128 state, n >= kGroupBits, with no FP64 in
+// the inner loop (GB300 issues FP64 at about 2 instructions per clock per SM,
+// fewer than reading the state at full bandwidth needs).  A warp takes groups
+// of 8192 consecutive amplitudes: lane l holds amplitudes l + 32 j, j < 256,
+// read in chunks of 8 (j = 8 c + k), so bits 0..4 of an index are the lane,
+// bits 5..7 are k, bits 8..12 are the chunk c and the higher bits are the
+// group's.  Each |a|^2 is a double-float from the IEEE bits (df_sqmag,
+// relative error below 2^-44; a chunk holding a magnitude >= 2 takes the FP64
+// branch).  Per group and lane the sums run in double-float over at most 32
+// terms: per k (bits 5..7), per set bit of c (bits 8..12, from the chunk
+// sums) and the group total.  At the end of the group they are added to FP64
+// accumulators; the group total, summed over the warp, is added by lane
+// b - 13 to bit b's accumulator when bit b of the group index is set.
+constexpr int kGroupBits = 13;
+
+__device__ __forceinline__ double df_sum_d(df x) { return (double)x.h + (double)x.l; }  // exact
+
+__global__ void __launch_bounds__(kRedThreads) k_bits_partial_df(const double2 *__restrict__ a, int n,
+                                                                  double *__restrict__ partial) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31;
+    double A[8], B[5], L = 0.0, H = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) A[k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 5; i++) B[i] = 0.0;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t ngroups = 1ull << (n - kGroupBits);
+    for (uint64_t gi = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < ngroups; gi += warps) {
+        const double2 *p = a + (gi << kGroupBits) + lane;
+        df ak[8], bc[5], tg{0.0f, 0.0f};
+#pragma unroll
+        for (int k = 0; k < 8; k++) ak[k] = df{0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 5; i++) bc[i] = df{0.0f, 0.0f};
+#pragma unroll 2
+        for (int c = 0; c < 32; c++) {
+            double2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = p[32 * (8 * c + k)];
+            uint32_t any = 0;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                any |= (uint32_t)(df_bits64(v[k].x) >> 32) | (uint32_t)(df_bits64(v[k].y) >> 32);
+            df q[8];
+            if (__any_sync(0xffffffffu, (any & 0x40000000u) != 0u)) {
+                // a magnitude >= 2 in the chunk: the squares in FP64
+#pragma unroll
+                for (int k = 0; k < 8; k++) q[k] = df_from_double(fma(v[k].x, v[k].x, v[k].y * v[k].y));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) q[k] = df_sqmag(v[k].x, v[k].y);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) ak[k] = df_add_pos(ak[k], q[k]);
+            const df cs = df_add_pos(df_add_pos(df_add_pos(q[0], q[1]), df_add_pos(q[2], q[3])),
+                                     df_add_pos(df_add_pos(q[4], q[5]), df_add_pos(q[6], q[7])));
+            tg = df_add_pos(tg, cs);
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+                if ((c >> i) & 1) bc[i] = df_add_pos(bc[i], cs);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) A[k] += df_sum_d(ak[k]);
+#pragma unroll
+        for (int i = 0; i < 5; i++) B[i] += df_sum_d(bc[i]);
+        const double t = df_sum_d(tg);
+        L += t;
+        const double G = warp_sum(t);
+        if (lane < n - kGroupBits && ((gi >> lane) & 1ull)) H += G;
+    }
+    for (int b = 0; b < n; b++) {  // uniform across the block
+        double v;
+        if (b < 5) {
+            v = ((lane >> b) & 1) ? L : 0.0;
+        } else if (b < 8) {
+            v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                if ((k >> (b - 5)) & 1) v += A[k];
+        } else if (b < kGroupBits) {
+            v = 0.0;
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+                if (i == b - 8) v = B[i];
+        } else {
+            v = lane == b - kGroupBits ? H : 0.0;
+        }
+        const double r = block_sum(v, sh);
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * n + b] = r;
     }
 }
 
@@ -302,6 +397,13 @@ cudaError_t launch_bit_probs(const void *amp, int dt, int n, double *scratch, do
             k_bits_small<float><<<1, 256, 0, s>>>(static_cast<const float2 *>(amp), n, dout);
         else
             k_bits_small<double><<<1, 256, 0, s>>>(static_cast<const double2 *>(amp), n, dout);
+        return cudaGetLastError();
+    }
+    if (dt != 0 && n >= kGroupBits) {
+        uint64_t blocks = ((1ull << (n - kGroupBits)) + 7) / 8;
+        if (blocks > (uint64_t)kRedBlocks) blocks = kRedBlocks;
+        k_bits_partial_df<<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const double2 *>(amp), n, scratch);
+        k_sum_columns<<<1, 256, 0, s>>>(scratch, (int)blocks, n, n, dout);
         return cudaGetLastError();
     }
     uint64_t nch = 1ull << (n - kChunkBits);

@@ -108,3 +108,75 @@ def test_double_float_conversions_and_arithmetic():
     bad, split, join, dot = int(out[0]), float(out[1]), float(out[2]), float(out[3])
     assert bad == 0, out
     assert split <= 2.0 ** -47 and join <= 1.0 and dot <= 2.0 ** -44
+
+
+SQMAG_DRIVER = r'''
+#include <cstdio>
+#include <cmath>
+#include <random>
+#include "df64.cuh"
+using namespace qsim;
+static long double ld(df x) { return (long double)x.h + (long double)x.l; }
+int main() {
+    std::mt19937_64 g(777);
+    std::uniform_real_distribution<double> U(-1.0, 1.0), E(-140.0, 1.0);
+    int bad = 0;
+    double worst = 0, worst_add = 0;
+    for (int i = 0; i < 400000; i++) {
+        double re = U(g) * std::ldexp(1.0, (int)E(g)), im = U(g) * std::ldexp(1.0, (int)E(g));
+        if (i % 53 == 0) re = 0.0;
+        if (i % 71 == 0) im = -0.0;
+        if (i % 89 == 0) im = std::ldexp(U(g), -1000);  // far below the float range
+        if (i % 101 == 0) re = std::nextafter(2.0, 0.0);  // the largest fast-path magnitude
+        if (df_mag_ge2(re) || df_mag_ge2(im)) { bad++; continue; }
+        const df p = df_sqmag(re, im);
+        const long double ex = (long double)re * re + (long double)im * im;
+        const long double err = fabsl(ld(p) - ex);
+        // relative 2^-44, plus 2^-120 absolute where the squares leave the float range
+        if ((double)err > std::ldexp((double)ex, -44) + std::ldexp(1.0, -120)) bad++;
+        if (ex > std::ldexp(1.0, -100) && (double)(err / ex) > worst) worst = (double)(err / ex);
+        if (std::fabs(p.l) > std::fabs(p.h) * std::ldexp(1.0, -23)) bad++;
+        if (p.h < 0.0f) bad++;
+    }
+    // the magnitude test of the fast split
+    const double big[] = {2.0, -2.0, 3.5, 1e300, -1e20};
+    for (double d : big) if (!df_mag_ge2(d)) bad++;
+    const double small[] = {0.0, -0.0, 1.0, -1.999, 1e-300, std::nextafter(2.0, 0.0)};
+    for (double d : small) if (df_mag_ge2(d)) bad++;
+    // sums of non-negative double-floats: 32 terms of mixed sizes
+    for (int i = 0; i < 50000; i++) {
+        df s{0.0f, 0.0f};
+        long double ex = 0;
+        for (int k = 0; k < 32; k++) {
+            const double v = std::fabs(U(g)) * std::ldexp(1.0, (int)(E(g) / 8));
+            const df t = df_sqmag(v, 0.0);
+            s = df_add_pos(s, t);
+            ex += ld(t);
+        }
+        const double rel = (double)(fabsl(ld(s) - ex) / ex);
+        if (rel > worst_add) worst_add = rel;
+        if (rel > 32 * std::ldexp(1.0, -47)) bad++;
+        if (std::fabs(s.l) > std::fabs(s.h) * std::ldexp(1.0, -23)) bad++;
+    }
+    std::printf("%d %.3e %.3e\n", bad, worst, worst_add);
+    return 0;
+}
+'''
+
+
+def test_squared_magnitudes_and_positive_sums():
+    """The complex128 marginals' arithmetic (k_reduce.cu): re^2 + im^2 as a
+    double-float from the IEEE bits (relative error <= 2^-44), the |d| >= 2
+    test that sends values to the FP64 branch, and sums of non-negative
+    double-floats (32 terms within 32 * 2^-47), against long double."""
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "sq.cpp")
+        exe = os.path.join(tmp, "sq")
+        open(src, "w").write(SQMAG_DRIVER)
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off",
+                               "-I", os.path.join(ROOT, "paper_quant_ph_0608239_gb300", "csrc"),
+                               "-o", exe, src])
+        out = subprocess.check_output([exe]).decode().split()
+    bad, worst, worst_add = int(out[0]), float(out[1]), float(out[2])
+    assert bad == 0, out
+    assert worst <= 2.0 ** -44 and worst_add <= 32 * 2.0 ** -47, out

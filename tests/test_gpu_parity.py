@@ -780,7 +780,7 @@ def test_phase_pass_random_phases(q, n):
 
 # ------------------------------------------------------------- reductions
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("n", [3, 9, 10, 16, 21])
+@pytest.mark.parametrize("n", [3, 9, 10, 13, 16, 21])
 def test_reductions(q, dt, n):
     psi = rand_state(n, 11 + n)
     st = q.State(n, dt)
@@ -790,6 +790,28 @@ def test_reductions(q, dt, n):
     assert abs(st.norm() - oracle.norm(a, n)) < tol
     np.testing.assert_allclose(st.qubit_probs(), oracle.qubit_probs(a, n), atol=tol)
     np.testing.assert_allclose(st.probs(), oracle.probs(a, n), atol=tol * 1e-3, rtol=1e-6 if dt == "c64" else 1e-12)
+    st.free()
+
+
+@pytest.mark.parametrize("n", [13, 15, 20])
+def test_bit_marginals_c128_wide_magnitudes(q, n):
+    """complex128 per-bit marginals (the double-float reduction for n >= 13)
+    on a state that is not normalised: exact zeros, magnitudes far below the
+    float range (1e-40, 1e-300), and chunks holding magnitudes >= 2 (the FP64
+    branch), against the oracle's FP64 sums, relative to the total."""
+    rng = np.random.default_rng(40 + n)
+    psi = rand_state(n, 90 + n)
+    D = 1 << n
+    psi[rng.choice(D, D // 4, replace=False)] = 0.0
+    psi[rng.choice(D, 64, replace=False)] *= 1e-40
+    psi[rng.choice(D, 64, replace=False)] = 1e-300 * (1 + 1j)
+    psi[rng.choice(D, 5, replace=False)] = 3.0 - 2.5j
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    got = st.qubit_probs()
+    ref = oracle.qubit_probs(psi, n)
+    tot = float(np.sum(np.abs(psi) ** 2))
+    assert np.max(np.abs(got - ref)) < 1e-13 * tot, (np.max(np.abs(got - ref)), tot)
     st.free()
 
 
