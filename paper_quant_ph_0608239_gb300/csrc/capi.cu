@@ -707,8 +707,11 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     return QSIM_OK;
 }
 
-// a phase pass among the blocks (tensor-core plans, either precision)
-static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t *d_phase, int idx) {
+// a phase pass among the blocks (tensor-core plans, either precision); a
+// complex128 pass reads and writes IEEE doubles only as the first / last
+// step of the plan, double-float form otherwise (as the blocks around it)
+static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t *d_phase, int idx,
+                             bool in_ieee = true, bool out_ieee = true) {
     const PhasePass &pp = P.phases[(size_t)idx];
     PhaseMeta m{};
     m.ntab = (int32_t)pp.ta.size();
@@ -721,7 +724,7 @@ static qsim_status run_phase(qsim_state *h, const qsim_plan_s &P, const uint32_t
               [&] {
                   return h->dt == QSIM_C64 ? launch_phase_pass(h->amp, h->n, tabs, m, h->sm_count, h->stream)
                                            : launch_phase_pass128(h->amp, h->n, reinterpret_cast<const uint64_t *>(tabs),
-                                                                  m, h->sm_count, h->stream);
+                                                                  m, h->sm_count, h->stream, in_ieee, out_ieee);
               },
               8.0 * std::ldexp(1.0, h->n)),
        "phase pass");
@@ -764,8 +767,12 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
     if (P.tc128) {
         const size_t per = fused_tc128_b_bytes() / sizeof(float);
         for (size_t b = 0; b < P.blocks.size(); b++) {
+            // double-float form between the first and the last step of the
+            // plan, blocks and phase passes alike
+            const bool first = b == 0;
+            const bool last = b + 1 == P.blocks.size();
             if (P.blocks[b].phase >= 0) {
-                const qsim_status st = run_phase(h, P, d_phase, P.blocks[b].phase);
+                const qsim_status st = run_phase(h, P, d_phase, P.blocks[b].phase, first, last);
                 if (st != QSIM_OK) return st;
                 continue;
             }
@@ -773,10 +780,6 @@ static qsim_status run_blocks(qsim_state *h, const qsim_plan_s &P, const float *
             FusedMap fm;
             fused_geometry(h->n, k, P.blocks[b].pos, g, fm);
             const uint16_t *bm = reinterpret_cast<const uint16_t *>(d_bmats + per * b);
-            // double-float form between the first and the last block of a
-            // stretch of blocks (phase passes read and write IEEE doubles)
-            const bool first = b == 0 || P.blocks[b - 1].phase >= 0;
-            const bool last = b + 1 == P.blocks.size() || P.blocks[b + 1].phase >= 0;
             CK(launch(h, F_FUSED_TC128, 2.0 * (double)state_bytes(h), 1,
                       [&] {
                           return launch_fused_tc128(h->amp, g, fm, bm, h->d_err, h->sm_count, h->stream, first, last);

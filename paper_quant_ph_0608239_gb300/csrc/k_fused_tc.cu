@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
     __shared__ __align__(8) uint64_t bar_ld[NS], bar_mma[NS], bar_b;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_hb[kMaxHTC];     // the high tile bits, indexed at run time
+    __shared__ uint32_t s_sink[kSlotThreads / 32 * NS];  // written, never read (see the fetch)
     const int L = g.L, H = g.H;
     const uint32_t nruns = 1u << H;
     const uint32_t run_bytes = 8u << L;
@@ -238,6 +239,17 @@ __global__ void __launch_bounds__(kSlotThreads * TcSlots<K>::NS, 1)
                 if (p < CK / HS - 1) slot_sync(bar_id);
             }
             if (p == CK / HS - 1) {
+                // The fetch buffer goes back to the bulk copies: every load
+                // of this part has returned (their words reduced over the
+                // warp and kept by a shared-memory store -- with no rotation
+                // nothing else uses them before the barrier) and is ordered
+                // before the copy that overwrites the buffer.
+                uint32_t fold = 0;
+#pragma unroll
+                for (int c = 0; c < HS; c++) fold ^= __float_as_uint(x[c].x) ^ __float_as_uint(x[c].y);
+                fold = __reduce_xor_sync(0xffffffffu, fold);
+                if (lane == 0) s_sink[warp] = fold;
+                fence_proxy_async_smem();
                 slot_sync(bar_id);
                 if (ws == 0 && tile + stride < ntiles) issue_load(tile + stride);  // the fetch buffer is free
             }

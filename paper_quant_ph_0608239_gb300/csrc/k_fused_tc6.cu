@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kThreads6, 1)
     // last tile's accumulator read (its MMAs may start); bar_mma: MMAs done;
     // bar_b: B loaded
     __shared__ __align__(8) uint64_t bar_ld[2], bar_free[2], bar_ready, bar_mma, bar_b;
+    __shared__ uint32_t s_sink[32];  // written, never read (see the fetch)
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_hb[kMaxH6];
     const int L = g.L, H = g.H;
@@ -307,6 +308,15 @@ __global__ void __launch_bounds__(kThreads6, 1)
                 v[j] = make_float2(__uint_as_float(a0), __uint_as_float(a1));
                 v[j + 1] = make_float2(__uint_as_float(b0), __uint_as_float(b1));
             }
+            // every load has returned (its words reduced over the warp and
+            // kept by a shared-memory store) and is ordered before the bulk
+            // copy that will overwrite the buffer
+            uint32_t fold = 0;
+#pragma unroll
+            for (int j = 0; j < 16; j++) fold ^= __float_as_uint(v[j].x) ^ __float_as_uint(v[j].y);
+            fold = __reduce_xor_sync(0xffffffffu, fold);
+            if (lane == 0) s_sink[warp] = fold;
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_free[b]);  // this warp's share of the buffer is read
             return ok;

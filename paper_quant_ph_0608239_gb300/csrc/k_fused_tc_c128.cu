@@ -364,7 +364,10 @@ __global__ void __launch_bounds__(kThreadsAll128, 1)
             if (rotated) unrot(v);
             s_max[b][qq][m] = mx;
             quarter_sync(1u + (uint32_t)lq);
-            // this warp's amplitudes are in registers: its share of the buffer is free
+            // this warp's amplitudes are in registers (the exponent maxima
+            // above used every load): its share of the buffer is free, the
+            // loads ordered before the bulk copy that overwrites it
+            fence_proxy_async_smem();
             if (lane == 0) mbar_arrive(&bar_free);
             Eg_next = max(max(s_max[b][0][m], s_max[b][1][m]), max(s_max[b][2][m], s_max[b][3][m])) >> 23;
             return true;

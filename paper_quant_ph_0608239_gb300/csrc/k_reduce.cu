@@ -6,8 +6,8 @@
 // amplitudes are summed in FP32 before they enter an FP64 accumulator (the
 // FP32 partial sums of non-negative terms carry at most 16 ulp of relative
 // error, far below the precision of the amplitudes themselves); complex128
-// states are summed in FP64, except the per-bit marginals for n >= 13, whose
-// inner sums run in double-float (k_bits_partial_df).
+// states are summed in FP64.  The per-bit marginals for n >= 13 of either
+// precision run their inner sums in double-float (k_bits_partial_df).
 //
 // The partial sums of each block go to a caller-provided scratch buffer in
 // global memory and a second kernel adds them up.
@@ -128,24 +128,27 @@ __global__ void __launch_bounds__(kRedThreads) k_bits_partial(const amp_t<R> *__
     }
 }
 
-// Per-bit marginals of a complex128 state, n >= kGroupBits, with no FP64 in
-// the inner loop (GB300 issues FP64 at about 2 instructions per clock per SM,
-// fewer than reading the state at full bandwidth needs).  A warp takes groups
-// of 8192 consecutive amplitudes: lane l holds amplitudes l + 32 j, j < 256,
-// read in chunks of 8 (j = 8 c + k), so bits 0..4 of an index are the lane,
-// bits 5..7 are k, bits 8..12 are the chunk c and the higher bits are the
-// group's.  Each |a|^2 is a double-float from the IEEE bits (df_sqmag,
-// relative error below 2^-44; a chunk holding a magnitude >= 2 takes the FP64
-// branch).  Per group and lane the sums run in double-float over at most 32
-// terms: per k (bits 5..7), per set bit of c (bits 8..12, from the chunk
-// sums) and the group total.  At the end of the group they are added to FP64
-// accumulators; the group total, summed over the warp, is added by lane
-// b - 13 to bit b's accumulator when bit b of the group index is set.
+// Per-bit marginals, n >= kGroupBits, with no FP64 in the inner loop (GB300
+// issues FP64 at about 2 instructions per clock per SM, fewer than reading
+// the state at full bandwidth needs).  A warp takes groups of 8192
+// consecutive amplitudes: lane l holds amplitudes l + 32 j, j < 256, read in
+// chunks of 8 (j = 8 c + k), so bits 0..4 of an index are the lane, bits 5..7
+// are k, bits 8..12 are the chunk c and the higher bits are the group's.
+// Each |a|^2 of a complex128 state is a double-float from the IEEE bits
+// (df_sqmag, relative error below 2^-44; a chunk holding a magnitude >= 2
+// takes the FP64 branch); of a complex64 state it is an FP32 square, and a
+// chunk's 8 squares are summed in FP32.  Per group and lane the sums run in
+// double-float over at most 32 terms: per k (bits 5..7), per set bit of c
+// (bits 8..12, from the chunk sums) and the group total.  At the end of the
+// group they are added to FP64 accumulators; the group total, summed over the
+// warp, is added by lane b - 13 to bit b's accumulator when bit b of the
+// group index is set.
 constexpr int kGroupBits = 13;
 
 __device__ __forceinline__ double df_sum_d(df x) { return (double)x.h + (double)x.l; }  // exact
 
-__global__ void __launch_bounds__(kRedThreads) k_bits_partial_df(const double2 *__restrict__ a, int n,
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_bits_partial_df(const amp_t<R> *__restrict__ a, int n,
                                                                   double *__restrict__ partial) {
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bits_partial_df(const double2 *
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t ngroups = 1ull << (n - kGroupBits);
     for (uint64_t gi = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < ngroups; gi += warps) {
-        const double2 *p = a + (gi << kGroupBits) + lane;
+        const amp_t<R> *p = a + (gi << kGroupBits) + lane;
         df ak[8], bc[5], tg{0.0f, 0.0f};
 #pragma unroll
         for (int k = 0; k < 8; k++) ak[k] = df{0.0f, 0.0f};
@@ -165,26 +168,37 @@ __global__ void __launch_bounds__(kRedThreads) k_bits_partial_df(const double2 *
         for (int i = 0; i < 5; i++) bc[i] = df{0.0f, 0.0f};
 #pragma unroll 2
         for (int c = 0; c < 32; c++) {
-            double2 v[8];
+            amp_t<R> v[8];
 #pragma unroll
             for (int k = 0; k < 8; k++) v[k] = p[32 * (8 * c + k)];
-            uint32_t any = 0;
-#pragma unroll
-            for (int k = 0; k < 8; k++)
-                any |= (uint32_t)(df_bits64(v[k].x) >> 32) | (uint32_t)(df_bits64(v[k].y) >> 32);
             df q[8];
-            if (__any_sync(0xffffffffu, (any & 0x40000000u) != 0u)) {
-                // a magnitude >= 2 in the chunk: the squares in FP64
+            if constexpr (sizeof(R) == 4) {
+                // complex64: the square in FP32 (the precision of the state)
 #pragma unroll
-                for (int k = 0; k < 8; k++) q[k] = df_from_double(fma(v[k].x, v[k].x, v[k].y * v[k].y));
+                for (int k = 0; k < 8; k++) q[k] = df{fmaf(v[k].x, v[k].x, v[k].y * v[k].y), 0.0f};
             } else {
+                uint32_t any = 0;
 #pragma unroll
-                for (int k = 0; k < 8; k++) q[k] = df_sqmag(v[k].x, v[k].y);
+                for (int k = 0; k < 8; k++)
+                    any |= (uint32_t)(df_bits64(v[k].x) >> 32) | (uint32_t)(df_bits64(v[k].y) >> 32);
+                if (__any_sync(0xffffffffu, (any & 0x40000000u) != 0u)) {
+                    // a magnitude >= 2 in the chunk: the squares in FP64
+#pragma unroll
+                    for (int k = 0; k < 8; k++) q[k] = df_from_double(fma(v[k].x, v[k].x, v[k].y * v[k].y));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; k++) q[k] = df_sqmag(v[k].x, v[k].y);
+                }
             }
 #pragma unroll
             for (int k = 0; k < 8; k++) ak[k] = df_add_pos(ak[k], q[k]);
-            const df cs = df_add_pos(df_add_pos(df_add_pos(q[0], q[1]), df_add_pos(q[2], q[3])),
-                                     df_add_pos(df_add_pos(q[4], q[5]), df_add_pos(q[6], q[7])));
+            df cs;
+            if constexpr (sizeof(R) == 4) {  // complex64: the chunk's 8 squares summed in FP32
+                cs = df{((q[0].h + q[1].h) + (q[2].h + q[3].h)) + ((q[4].h + q[5].h) + (q[6].h + q[7].h)), 0.0f};
+            } else {
+                cs = df_add_pos(df_add_pos(df_add_pos(q[0], q[1]), df_add_pos(q[2], q[3])),
+                                df_add_pos(df_add_pos(q[4], q[5]), df_add_pos(q[6], q[7])));
+            }
             tg = df_add_pos(tg, cs);
 #pragma unroll
             for (int i = 0; i < 5; i++)
@@ -399,10 +413,15 @@ cudaError_t launch_bit_probs(const void *amp, int dt, int n, double *scratch, do
             k_bits_small<double><<<1, 256, 0, s>>>(static_cast<const double2 *>(amp), n, dout);
         return cudaGetLastError();
     }
-    if (dt != 0 && n >= kGroupBits) {
+    if (n >= kGroupBits) {
         uint64_t blocks = ((1ull << (n - kGroupBits)) + 7) / 8;
         if (blocks > (uint64_t)kRedBlocks) blocks = kRedBlocks;
-        k_bits_partial_df<<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const double2 *>(amp), n, scratch);
+        if (dt == 0)
+            k_bits_partial_df<float><<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const float2 *>(amp), n,
+                                                                         scratch);
+        else
+            k_bits_partial_df<double><<<(int)blocks, kRedThreads, 0, s>>>(static_cast<const double2 *>(amp), n,
+                                                                          scratch);
         k_sum_columns<<<1, 256, 0, s>>>(scratch, (int)blocks, n, n, dout);
         return cudaGetLastError();
     }

@@ -223,8 +223,8 @@ cudaError_t launch_permute(void *amp, int elem_bytes, const TileGeom &g, const P
                            int sm_count, cudaStream_t s);
 
 // ------------------------------------------------------------ phase passes
-// A run of commuting phase shifts applied in one pass (k_phase.cu, complex64;
-// tables built by the planner, planner.hpp PhasePass): ntab tables of
+// A run of commuting phase shifts applied in one pass (k_phase.cu; tables
+// built by the planner, planner.hpp PhasePass): ntab tables of
 // kPhaseTableWords fixed-point turns, table t for the chunk pair (ta[t],
 // tb[t]), ta <= tb, chunk c = index bits kPhaseChunk c .. kPhaseChunk c + 4.
 constexpr int kPhaseChunk = 5;
@@ -238,10 +238,12 @@ struct PhaseMeta {
 // n >= 10; tables: device copy of ntab * kPhaseTableWords words.
 cudaError_t launch_phase_pass(void *amp, int n, const uint32_t *tables, const PhaseMeta &m, int sm_count,
                               cudaStream_t s);
-// complex128 (IEEE doubles in and out, double-float arithmetic): 64-bit
-// turns, ntab <= 24.
+// complex128, double-float arithmetic: 64-bit turns, ntab <= 24.  The state
+// is read as IEEE doubles if in_ieee, else in the double-float form of the
+// tensor-core blocks (re.h, re.l, im.h, im.l floats in the amplitude's 16
+// bytes), and written as IEEE doubles if out_ieee, else double-float.
 cudaError_t launch_phase_pass128(void *amp, int n, const uint64_t *tables, const PhaseMeta &m, int sm_count,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool in_ieee, bool out_ieee);
 
 // ------------------------------------------------------------ batches
 struct BatchCircuit {

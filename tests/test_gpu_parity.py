@@ -753,6 +753,37 @@ def test_phase_pass_adder_c128(q, m):
     st.free()
 
 
+@pytest.mark.parametrize("shape", ["alone", "first", "last"])
+@pytest.mark.parametrize("pairs", ["separable", "chunk01"])
+def test_phase_pass_c128_ends(q, shape, pairs):
+    """complex128 phase pass as the whole plan (IEEE doubles in and out), as
+    its first step (IEEE in, double-float out to the blocks) and as its last
+    (double-float in, IEEE out), with the factor split into lane and loop
+    parts (no gate pairs index bits 0..4 with bits 5..9) and without, on a
+    random state, against the oracle."""
+    n = 16
+    rng = np.random.default_rng(3 * ["alone", "first", "last"].index(shape) + (pairs == "chunk01"))
+    phases = []
+    while len(phases) < 40:
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        if pairs == "separable" and {a // 5, b // 5} == {0, 1}:
+            continue
+        phases.append(g1("R", a, (b,), (float(rng.uniform(0, 2 * np.pi)),)))
+    if pairs == "chunk01":
+        phases.append(g1("R", 2, (7,), (0.3,)))
+    layer = [g1("H", t) for t in range(n)]
+    gates = {"alone": phases, "first": phases + layer, "last": layer + phases}[shape]
+    psi = rand_state(n, 5)
+    ref = oracle.run(n, gates, state=psi.copy())
+    st = q.State(n, "c128")
+    st.set_state(psi)
+    st.profile(True)
+    st.run(gates, fuse_k=5)
+    assert "phase_pass" in st.profile_read()
+    assert err(st.get_state(), ref) < TOL["c128"], err(st.get_state(), ref)
+    st.free()
+
+
 @pytest.mark.parametrize("n", [12, 13, 22])
 def test_phase_pass_random_phases(q, n):
     """A long run of controlled phases on random qubit pairs (every chunk
