@@ -838,7 +838,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-companions", action="store_true")
-    ap.add_argument("--n", type=int, default=0, help="override the qubit count (smaller cases for profiling)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="override the qubit count of the random, Hadamard and seeded adder workloads (smaller cases for profiling)")
     ap.add_argument("--pergate", action="store_true", help="one sweep of the state per gate (no tile passes)")
     ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's precision")
     ap.add_argument("--batch-count", type=int, default=0, help="batch workload: only the first N circuits")
@@ -851,7 +852,12 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     ws, rank, local = dist_env()
     w = dict(WORKLOADS[args.workload])
-    if args.n and w["kind"] in ("random", "hadamard"):
+    if args.n and (w["kind"] in ("random", "hadamard") or (w["kind"] == "adder" and "seed" in w)):
+        if w["kind"] == "adder":  # two registers of n / 2 qubits
+            if args.n % 2:
+                ap.error("the seeded adder takes an even --n")
+            w["m"] = args.n // 2
+            w["text"] = w["text"].replace("two 15-qubit registers", "two %d-qubit registers" % w["m"])
         w["n"] = args.n
         w["text"] = w["text"].replace("%d qubits" % WORKLOADS[args.workload]["n"], "%d qubits" % args.n)
         args.workload = args.workload + "_n%d" % args.n
