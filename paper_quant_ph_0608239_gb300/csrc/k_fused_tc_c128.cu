@@ -556,6 +556,8 @@ bool fused_tc128_prepare_b(const double *U, uint16_t *out) {
     double rowsum[kReals][kDigits];
     for (int n = 0; n < kReals; n++)
         for (int j = 0; j < kDigits; j++) rowsum[n][j] = 0.0;
+    double unit[kDigits];  // 2^(7 + 9 j): slice j's digit times this is the integer c_j (exact)
+    for (int j = 0; j < kDigits; j++) unit[j] = std::ldexp(1.0, 7 + kDigitBits * j);
     for (int r = 0; r < kAmps; r++)
         for (int c = 0; c < kAmps; c++) {
             const double ur = U[2 * (r * kAmps + c)], ui = U[2 * (r * kAmps + c) + 1];
@@ -568,7 +570,7 @@ bool fused_tc128_prepare_b(const double *U, uint16_t *out) {
                 dg_split_entry(v[e], d);
                 for (int j = 0; j < kDigits; j++) {
                     out[(j * kSliceBytes + bcanon_off((uint32_t)nn[e], (uint32_t)kk[e])) / 2] = (uint16_t)dg_bf16(d[j]);
-                    rowsum[nn[e]][j] += std::fabs(std::ldexp((double)d[j], 7 + kDigitBits * j));  // |c_j|
+                    rowsum[nn[e]][j] += std::fabs((double)d[j] * unit[j]);  // |c_j|
                 }
             }
         }

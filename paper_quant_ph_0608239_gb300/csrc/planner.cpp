@@ -696,33 +696,41 @@ namespace qsim {
 
 namespace {
 
-// Apply one gate to a 2^k vector in block coordinates (bit j = pos[j]).
-void apply_in_block(const PGate &g, const int *pos, int k, std::complex<double> *v) {
+// Apply one gate to the D = 2^k columns of a block matrix in block
+// coordinates (bit j = pos[j]); cols holds column c at c * D.  The bit
+// positions are resolved once per gate, then every column takes the same
+// update.
+void apply_in_block(const PGate &g, const int *pos, int k, std::complex<double> *cols) {
     auto loc = [&](int b) {
         for (int j = 0; j < k; j++)
             if (pos[j] == b) return j;
         return -1;
     };
     uint32_t cm = 0;
-    for (int b = 0; b < 64; b++)
-        if ((g.cmask >> b) & 1ull) cm |= 1u << loc(b);
+    for (uint64_t m = g.cmask; m; m &= m - 1) cm |= 1u << loc(__builtin_ctzll(m));
     const uint32_t D = 1u << k;
     if (g.kind == QSIM_GATE_SWAP) {
         const uint32_t b0 = 1u << loc(g.t0), b1 = 1u << loc(g.t1);
-        for (uint32_t i = 0; i < D; i++) {
-            if (!(i & b0) || (i & b1) || (i & cm) != cm) continue;
-            std::swap(v[i], v[(i & ~b0) | b1]);
+        for (uint32_t c = 0; c < D; c++) {
+            std::complex<double> *v = cols + (size_t)c * D;
+            for (uint32_t i = 0; i < D; i++) {
+                if (!(i & b0) || (i & b1) || (i & cm) != cm) continue;
+                std::swap(v[i], v[(i & ~b0) | b1]);
+            }
         }
         return;
     }
     const uint32_t bt = 1u << loc(g.t0);
     const std::complex<double> u00(g.U.u[0], g.U.u[1]), u01(g.U.u[2], g.U.u[3]);
     const std::complex<double> u10(g.U.u[4], g.U.u[5]), u11(g.U.u[6], g.U.u[7]);
-    for (uint32_t i = 0; i < D; i++) {
-        if ((i & bt) || (i & cm) != cm) continue;
-        const std::complex<double> a0 = v[i], a1 = v[i | bt];
-        v[i] = u00 * a0 + u01 * a1;
-        v[i | bt] = u10 * a0 + u11 * a1;
+    for (uint32_t c = 0; c < D; c++) {
+        std::complex<double> *v = cols + (size_t)c * D;
+        for (uint32_t i = 0; i < D; i++) {
+            if ((i & bt) || (i & cm) != cm) continue;
+            const std::complex<double> a0 = v[i], a1 = v[i | bt];
+            v[i] = u00 * a0 + u01 * a1;
+            v[i | bt] = u10 * a0 + u11 * a1;
+        }
     }
 }
 
@@ -742,17 +750,17 @@ void emit_block(const std::vector<const PGate *> &gs, uint64_t mask, int n, int 
         if (!((mask >> q) & 1ull)) b.pos[j++] = q;
     std::sort(b.pos, b.pos + k);
     const uint32_t D = 1u << k;
-    std::vector<std::complex<double>> col(D);
+    // column c of U = the block applied to |c>: every column starts as its
+    // basis vector and takes the gates in order
+    std::vector<std::complex<double>> cols((size_t)D * D, std::complex<double>(0.0, 0.0));
+    for (uint32_t c = 0; c < D; c++) cols[(size_t)c * D + c] = 1.0;
+    for (const PGate *g : gs) apply_in_block(*g, b.pos, k, cols.data());
     b.U.assign(2 * (size_t)D * D, 0.0);
-    for (uint32_t c = 0; c < D; c++) {  // column c of U = the block applied to |c>
-        std::fill(col.begin(), col.end(), std::complex<double>(0.0, 0.0));
-        col[c] = 1.0;
-        for (const PGate *g : gs) apply_in_block(*g, b.pos, k, col.data());
+    for (uint32_t c = 0; c < D; c++)
         for (uint32_t r = 0; r < D; r++) {
-            b.U[2 * (r * D + c)] = col[r].real();
-            b.U[2 * (r * D + c) + 1] = col[r].imag();
+            b.U[2 * (r * D + c)] = cols[(size_t)c * D + r].real();
+            b.U[2 * (r * D + c) + 1] = cols[(size_t)c * D + r].imag();
         }
-    }
     b.flops = 8.0 * D * std::ldexp(1.0, n);
     out.push_back(std::move(b));
 }
