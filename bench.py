@@ -77,6 +77,23 @@ FALLBACK_BF16_TFLOPS = 1900.0
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
+def resize_workload(name, n):
+    """The workload `name` at n qubits (the random circuit, the Hadamard
+    replay, the seeded adder with two registers of n / 2 qubits): its
+    description and its new name."""
+    w = dict(WORKLOADS[name])
+    if not (w["kind"] in ("random", "hadamard") or (w["kind"] == "adder" and "seed" in w)):
+        raise ValueError("--n does not apply to %s" % name)
+    if w["kind"] == "adder":
+        if n % 2:
+            raise ValueError("the seeded adder takes an even --n")
+        w["m"] = n // 2
+        w["text"] = w["text"].replace("two %d-qubit registers" % WORKLOADS[name]["m"], "two %d-qubit registers" % w["m"])
+    w["text"] = w["text"].replace("%d qubits" % WORKLOADS[name]["n"], "%d qubits" % n)
+    w["n"] = n
+    return w, "%s_n%d" % (name, n)
+
+
 def workload_gates(w):
     if w["kind"] == "random":
         return inputs.random_circuit(w["n"], w["depth"], w["seed"]), inputs.random_basis(w["n"], w["seed"])
@@ -852,15 +869,11 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     ws, rank, local = dist_env()
     w = dict(WORKLOADS[args.workload])
-    if args.n and (w["kind"] in ("random", "hadamard") or (w["kind"] == "adder" and "seed" in w)):
-        if w["kind"] == "adder":  # two registers of n / 2 qubits
-            if args.n % 2:
-                ap.error("the seeded adder takes an even --n")
-            w["m"] = args.n // 2
-            w["text"] = w["text"].replace("two 15-qubit registers", "two %d-qubit registers" % w["m"])
-        w["n"] = args.n
-        w["text"] = w["text"].replace("%d qubits" % WORKLOADS[args.workload]["n"], "%d qubits" % args.n)
-        args.workload = args.workload + "_n%d" % args.n
+    if args.n:
+        try:
+            w, args.workload = resize_workload(args.workload, args.n)
+        except ValueError as e:
+            ap.error(str(e))
     if args.dtype and args.dtype != w["dtype"] and w["kind"] != "batch":
         w["dtype"] = args.dtype
         w["text"] = w["text"].replace("complex128", args.dtype).replace("complex64", args.dtype)

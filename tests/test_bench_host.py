@@ -164,3 +164,30 @@ def test_config_lines_bookkeeping(monkeypatch):
     assert res["batch512_c64"]["eff_hbm_frac"] == pytest.approx(5e9 / (bms / 1e3) / 1e9 / 1000.0)
     assert set(res["random34_c64"]) == {"tensor_cores_k5", "tensor_cores_k6"}
     assert "random34_c64" in res and "qft10_c128" in res
+
+
+def test_resize_workload():
+    """--n: the random circuit and the Hadamard replay at n qubits, the seeded
+    adder as two registers of n / 2 qubits (its gate list on exactly n
+    qubits, its operation count the adder's N_O); the paper's fixed adders,
+    the batch and an odd adder size refuse it."""
+    import numpy as np
+
+    import bench
+    import inputs
+
+    w, name = bench.resize_workload("random30_c128", 24)
+    assert (w["n"], name) == (24, "random30_c128_n24") and "24 qubits" in w["text"]
+    assert bench.WORKLOADS["random30_c128"]["n"] == 30  # the table itself is left alone
+    w, name = bench.resize_workload("hadamard30_c128", 27)
+    assert w["n"] == 27 and len(bench.workload_gates(w)[0]) == 27
+    w, name = bench.resize_workload("adder30_c64", 26)
+    assert (w["n"], w["m"], name) == (26, 13, "adder30_c64_n26")
+    assert "two 13-qubit registers" in w["text"] and "26 qubits" in w["text"]
+    gates, x0 = bench.workload_gates(w)
+    used = {q for g in gates for q in tuple(g.targets) + tuple(g.controls)}
+    values = [int(v) for v in np.random.default_rng(w["seed"]).integers(0, 1 << 13, 2)]
+    assert x0 == 0 and max(used) == 25 and len(gates) == inputs.adder_gate_count(values, 13)
+    for bad, n in (("adder3x11_c128", 30), ("batch512_c64", 20), ("adder30_c64", 25)):
+        with pytest.raises(ValueError):
+            bench.resize_workload(bad, n)
