@@ -377,7 +377,11 @@ QSIM_API qsim_status qsim_norm(qsim_handle h, double *out);
 QSIM_API qsim_status qsim_probs(qsim_handle h, double *out, size_t len);
 
 /* qsim_qubit_probs: out[q] = <Q_q> = probability that logical qubit q is 1
- * (Eq. Shor7; DO MEASUREMENT of App. A, no collapse), FP64, n values. */
+ * (Eq. Shor7; DO MEASUREMENT of App. A, no collapse), FP64, n values.  For
+ * n >= 13 the sums run in double-float (about 48 bits) over groups of 8192
+ * amplitudes and in FP64 across groups; complex128 squares carry a relative
+ * error below 2^-44, and magnitudes of 2^64 or more are outside the float
+ * range these sums use. */
 QSIM_API qsim_status qsim_qubit_probs(qsim_handle h, double *out);
 
 /* qsim_qubit_probs_noalloc: the per-qubit marginals of qsim_qubit_probs for
