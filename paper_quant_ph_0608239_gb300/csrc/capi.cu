@@ -543,8 +543,10 @@ static void gather_phase_tables(qsim_plan_s &P, bool wide) {
     }
 }
 
+// search: the block planner also tries its beam search (plan_fused); the
+// batch's many small plans skip it
 static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, const qsim_opts *opts,
-                              qsim_plan_s &P) {
+                              qsim_plan_s &P, bool search = true) {
     if (ng && !gates) return fail(QSIM_EINVAL, "gates is NULL");
     qsim_opts o;
     qsim_default_opts(&o);
@@ -577,7 +579,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
         // complex128 blocks on the tensor cores (bf16 digit slices) and phase
         // passes; a block the scheme cannot take exactly sends the whole plan
         // to the CUDA cores
-        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables128, P.blocks, P.phases))
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables128, P.blocks, P.phases, search))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         gather_phase_tables(P, true);
         const size_t per = fused_tc128_b_bytes() / sizeof(float);
@@ -611,7 +613,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     if (o.fuse_k == 6 && h->dt == QSIM_C64 && fused_tc6_supported(h->n)) {
         // complex64 6-qubit blocks on the tensor cores (bf16 hi/mid/lo slices),
         // long runs of phase shifts as phase passes
-        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases))
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases, search))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         gather_phase_tables(P, false);
         const size_t per = fused_tc6_b_bytes() / sizeof(float);
@@ -637,7 +639,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     if (o.fuse_k > 0 && (h->dt == QSIM_C128 || !fused_tc_supported((int)h->dt, o.fuse_k, h->n))) {
         // dense blocks on the CUDA cores (complex128, k = 1..6, small registers)
         if (o.fuse_k > 6 || o.fuse_k > h->n) return fail(QSIM_EUNSUPPORTED, "fused blocks need k <= min(6, n)");
-        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks))
+        if (!plan_fused(pg, h->n, o.fuse_k, P.blocks, search))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         const size_t ent = (size_t)1 << (2 * o.fuse_k);
         P.cuda_core = true;
@@ -664,7 +666,7 @@ static qsim_status build_plan(qsim_state *h, const qsim_gate *gates, size_t ng, 
     if (o.fuse_k > 0) {
         // complex64 4- and 5-qubit blocks on the tensor cores (3xTF32), long
         // runs of phase shifts as phase passes
-        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases))
+        if (!plan_fused_phases(pg, h->n, o.fuse_k, kPhaseRunMin, kMaxPhaseTables, P.blocks, P.phases, search))
             return fail(QSIM_EINVAL, "a gate acts on more qubits than fuse_k");
         gather_phase_tables(P, false);
         const size_t per = 2 * (size_t)(2 << o.fuse_k) * (size_t)(2 << o.fuse_k);
@@ -1622,7 +1624,7 @@ static qsim_status batch_create(const qsim_circuit *cs, size_t nc, const qsim_op
             for (size_t j = next++; j < lane.size(); j = next++) {
                 const size_t i = lane[j];
                 qsim_plan_s *P = new qsim_plan_s;
-                built_st[i] = build_plan(cs[i].state, cs[i].gates, cs[i].ng, &fo, *P);
+                built_st[i] = build_plan(cs[i].state, cs[i].gates, cs[i].ng, &fo, *P, false);
                 if (built_st[i] == QSIM_OK) built[i] = P;
                 else plan_release(P);
             }

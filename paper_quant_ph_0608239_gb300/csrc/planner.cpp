@@ -767,16 +767,30 @@ void emit_block(const std::vector<const PGate *> &gs, uint64_t mask, int n, int 
 
 }  // namespace
 
-bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out) {
-    out.clear();
-    const int ng = (int)gates.size();
-    std::vector<uint64_t> bits((size_t)ng);
-    std::vector<std::vector<int>> queue(64);  // per qubit: the gates touching it, in circuit order
-    for (int i = 0; i < ng; i++) {
-        bits[i] = block_bits(gates[i]);
-        if (popc(bits[i]) > k) return false;
-        for (uint64_t m = bits[i]; m; m &= m - 1) queue[__builtin_ctzll(m)].push_back(i);
-    }
+namespace {
+
+// Candidate block sets of the search: the breadth of the search over the
+// qubit sets a block can reach (plan_fused).
+constexpr int kBlockBeam = 16;
+
+struct BlockDraft {
+    std::vector<int> picks;  // gate indices in the order they are applied
+    uint64_t mask;           // the block's qubits
+};
+
+// One grouping of the circuit into blocks of at most k qubits.  A block
+// starts at the earliest gate not yet placed and takes only gates whose
+// earlier gates on each of their qubits are placed.  beam = 0: the greedy
+// block (gates inside the block's qubits first, else the gate after which the
+// fewest-qubits-first rule takes the most gates).  beam > 0: the larger of
+// that block and the best one found by a beam search over the qubit sets the
+// block can grow into (beam sets kept per added gate, ranked by the gates
+// they hold plus those the fewest-qubits-first rule would still add).
+void draft_blocks(const std::vector<uint64_t> &bits, const std::vector<std::vector<int>> &queue, int k, int beam,
+                  std::vector<BlockDraft> &out) {
+    const int ng = (int)bits.size();
+    int nq = 0;  // qubits that have gates: the scans below stop there
+    for (uint64_t b : bits) nq = std::max(nq, 64 - __builtin_clzll(b));
     using Heads = std::array<uint32_t, 64>;  // per qubit: first gate of its queue not yet placed
     auto front = [&](const Heads &hd, int q) { return hd[q] < queue[q].size() ? queue[q][hd[q]] : -1; };
     auto ready = [&](const Heads &hd, int i) {  // every earlier gate on i's qubits is placed
@@ -792,7 +806,7 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
     auto next_min = [&](const Heads &hd, uint64_t mask, int &add) {
         int pick = -1;
         add = 65;
-        for (int q = 0; q < 64; q++) {
+        for (int q = 0; q < nq; q++) {
             const int i = front(hd, q);
             if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | mask) > k) continue;
             const int a = popc(bits[i] & ~mask);
@@ -812,34 +826,47 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
         }
         return c;
     };
+    struct Node {
+        uint64_t mask;
+        Heads hd;
+        std::vector<int> picks;
+        int score;
+    };
+    // every ready gate inside the node's qubits (the block's final gate set
+    // depends only on its qubit set)
+    auto close = [&](Node &nd) {
+        int add, i;
+        while ((i = next_min(nd.hd, nd.mask, add)) >= 0 && add == 0) {
+            take(nd.hd, i);
+            nd.picks.push_back(i);
+        }
+    };
     Heads head{};
     std::vector<char> placed((size_t)ng, 0);
-    std::vector<const PGate *> cur;
     int first = 0;
     for (;;) {
         while (first < ng && placed[first]) first++;
         if (first == ng) break;
-        uint64_t mask = 0;
-        cur.clear();
-        int pick = first;  // a block starts at the earliest gate not yet placed
+        Node best{0, head, {}, 0};
+        int pick = first;
         while (pick >= 0) {
-            mask |= bits[pick];
-            cur.push_back(&gates[pick]);
-            placed[pick] = 1;
-            take(head, pick);
+            best.mask |= bits[pick];
+            best.picks.push_back(pick);
+            take(best.hd, pick);
             int add;
-            pick = next_min(head, mask, add);  // gates inside the block's qubits come first
+            pick = next_min(best.hd, best.mask, add);  // gates inside the block's qubits come first
             if (pick < 0 || add == 0) continue;
             // a gate adding qubits: the one after which the block takes the
             // most gates (fewer added qubits, then the earliest, on ties)
             int best_cnt = -1, best_add = 65;
-            for (int q = 0; q < 64; q++) {
-                const int i = front(head, q);
-                if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | mask) > k || !ready(head, i)) continue;
-                Heads h2 = head;
+            for (int q = 0; q < nq; q++) {
+                const int i = front(best.hd, q);
+                if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | best.mask) > k || !ready(best.hd, i))
+                    continue;
+                Heads h2 = best.hd;
                 take(h2, i);
-                const int cnt = greedy_count(h2, mask | bits[i]);
-                const int a = popc(bits[i] & ~mask);
+                const int cnt = greedy_count(h2, best.mask | bits[i]);
+                const int a = popc(bits[i] & ~best.mask);
                 if (cnt > best_cnt || (cnt == best_cnt && (a < best_add || (a == best_add && i < pick)))) {
                     best_cnt = cnt;
                     best_add = a;
@@ -847,7 +874,69 @@ bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<Fused
                 }
             }
         }
-        emit_block(cur, mask, n, k, out);
+        if (beam > 0) {
+            Node root{bits[first], head, {first}, 0};
+            take(root.hd, first);
+            close(root);
+            root.score = (int)root.picks.size() + greedy_count(root.hd, root.mask);
+            if (root.picks.size() > best.picks.size()) best = root;
+            std::vector<Node> level{root}, next;
+            while (!level.empty()) {
+                next.clear();
+                for (const Node &nd : level)
+                    for (int q = 0; q < nq; q++) {
+                        const int i = front(nd.hd, q);
+                        if (i < 0 || __builtin_ctzll(bits[i]) != q || popc(bits[i] | nd.mask) > k || !ready(nd.hd, i))
+                            continue;
+                        const uint64_t m2 = nd.mask | bits[i];
+                        bool seen = false;
+                        for (const Node &o : next) seen = seen || o.mask == m2;
+                        if (seen) continue;
+                        Node c = nd;
+                        c.mask = m2;
+                        take(c.hd, i);
+                        c.picks.push_back(i);
+                        close(c);
+                        c.score = (int)c.picks.size() + greedy_count(c.hd, c.mask);
+                        if (c.picks.size() > best.picks.size()) best = c;
+                        next.push_back(std::move(c));
+                    }
+                std::stable_sort(next.begin(), next.end(), [](const Node &x, const Node &y) { return x.score > y.score; });
+                if ((int)next.size() > beam) next.resize((size_t)beam);
+                level.swap(next);
+            }
+        }
+        for (int i : best.picks) placed[i] = 1;
+        head = best.hd;
+        out.push_back(BlockDraft{std::move(best.picks), best.mask});
+    }
+}
+
+}  // namespace
+
+bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out, bool search) {
+    out.clear();
+    const int ng = (int)gates.size();
+    std::vector<uint64_t> bits((size_t)ng);
+    std::vector<std::vector<int>> queue(64);  // per qubit: the gates touching it, in circuit order
+    for (int i = 0; i < ng; i++) {
+        bits[i] = block_bits(gates[i]);
+        if (popc(bits[i]) > k) return false;
+        for (uint64_t m = bits[i]; m; m &= m - 1) queue[__builtin_ctzll(m)].push_back(i);
+    }
+    // the greedy grouping, and with search the one that also tries the beam's
+    // blocks: the one with fewer blocks is kept (the greedy one on ties)
+    std::vector<BlockDraft> plan, alt;
+    draft_blocks(bits, queue, k, 0, plan);
+    if (search) {
+        draft_blocks(bits, queue, k, kBlockBeam, alt);
+        if (alt.size() < plan.size()) plan.swap(alt);
+    }
+    std::vector<const PGate *> cur;
+    for (const BlockDraft &d : plan) {
+        cur.clear();
+        for (int i : d.picks) cur.push_back(&gates[i]);
+        emit_block(cur, d.mask, n, k, out);
     }
     return true;
 }
@@ -954,9 +1043,9 @@ static int phase_tables(const std::vector<PGate> &run) {
 }
 
 bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, int max_tables,
-                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases) {
+                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases, bool search) {
     std::vector<FusedBlock> plain;
-    if (!plan_fused(gates, n, k, plain)) return false;
+    if (!plan_fused(gates, n, k, plain, search)) return false;
     // Runs: phase shifts are held back while the gates after them commute
     // with them (none targets one of their bits); a gate that does not
     // commute releases the whole held set before it -- as one run if it is
@@ -996,7 +1085,7 @@ bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_ga
     std::vector<PhasePass> pps;
     for (size_t s = 0; s < segs.size(); s++) {
         std::vector<FusedBlock> part;
-        if (!plan_fused(segs[s], n, k, part)) return false;
+        if (!plan_fused(segs[s], n, k, part, search)) return false;
         for (FusedBlock &b : part) with.push_back(std::move(b));
         if (s < runs.size()) {
             PhasePass pp;

@@ -119,7 +119,10 @@ struct FusedBlock {
     double flops;             // algorithmic flops: 8 * 2^k per amplitude
     int phase = -1;           // >= 0: not a dense block but phase pass number `phase` (PhasePass)
 };
-bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out);
+// With search, a second grouping whose blocks may instead come from a beam
+// search over the qubit sets a block can grow into (planner.cpp,
+// draft_blocks) is made too, and the one with fewer blocks is kept.
+bool plan_fused(const std::vector<PGate> &gates, int n, int k, std::vector<FusedBlock> &out, bool search = true);
 
 // Phase passes.  Phase shifts with up to one control, diag(1, e^(i phi)) on
 // a target with its control (Eqs. NUM5 and COMM5), commute with each other and
@@ -145,7 +148,7 @@ bool phase_term(const PGate &g, uint64_t &turns, uint64_t &bits);
 // pairs) taken out as a phase pass where that gives fewer passes in all;
 // blocks with phase >= 0 stand for phases[phase].
 bool plan_fused_phases(const std::vector<PGate> &gates, int n, int k, int min_gates, int max_tables,
-                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases);
+                       std::vector<FusedBlock> &out, std::vector<PhasePass> &phases, bool search = true);
 
 // Tile geometry of a fused block on the tensor cores: T = k + 7 bits holding
 // the block's qubits; false if n is too small.

@@ -135,3 +135,29 @@ def test_gate_wider_than_k_is_rejected(q):
         with pytest.raises(QsimError):
             q.fuse_blocks(8, cnot, bad_k)
     assert q.fuse_blocks(4, [], 3) == []
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_searched_blocks_equal_the_circuit(q, seed):
+    """The grouping the beam search may pick (plan_fused keeps whichever of
+    the greedy and the searched grouping has fewer blocks): deep random
+    circuits with controlled gates and SWAP gates, where the search changes
+    the blocks, applied block by block against the oracle."""
+    rng = np.random.default_rng(500 + seed)
+    n = 11
+    k = 3 + seed % 4
+    gates = inputs.random_circuit(n, 12, seed=600 + seed)
+    for g in controlled_mix(rng, n, 40, k):
+        gates.insert(int(rng.integers(len(gates) + 1)), g)
+    x0 = inputs.random_basis(n, seed=seed)
+    ref = oracle.run(n, gates, x0=x0)
+    blocks = q.fuse_blocks(n, gates, k)
+    assert np.max(np.abs(apply_blocks(n, blocks, x0) - ref)) < 1e-12
+    assert len(blocks) <= consecutive_count(gates, k)
+
+
+def test_search_saves_blocks_on_the_bench_circuit(q):
+    """On the 30-qubit depth-40 bench circuit the searched grouping needs
+    fewer 5-qubit blocks than the greedy one alone (145)."""
+    gates = inputs.random_circuit(30, 40, seed=2)
+    assert len(q.fuse_blocks(30, gates, 5)) <= 140
