@@ -997,8 +997,8 @@ void build_phase_pass(const std::vector<PGate> &run, PhasePass &pp) {
     for (const PGate &g : run) {
         uint64_t turns, bits;
         phase_term(g, turns, bits);
-        int b[2], nb = 0;
-        for (uint64_t m = bits; m; m &= m - 1) b[nb++] = __builtin_ctzll(m);
+        int b[2] = {0, 0}, nb = 0;  // a phase term has one or two bits
+        for (uint64_t m = bits; m && nb < 2; m &= m - 1) b[nb++] = __builtin_ctzll(m);
         const int ca = b[0] / kPhaseChunk, cb = (nb == 2 ? b[1] : b[0]) / kPhaseChunk;  // ca <= cb
         int &t = slot[ca * 64 + cb];
         if (t < 0) {
