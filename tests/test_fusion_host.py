@@ -161,3 +161,15 @@ def test_search_saves_blocks_on_the_bench_circuit(q):
     fewer 5-qubit blocks than the greedy one alone (145)."""
     gates = inputs.random_circuit(30, 40, seed=2)
     assert len(q.fuse_blocks(30, gates, 5)) <= 140
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_bench_generators_blocks_equal_the_circuit(q, k):
+    """The bench circuits' generators (depth 40 seed 2, depth 20 seed 4) at 16
+    qubits, grouped as the GPU plans group them, against the oracle."""
+    n = 16
+    for depth, seed in ((40, 2), (20, 4)):
+        gates = inputs.random_circuit(n, depth, seed=seed)
+        x0 = inputs.random_basis(n, seed=seed)
+        got = apply_blocks(n, q.fuse_blocks(n, gates, k), x0)
+        assert np.max(np.abs(got - oracle.run(n, gates, x0=x0))) < 1e-12
